@@ -1,0 +1,337 @@
+"""Benchmark of the folded-stencil hot path on one GB300 (or N replicas).
+
+Workload: 2D 5-point star, 4096 x 4096 FP32 grid, seeded dyadic coefficients
+summing to 1, values uniform in [0, 1), periodic, T = 1000 steps, advanced by
+temporal computation folding with temporal blocking.  One "step" of this
+bench is one full stencil_run of T = 1000 time steps on that grid.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2103_09235_gb300 import synth  # noqa: E402
+
+SHAPE = (4096, 4096)
+T_STEPS = 1000
+KIND = "star"
+SEED = synth.BASE_SEED + 2
+METRIC = "GStencil/s and % HBM roofline, folded TC vs plain FP32 at rel-L2 <= 1e-5"
+UNIT = "GStencil/s"
+WORKLOAD = "2D 5-point star 4096x4096 FP32, periodic, T=1000, dyadic coefficients (seeded)"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(T_sample: int, shape=SHAPE):
+    """Times the FP64 oracle on a bounded sample: the full grid, T_sample steps."""
+    import oracle
+    c = synth.dyadic_coeffs(SEED, 2, 1, KIND)
+    x = synth.grid(SEED, shape, np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.run(x, c, T_sample)
+    dt = time.perf_counter() - t0
+    return float(np.prod(shape)) * T_sample / dt / 1e9, dt, oracle.max_threads()
+
+
+def calibrate_oracle_steps(target_s: float) -> int:
+    _, dt, _ = oracle_sample(2)
+    return int(max(2, min(2000, round(target_s / max(dt / 2, 1e-6)))))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    T_sample = calibrate_oracle_steps(max(1.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(T_sample)
+    vals, secs = [], []
+    cores = 1
+    for _ in range(args.steps):
+        v, dt, cores = oracle_sample(T_sample)
+        vals.append(v)
+        secs.append(dt)
+    value = statistics.median(vals)
+    ms = 1e3 * float(np.prod(SHAPE)) * T_STEPS / (value * 1e9)
+    sample = "full %dx%d grid, %d of the %d steps per timed step (FP64 C oracle, OpenMP)" % (
+        SHAPE[0], SHAPE[1], T_sample, T_STEPS)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(SHAPE), "T": T_STEPS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    from paper_2103_09235_gb300 import build, binding
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    build.build()
+
+    c = synth.dyadic_coeffs(SEED, 2, 1, KIND)
+    x_host = synth.grid(SEED, SHAPE, np.float32)
+    npts = float(np.prod(SHAPE))
+    stream = torch.cuda.current_stream(dev)
+
+    def make_plan(m, b):
+        plan = binding.Plan(SHAPE, c)
+        plan.set_option("block_b", b)
+        return plan
+
+    xd = torch.from_numpy(x_host).to(dev)
+    yd = torch.empty_like(xd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed_steps(plan, m, T, k, w):
+        for _ in range(w):
+            plan.run(xd, yd, T, fold_m=m, stream=stream)
+        plan.sync(stream)
+        times = []
+        launches0 = plan.get("launches")
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.run(xd, yd, T, fold_m=m, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        plan.sync(stream)
+        return times, plan.get("launches") - launches0
+
+    m_best, b_best = args.fold_m, args.block_b
+    plan = make_plan(m_best, b_best)
+
+    # --- main timed region: whole job, inputs resident on the device
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times, launches = timed_steps(plan, m_best, T_STEPS, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if pg:
+        pg.barrier()
+    ms_step = statistics.mean(times)
+    ms_total = sum(times)
+    if pg:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = ws * npts * T_STEPS * args.steps / (ms_total * 1e-3) / 1e9
+    used_m, used_b = plan.get("last_m"), plan.get("last_b")
+
+    # --- dominant kernel: average duration of one folded pass, by difference of
+    # two CUDA-event-timed runs (T = one pass vs the full T) on the same stream
+    T_one = used_m * used_b
+    t_one, _ = timed_steps(plan, m_best, T_one, 5, 2)
+    n_pass = T_STEPS // (used_m * used_b)
+    rem_steps = T_STEPS - n_pass * used_m * used_b
+    pass_ms = (statistics.median(times) - statistics.median(t_one)) / max(1, n_pass - 1)
+    if rem_steps:
+        pass_ms = statistics.median(times) / max(1, n_pass)
+    peak, peak_kind = load_peaks()
+    alg_bytes = 2 * 4 * npts  # one read and one write of the grid per pass
+    achieved = alg_bytes / (pass_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                tr = json.load(f)
+            key = "m%d_b%d" % (used_m, used_b)
+            traffic = tr.get(key)
+        except Exception:
+            traffic = None
+
+    # --- end to end through the C ABI with host buffers (copies inside the timed region)
+    xh = torch.from_numpy(x_host).pin_memory().numpy()
+    yh = torch.empty(SHAPE, dtype=torch.float32).pin_memory().numpy()
+    for _ in range(max(1, args.warmup)):
+        plan.run(xh, yh, T_STEPS, fold_m=m_best, stream=stream)
+    e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.run(xh, yh, T_STEPS, fold_m=m_best, stream=stream)  # returns after the D2H copy
+        e1.record(stream)
+        e1.synchronize()
+        e_times.append(e0.elapsed_time(e1))
+    e2e_total = sum(e_times)
+    if pg:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = ws * npts * T_STEPS * args.steps / (e2e_total * 1e-3) / 1e9
+
+    # --- plain FP32 sweep beside it (the comparison the metric names)
+    variants = {}
+    if not args.no_variants:
+        pplan = make_plan(1, 1)
+        pt, _ = timed_steps(pplan, 1, 200, 3, 2)
+        variants["plain_fp32_m1_b1"] = npts * 200 / (statistics.median(pt) * 1e-3) / 1e9
+        pplan.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        Ts = calibrate_oracle_steps(args.cpu_seconds)
+        v, dt, cores = oracle_sample(Ts)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "full %dx%d grid, %d steps (%.1f s), FP64 C oracle" % (
+                   SHAPE[0], SHAPE[1], Ts, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(SHAPE), "T": T_STEPS,
+                       "fold_m": used_m, "block_b": used_b, "engine": "cuda-core",
+                       "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind, "kernel": "k_sweep2d",
+                         "pass_ms": pass_ms, "alg_bytes_per_launch": alg_bytes},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(npts * 4),
+                    "d2h_bytes_per_step": int(npts * 4)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fold-m", type=int, default=4)
+    ap.add_argument("--block-b", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

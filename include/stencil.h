@@ -1,0 +1,187 @@
+/*
+ * C ABI of the GB300 folded-stencil library.
+ *
+ * The library iterates a constant-coefficient star or box stencil over T time
+ * steps on a periodic 1D, 2D or 3D grid (Li et al., "Reducing Redundancy in
+ * Data Organization and Arithmetic Calculation for Stencil Computations",
+ * Section 1: each point at t+1 is the weighted sum of itself and its
+ * neighbours at t), optionally with temporal computation folding (Section 3):
+ * m consecutive steps collapse into one sweep of a folded stencil whose
+ * weights are the m-fold convolution power of the base weights (Section 3.2
+ * folding matrix, Section 3.3 Eq. vfold and Eq. horifold), and with temporal
+ * blocking of several folded sweeps per memory round trip (Section 3.4,
+ * tessellate tiling and time-loop fusion).
+ *
+ * Conventions used by every call:
+ *  - Orientation: out[p] = sum_o c[o] * in[(p + o) mod shape].
+ *  - Grids are dense C-order arrays, shape[0] slowest.
+ *  - Coefficients are a dense (2r+1)^ndim array of doubles, axis order
+ *    (z, y, x), each axis indexed by offset + r; a star stencil stores zeros
+ *    off the axes.
+ *  - Every call returns a status; none aborts, exits or traps.  Device-side
+ *    waits are bounded; a wait that runs out records STENCIL_ERR_TIMEOUT in
+ *    the plan's device status word, which stencil_sync reports.
+ *  - A "stream" is a cudaStream_t; NULL means the legacy default stream.
+ *  - Calls are not thread-safe on the same plan; one plan is used by one
+ *    stream at a time.  Different plans are independent.
+ */
+#ifndef STENCIL_GB300_H
+#define STENCIL_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stencil_plan_s *stencil_plan_t;   /* opaque, library-owned */
+typedef struct CUstream_st *stencil_stream_t;    /* same type as cudaStream_t */
+
+typedef enum {
+    STENCIL_F32 = 0,   /* float  */
+    STENCIL_F64 = 1    /* double */
+} stencil_dtype_t;
+
+typedef enum {
+    STENCIL_OK = 0,
+    STENCIL_ERR_INVALID_ARG = 1,   /* bad rank, radius, shape, pointer, T or m      */
+    STENCIL_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement   */
+    STENCIL_ERR_OOM = 3,           /* a device or host allocation failed            */
+    STENCIL_ERR_CUDA = 4,          /* a CUDA runtime or driver call failed          */
+    STENCIL_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out            */
+    STENCIL_ERR_DEVICE_CHECK = 6   /* a device-side consistency check failed        */
+} stencil_status_t;
+
+/* Values of the "precision" option. */
+typedef enum {
+    STENCIL_PREC_FP32 = 0,    /* CUDA-core FP32 sweeps (default)                          */
+    STENCIL_PREC_BF16X3 = 1,  /* folded 2D box on tcgen05: BF16 hi/lo split, 3 products,
+                                 FP32 accumulation in tensor memory                        */
+    STENCIL_PREC_BF16X1 = 2   /* as BF16X3 with the hi*hi product only (error study)      */
+} stencil_precision_t;
+
+/*
+ * Creates a plan for one grid and one base stencil (Section 1).
+ *   out_plan  receives the plan; the caller destroys it with stencil_plan_destroy.
+ *   ndim      1, 2 or 3.
+ *   shape     ndim extents, C order (shape[0] slowest); each >= 2*radius+1.
+ *   radius    r >= 1; r <= 4 (CUDA-core sweeps take folded radius m*r <= 16).
+ *   coeffs    (2r+1)^ndim doubles as described above; copied, not retained.
+ *   dtype     STENCIL_F32 for 1D/2D/3D; STENCIL_F64 for 1D only.
+ * The plan binds the CUDA device current at the call.  It computes the FP64
+ * folded weights on that device on demand (Section 3.2) and owns all scratch
+ * memory, which it allocates on first use.
+ * Errors: INVALID_ARG for a bad argument, UNSUPPORTED for F64 in 2D/3D,
+ * OOM / CUDA on allocation or device failures.
+ */
+stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t *shape,
+                              int radius, const double *coeffs, stencil_dtype_t dtype);
+
+/*
+ * Sets a tuning option (all optional).  Keys:
+ *   "precision"     stencil_precision_t; BF16 modes apply to 2D box stencils with m > 1.
+ *   "block_b"       temporal-blocking depth: folded sweeps per memory round trip
+ *                   (0 = automatic).
+ *   "tile_y"        rows per CTA tile of the 2D CUDA-core sweep (0 = automatic).
+ *   "tc_tile_n"     output columns per tensor-core tile: 32, 64 or 128.
+ *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
+ *   "wait_limit_ms" bound of every device-side wait (default 2000).
+ *   "autotune"      1 = time candidates when stencil_run gets fold_m = 0 (default 1).
+ * Errors: INVALID_ARG for an unknown key or an out-of-range value.
+ */
+stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, int64_t value);
+
+/*
+ * Reads a plan property.  Keys: "last_m", "last_b", "last_engine" (0 CUDA core,
+ * 1 tensor core), "launches" (kernels the plan has launched so far),
+ * "scratch_bytes" (device bytes the plan owns).
+ */
+stencil_status_t stencil_plan_get(stencil_plan_t plan, const char *key, int64_t *value);
+
+/*
+ * Advances `in` by T steps into `out` (Section 1 time loop; Section 3 folding).
+ *   in, out   prod(shape) elements of the plan's dtype.  Either both device
+ *             pointers or both host pointers (pageable or pinned).  With host
+ *             pointers the call copies in and out through plan-owned device
+ *             buffers and returns after the result is in `out`.  in == out is
+ *             allowed.  `in` is only read.  The caller keeps ownership.
+ *   T         time steps, >= 0 (T = 0 copies).
+ *   fold_m    1 = plain sweeps; m > 1 = floor(T/m) folded sweeps of the m-fold
+ *             convolution power plus T mod m plain steps; 0 = let the
+ *             autotuner choose m (and the blocking depth), cached per
+ *             (ndim, shape, radius, coefficients, dtype, GPU).
+ *   stream    the stream all work is ordered on.  With device pointers the
+ *             call is asynchronous.
+ * Errors: INVALID_ARG (null pointers, T < 0, fold_m < 0, folded radius wider
+ * than the grid), UNSUPPORTED (folding a stencil or precision this build has
+ * no kernel for), CUDA on a failed launch.
+ */
+stencil_status_t stencil_run(stencil_plan_t plan, const void *in, void *out, int64_t T,
+                             int fold_m, stencil_stream_t stream);
+
+/*
+ * Advances n independent grids in one persistent launch fed by a device work
+ * queue (a CUDA graph is captured once per set of plans and replayed).
+ *   plans     n plans, each 2D FP32, created on the current device.
+ *   in, out   n device pointers each (dense grids of the matching plan).
+ *   T         n step counts (>= 0).
+ *   fold_m    n fold factors (1 plain, > 1 folded, 0 automatic) or NULL for 0.
+ * Grids must not alias one another.  Errors as for stencil_run; a timed-out
+ * dependency wait is reported by stencil_sync on plans[0].
+ */
+stencil_status_t stencil_run_batched(int n, const stencil_plan_t *plans,
+                                     const void *const *in, void *const *out,
+                                     const int64_t *T, const int *fold_m,
+                                     stencil_stream_t stream);
+
+/*
+ * Waits for `stream` and returns the plan's device status (TIMEOUT or
+ * DEVICE_CHECK if a kernel recorded one since the last sync), then clears it.
+ */
+stencil_status_t stencil_sync(stencil_plan_t plan, stencil_stream_t stream);
+
+/*
+ * Copies the FP64 folded weights c^(m) (Section 3.2) the plan computed on the
+ * GPU into host_out, which holds n >= (2*m*r+1)^ndim doubles (dense, centred).
+ * Synchronous.  Errors: INVALID_ARG for m < 1 or n too small.
+ */
+stencil_status_t stencil_folded_coeffs(stencil_plan_t plan, int m, double *host_out, size_t n);
+
+/*
+ * Relative L2 error on the GPU, accumulated in FP64:
+ *   host_out[0] = ||y - ref|| / ||ref||,
+ *   host_out[1] = the same after removing each array's mean.
+ *   y         n device elements of type ydtype; ref: n device doubles.
+ * Synchronises `stream`.  Uses temporary device memory from the stream-ordered
+ * allocator.  Errors: INVALID_ARG for null pointers or n < 1.
+ */
+stencil_status_t stencil_rel_l2(const void *y, stencil_dtype_t ydtype, const double *ref,
+                                int64_t n, double *host_out, stencil_stream_t stream);
+
+/*
+ * Host-only planner counts of the scalar profitability analysis (Section 3.2,
+ * Eq. ce, Eq. uce, Eq. pi) for folding m steps of the given stencil:
+ *   out[0] = |C(E)|  : instructions of the naive m-step expression, i.e.
+ *            |S| * sum_{s<m} |support(c^(s))| (each intermediate point is a
+ *            |S|-way weighted sum);
+ *   out[1] = |C(E_lambda)| : taps of the folded stencil, |support(c^(m))|.
+ * The profitable index is out[0] / out[1].  Needs no GPU.
+ */
+stencil_status_t stencil_fold_cost(int ndim, int radius, const double *coeffs, int m,
+                                   int64_t *out);
+
+/* Frees the plan and everything it owns.  Waits for the plan's work first. */
+void stencil_plan_destroy(stencil_plan_t plan);
+
+/* Static name of a status code. */
+const char *stencil_status_string(stencil_status_t status);
+
+/* Detail of the last error on the calling thread ("" if none). */
+const char *stencil_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_GB300_H */

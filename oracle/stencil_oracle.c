@@ -18,6 +18,7 @@
  *  - coefficient layout: dense (2r+1)^ndim array, axis order (z, y, x), each
  *    axis indexed by offset + r; a star stencil has zeros off the axes.
  * Arithmetic is double throughout; no folding, blocking or reordering.
+ * Taps whose weight is zero (the off-axis taps of a star) are skipped.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -97,7 +98,7 @@ int oracle_stencil_run(int ndim, const int64_t *shape, int radius,
                             const int64_t row = (zz * ny + ty[y + dy]) * nx;
                             const double *c = coeffs + ((int64_t)dz * wy + dy) * wx;
                             for (int dx = 0; dx < wx; ++dx)
-                                s += c[dx] * a[row + tx[x + dx]];
+                                if (c[dx] != 0.0) s += c[dx] * a[row + tx[x + dx]];
                         }
                     }
                     b[(z * ny + y) * nx + x] = s;

@@ -1,0 +1,148 @@
+// Host-side declarations shared by the library's translation units: device
+// grid layouts, kernel argument blocks and launcher entry points.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace sg {
+
+__host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int round_up(int a, int b) { return ceil_div(a, b) * b; }
+
+// Ghost width allocated on every side of a padded 2D/3D grid.  Sweeps read
+// their halo from these ghost cells instead of wrapping indices, so every
+// tile (interior or boundary) is one rectangular TMA box.
+constexpr int kGhost = 16;
+
+// Largest folded radius R = m*r of a CUDA-core 2D/3D sweep kernel.
+constexpr int kMaxR2D = 8;
+constexpr int kMaxTaps2D = (2 * kMaxR2D + 1) * (2 * kMaxR2D + 1);
+constexpr int kMaxR3D = 4;
+constexpr int kMaxTaps3D = (2 * kMaxR3D + 1) * (2 * kMaxR3D + 1) * (2 * kMaxR3D + 1);
+constexpr int kMaxR1D = 16;
+
+// Tap patterns a kernel is specialised for.  A star of base radius rb folded
+// m times keeps tap (a, b[, c]) iff sum ceil(|offset_i| / rb) <= m; a box
+// keeps every tap.
+enum Pattern : int { PAT_STAR = 0, PAT_BOX = 1 };
+
+// FP32 grid in device memory surrounded by kGhost ghost cells per side.
+// Interior point (x, y, z) lives at origin[z*pz + y*py + x].
+struct Padded {
+    float *alloc = nullptr;
+    float *origin = nullptr;
+    int ndim = 0;
+    int nx = 1, ny = 1, nz = 1;
+    int64_t py = 0, pz = 0;
+    int gx = 0, gy = 0, gz = 0;
+    size_t elems = 0;
+};
+
+// ---- 2D CUDA-core sweep (plain, folded, temporally blocked) ---------------
+constexpr int kTileX2D = 128;   // output columns per CTA tile
+constexpr int kThreads2D = 256;
+
+struct Sweep2DArgs {
+    int nx, ny;
+    int tiles_x, ntiles;
+    int tile_y;        // output rows per CTA tile
+    int b;             // folded sweeps fused in this pass
+    int halo;          // H = b * R rows/columns of halo
+    int halo_x;        // H rounded up to a multiple of 4 (16-byte TMA column alignment)
+    int map_x0, map_y0;  // tensor-map coordinates of the interior origin
+    int buf_floats;    // floats between consecutive shared-memory buffers
+    float *dst;        // destination interior origin
+    int64_t dst_py;    // destination row stride (elements)
+    int dst_gw;        // ghost band of the destination to refresh (0 = dense output)
+    int dst_vec4;      // destination rows allow 16-byte stores
+    int *status;
+    unsigned long long wait_ns;
+    float c[kMaxTaps2D];  // folded weights, (2R+1)^2, row-major (dy, dx)
+};
+
+bool sweep2d_supported(int rb, int m, int pattern);
+size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats);
+int sweep2d_ctas_per_sm(int rb, int m, int pattern, size_t smem);
+cudaError_t launch_sweep2d(int rb, int m, int pattern, const CUtensorMap &map,
+                           const Sweep2DArgs &a, int grid, size_t smem, cudaStream_t s);
+
+// ---- 3D CUDA-core sweep (streaming along z) -------------------------------
+struct Sweep3DArgs {
+    int nx, ny, nz;
+    int tiles_x, tiles_y, ntiles_xy, zchunks, ntiles;
+    int tile_y, zchunk;
+    int halo_x;                 // R rounded up to a multiple of 4
+    int map_x0, map_y0, map_z0;
+    int buf_floats;             // floats per shared-memory plane slot
+    float *dst;
+    int64_t dst_py, dst_pz;
+    int dst_gw;
+    int dst_vec4;
+    int *status;
+    unsigned long long wait_ns;
+    float c[kMaxTaps3D];
+};
+bool sweep3d_supported(int rb, int m, int pattern);
+size_t sweep3d_smem_bytes(int tile_y, int R, int *buf_floats);
+cudaError_t launch_sweep3d(int rb, int m, int pattern, const CUtensorMap &map,
+                           const Sweep3DArgs &a, int grid, size_t smem, cudaStream_t s);
+int sweep3d_ctas_per_sm(int rb, int m, int pattern, size_t smem);
+
+// ---- 1D sweep (FP32/FP64, temporally blocked in shared memory) ------------
+struct Sweep1DArgs {
+    const void *src;
+    void *dst;
+    long long n;
+    int tile;       // outputs per CTA
+    int b;          // steps fused per launch
+    double c[2 * kMaxR1D + 1];
+};
+bool sweep1d_supported(int R, bool f64);
+cudaError_t launch_sweep1d(int R, bool f64, const Sweep1DArgs &a, cudaStream_t s);
+
+// ---- layout conversion, coefficient folding, error reduction --------------
+cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_t s);
+cudaError_t launch_export(const Padded &P, float *dst, cudaStream_t s);
+// c^(m) by m-1 convolutions with c (FP64 on the GPU); work holds 2*(2mr+1)^ndim doubles.
+cudaError_t launch_fold_power(int ndim, int r, int m, const double *d_c, double *d_out,
+                              double *d_work, cudaStream_t s);
+// Accumulates sum (y-r)^2, sum r^2, sum y, sum r into acc[4] (zeroed by the caller).
+cudaError_t launch_rel_l2(const void *y, bool y_f64, const double *ref, long long n,
+                          double *acc, cudaStream_t s);
+
+// ---- tcgen05 folded 2D box sweep (BF16 hi/lo split) -----------------------
+struct TC2DArgs {
+    int nx, ny;
+    int tiles_x, tiles_y, ntiles;
+    int R;                 // folded radius
+    int tile_n;            // output columns per tile (N of the MMA)
+    int kpad;              // K = tile_n + 2R rounded up to 16
+    int terms;             // 3 = hi*hi + lo*hi + hi*lo, 1 = hi*hi
+    int map_x0, map_y0;
+    float mu;              // value subtracted before the BF16 split and added back
+    float sum_c;           // sum of the folded weights
+    const uint16_t *panels;  // Toeplitz panels, see tc2d_panel_layout
+    float *dst;
+    int64_t dst_py;
+    int dst_gw;
+    int *status;
+    unsigned long long wait_ns;
+};
+bool tc2d_supported(int R, int tile_n);
+size_t tc2d_smem_bytes(int R, int tile_n, int *layout_words);
+size_t tc2d_panel_elems(int R, int tile_n);
+void tc2d_build_panels(const double *cm, int R, int tile_n, uint16_t *host_out);
+cudaError_t launch_tc2d(const CUtensorMap &map, const TC2DArgs &a, int grid, size_t smem,
+                        cudaStream_t s);
+cudaError_t launch_grid_mean(const float *origin, int nx, int ny, int64_t py, double *acc,
+                             cudaStream_t s);
+
+// ---- tensor maps ------------------------------------------------------------
+// Encodes a tiled FP32 tensor map over a padded grid's whole allocation.
+// box has P.ndim entries (x first).  Returns false if the driver refuses it.
+bool encode_padded_map(CUtensorMap *map, const Padded &P, const int *box);
+
+}  // namespace sg

@@ -1,0 +1,34 @@
+// Entry points whose kernels are not built yet report STENCIL_ERR_UNSUPPORTED.
+#include "plan.h"
+
+namespace sg {
+
+stencil_status_t run3d(stencil_plan_s *, const float *, float *, int64_t, int, cudaStream_t)
+{
+    set_error("3D sweeps are not built yet");
+    return STENCIL_ERR_UNSUPPORTED;
+}
+
+stencil_status_t run2d_tc(stencil_plan_s *, const float *, float *, int64_t, int, cudaStream_t)
+{
+    set_error("tensor-core sweeps are not built yet");
+    return STENCIL_ERR_UNSUPPORTED;
+}
+
+stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t)
+{
+    p->tuned_m = 1;
+    p->tuned_b = 1;
+    p->tuned_ty = 0;
+    return STENCIL_OK;
+}
+
+}  // namespace sg
+
+extern "C" stencil_status_t stencil_run_batched(int, const stencil_plan_t *, const void *const *,
+                                                void *const *, const int64_t *, const int *,
+                                                stencil_stream_t)
+{
+    sg::set_error("batched runs are not built yet");
+    return STENCIL_ERR_UNSUPPORTED;
+}

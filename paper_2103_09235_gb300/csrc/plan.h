@@ -1,0 +1,72 @@
+// The plan object behind the opaque stencil_plan_t, shared by the host
+// translation units of the library.
+#pragma once
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/stencil.h"
+#include "internal.h"
+
+struct stencil_plan_s {
+    int device = 0;
+    int ndim = 0;
+    int64_t shape[3] = {1, 1, 1};  // C order, as given
+    int nx = 1, ny = 1, nz = 1;    // x fastest
+    int r = 1;
+    stencil_dtype_t dtype = STENCIL_F32;
+    std::vector<double> coeffs;  // (2r+1)^ndim, axis order (z, y, x)
+    int pattern = sg::PAT_BOX;
+
+    // options
+    int precision = STENCIL_PREC_FP32;
+    int block_b = 0;
+    int tile_y = 0;
+    int tc_tile_n = 64;
+    int tc_center = 1;
+    int autotune = 1;
+    long long wait_ms = 2000;
+
+    // FP64 folded weights computed on the GPU, by m
+    std::map<int, std::vector<double>> folded;
+
+    // device state
+    int *d_status = nullptr;
+    sg::Padded A, B;                          // 2D / 3D working grids
+    void *d1a = nullptr, *d1b = nullptr;      // 1D working grids
+    void *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
+    double *d_acc = nullptr;                  // small FP64 reduction buffer
+    std::map<int, uint16_t *> panels;         // tensor-core Toeplitz panels by (m, tile_n) key
+    std::map<std::tuple<const void *, int, int, int>, CUtensorMap> maps;
+    size_t scratch_bytes = 0;
+
+    // bookkeeping
+    long long launches = 0;
+    int last_m = 0, last_b = 0, last_engine = 0;
+    // autotuner choice for fold_m = 0: m, b, tile_y, engine (m = 0: not tuned yet)
+    int tuned_m = 0, tuned_b = 0, tuned_ty = 0, tuned_engine = 0;
+};
+
+namespace sg {
+
+// Thread-local error detail.
+void set_error(const char *fmt, ...);
+stencil_status_t cuda_fail(cudaError_t e, const char *what);
+
+// FP64 folded weights c^(m) of the plan, computed on the GPU once per m.
+stencil_status_t plan_folded(stencil_plan_s *p, int m, const std::vector<double> **out);
+stencil_status_t ensure_padded(stencil_plan_s *p);
+const CUtensorMap *plan_map(stencil_plan_s *p, const Padded &P, const int *box);
+
+// Per-dimension drivers of stencil_run on device pointers.
+stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, int m,
+                       cudaStream_t s);
+stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
+                       cudaStream_t s);
+stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
+                       cudaStream_t s);
+stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s);
+
+}  // namespace sg

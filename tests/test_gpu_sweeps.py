@@ -1,0 +1,212 @@
+"""GPU parity of the CUDA-core sweeps against the FP64 oracle.
+
+Every case draws seeded inputs, runs the library through the C ABI and
+compares element by element with the oracle's plain time loop.  Tolerance:
+relative L2 <= 1e-5 (FP32), <= 1e-12 (FP64), and max abs error <= 1e-5 (FP32,
+values in [0, 1)).  Shapes cover several 128 x 64 tiles with ragged tails,
+grids narrower than one tile, and T values that leave a remainder after
+folding.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2103_09235_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod):
+    import torch
+    from paper_2103_09235_gb300 import build, binding
+    build.build()
+    assert torch.cuda.is_available()
+    torch.cuda.init()
+    return torch, binding, oracle_mod
+
+
+def gpu_run(env, shape, c, x, T, m, dtype="f32", **opts):
+    torch, binding, _ = env
+    plan = binding.Plan(shape, c, dtype)
+    for k, v in opts.items():
+        plan.set_option(k, v)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, T, fold_m=m)
+    plan.sync()
+    y = yd.cpu().numpy()
+    info = {"m": plan.get("last_m"), "b": plan.get("last_b"), "launches": plan.get("launches")}
+    plan.close()
+    return y, info
+
+
+def check(y, ref, tol=TOL_F32, abs_tol=1e-5):
+    import oracle
+    err = oracle.rel_l2(y, ref)
+    assert err <= tol, err
+    if abs_tol is not None:
+        assert np.max(np.abs(y.astype(np.float64) - ref)) <= abs_tol
+    return err
+
+
+CASES_2D = [
+    # shape, kind, r, T, m, b
+    ((64, 128), "star", 1, 5, 1, 1),
+    ((300, 520), "star", 1, 17, 1, 1),
+    ((300, 520), "star", 1, 17, 1, 4),
+    ((37, 45), "star", 1, 9, 1, 2),
+    ((300, 520), "star", 1, 21, 2, 1),
+    ((300, 520), "star", 1, 21, 2, 4),
+    ((129, 257), "star", 1, 30, 3, 2),
+    ((300, 520), "star", 1, 41, 4, 2),
+    ((300, 520), "star", 1, 41, 4, 0),
+    ((300, 520), "box", 1, 13, 1, 1),
+    ((300, 520), "box", 1, 13, 1, 3),
+    ((129, 257), "box", 1, 22, 2, 2),
+    ((300, 520), "box", 1, 25, 4, 1),
+    ((300, 520), "box", 1, 25, 4, 2),
+    ((41, 77), "box", 1, 11, 3, 1),
+    ((200, 300), "star", 2, 9, 1, 1),
+    ((200, 300), "star", 2, 9, 2, 2),
+    ((200, 300), "box", 2, 7, 1, 2),
+    ((200, 300), "box", 2, 7, 2, 1),
+    ((90, 140), "box", 3, 5, 1, 1),
+    ((90, 140), "box", 4, 5, 1, 2),
+    ((130, 17), "star", 1, 12, 2, 1),
+]
+
+
+@pytest.mark.parametrize("shape,kind,r,T,m,b", CASES_2D)
+def test_sweep2d_parity(env, shape, kind, r, T, m, b):
+    _, _, oracle = env
+    c = synth.dyadic_coeffs(1000 + r, 2, r, kind)
+    x = synth.grid(2000 + T, shape, np.float32)
+    opts = {"block_b": b} if b else {}
+    y, info = gpu_run(env, shape, c, x, T, m, **opts)
+    ref = oracle.run(x.astype(np.float64), c, T)
+    check(y, ref)
+    assert info["m"] == m
+
+
+@pytest.mark.parametrize("tile_y", [16, 32, 48, 96])
+def test_sweep2d_tile_shapes(env, tile_y):
+    _, _, oracle = env
+    shape = (250, 300)
+    c = synth.dyadic_coeffs(7, 2, 1, "star")
+    x = synth.grid(8, shape, np.float32)
+    y, _ = gpu_run(env, shape, c, x, 18, 2, block_b=3, tile_y=tile_y)
+    check(y, oracle.run(x.astype(np.float64), c, 18))
+
+
+CASES_1D = [
+    (1000, 1, 1, "f32"), (4097, 37, 1, "f32"), (65539, 100, 1, "f32"), (65539, 100, 2, "f32"),
+    (65539, 99, 3, "f32"), (4097, 37, 1, "f64"), (65539, 100, 1, "f64"), (65539, 101, 4, "f64"),
+    (9, 50, 1, "f64"), (300, 64, 1, "f32"),
+]
+
+
+@pytest.mark.parametrize("n,T,m,dt", CASES_1D)
+def test_sweep1d_parity(env, n, T, m, dt):
+    _, _, oracle = env
+    c = synth.heat1d_coeffs() if n % 2 else synth.dyadic_coeffs(5, 1, 1, "box")
+    npdt = np.float64 if dt == "f64" else np.float32
+    x = synth.grid(3000 + n, (n,), npdt)
+    y, _ = gpu_run(env, (n,), c, x, T, m, dt)
+    ref = oracle.run(x.astype(np.float64), c, T)
+    if dt == "f64":
+        check(y, ref, tol=1e-12, abs_tol=1e-12)
+    else:
+        check(y, ref)
+
+
+def test_sweep1d_radius2(env):
+    _, _, oracle = env
+    c = synth.dyadic_coeffs(9, 1, 2, "box")
+    x = synth.grid(10, (5003,), np.float32)
+    y, _ = gpu_run(env, (5003,), c, x, 40, 2)
+    check(y, oracle.run(x.astype(np.float64), c, 40))
+
+
+def test_host_pointers(env):
+    """Host numpy arrays in and out: the call copies through plan-owned buffers."""
+    torch, binding, oracle = env
+    shape = (100, 140)
+    c = synth.dyadic_coeffs(11, 2, 1, "box")
+    x = synth.grid(12, shape, np.float32)
+    y = np.empty_like(x)
+    plan = binding.Plan(shape, c)
+    plan.run(x, y, 10, fold_m=2)
+    check(y, oracle.run(x.astype(np.float64), c, 10))
+    x1 = synth.grid(13, (777,), np.float64)
+    y1 = np.empty_like(x1)
+    p1 = binding.Plan((777,), synth.heat1d_coeffs(), "f64")
+    p1.run(x1, y1, 20)
+    check(y1, oracle.run(x1, synth.heat1d_coeffs(), 20), tol=1e-12, abs_tol=1e-12)
+
+
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_in_place_and_zero_steps(env, ndim):
+    torch, binding, oracle = env
+    shape = (5000,) if ndim == 1 else (96, 160)
+    kind = "box"
+    c = synth.dyadic_coeffs(14, ndim, 1, kind)
+    x = synth.grid(15, shape, np.float32)
+    plan = binding.Plan(shape, c)
+    xd = torch.from_numpy(x).cuda()
+    plan.run(xd, xd, 7, fold_m=1)
+    plan.sync()
+    check(xd.cpu().numpy(), oracle.run(x.astype(np.float64), c, 7))
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, 0)
+    plan.sync()
+    assert torch.equal(xd, yd)
+
+
+def test_split_run_equals_whole(env):
+    """run(T1) then run(T2) matches run(T1 + T2): resuming is calling again."""
+    torch, binding, oracle = env
+    shape = (140, 200)
+    c = synth.dyadic_coeffs(16, 2, 1, "star")
+    x = synth.grid(17, shape, np.float32)
+    plan = binding.Plan(shape, c)
+    xd = torch.from_numpy(x).cuda()
+    y1, y2 = torch.empty_like(xd), torch.empty_like(xd)
+    plan.run(xd, y1, 12, fold_m=4)
+    plan.run(y1, y2, 9, fold_m=2)
+    plan.sync()
+    check(y2.cpu().numpy(), oracle.run(x.astype(np.float64), c, 21))
+
+
+@pytest.mark.parametrize("ndim,r,kind,m", [(1, 1, "box", 5), (2, 1, "star", 4), (2, 1, "box", 4),
+                                           (2, 1, "box", 8), (2, 2, "star", 3), (3, 1, "star", 2),
+                                           (3, 1, "box", 2)])
+def test_folded_coeffs_fp64_on_gpu(env, ndim, r, kind, m):
+    """The plan's FP64 folded weights (computed by a GPU kernel) equal the oracle's."""
+    torch, binding, oracle = env
+    c = synth.dyadic_coeffs(18 + m, ndim, r, kind)
+    shape = (64,) * ndim
+    plan = binding.Plan(shape, c)
+    got = plan.folded_coeffs(m)
+    ref = oracle.fold_coeffs(c, m)
+    assert got.shape == ref.shape
+    assert np.max(np.abs(got - ref)) < 1e-15
+
+
+def test_rel_l2_on_gpu(env):
+    torch, binding, oracle = env
+    ref = synth.grid(19, (1000, 37), np.float64)
+    y = (ref + 1e-3 * synth.grid(20, (1000, 37), np.float64)).astype(np.float32)
+    got = binding.rel_l2(torch.from_numpy(y).cuda(), torch.from_numpy(ref).cuda())
+    assert abs(got[0] - oracle.rel_l2(y, ref)) < 1e-12
+    assert abs(got[1] - oracle.rel_l2_zero_mean(y, ref)) < 1e-9
+
+
+def test_bad_fold_rejected(env):
+    torch, binding, _ = env
+    plan = binding.Plan((20, 20), synth.dyadic_coeffs(1, 2, 1, "star"))
+    x = torch.zeros((20, 20), device="cuda")
+    assert plan.run_status(x, x, 10, 10) == 1   # folded width 21 > 20
+    assert plan.run_status(x, x, -1, 1) == 1
