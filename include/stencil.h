@@ -171,6 +171,33 @@ stencil_status_t stencil_rel_l2(const void *y, stencil_dtype_t ydtype, const dou
 stencil_status_t stencil_fold_cost(int ndim, int radius, const double *coeffs, int m,
                                    int64_t *out);
 
+/*
+ * T plain steps of a 1D periodic stencil without allocating any memory.
+ * The paper has no counterpart of this call: it serves callers that cannot
+ * call cudaMalloc -- code running while a CUDA graph is captured in a mode
+ * that forbids allocation, code inside a framework whose allocator owns all
+ * device memory, and deployments that must not touch the allocator after
+ * start-up.  stencil_run needs a plan, which allocates; this call does not.
+ *   in, out   n device elements of `dtype` (F32 or F64); in == out allowed.
+ *   n         points, 2*radius+1 <= n and n * sizeof(dtype) <= 16 MiB.
+ *   radius    1, 2, 3, 4, 6, 8, 12 or 16.
+ *   coeffs    2*radius+1 host doubles (offsets -radius..radius); copied.
+ *   T         steps, >= 0.
+ * The intermediate grid lives in one fixed 16 MiB device array inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the array and each call fully
+ * overwrites what it reads back, so nothing needs clearing, but calls whose
+ * work overlaps on the GPU (other streams, other threads) race on it.
+ * Asynchronous on `stream`.  Allocates nothing: no cudaMalloc, no cudaFree.
+ * Errors: INVALID_ARG for bad arguments or a grid above 16 MiB,
+ * UNSUPPORTED for another radius, CUDA on a failed launch.
+ */
+stencil_status_t stencil_run_1d_noalloc(const void *in, void *out, int64_t n, int radius,
+                                        const double *coeffs, int64_t T, stencil_dtype_t dtype,
+                                        stencil_stream_t stream);
+
 /* Frees the plan and everything it owns.  Waits for the plan's work first. */
 void stencil_plan_destroy(stencil_plan_t plan);
 

@@ -31,6 +31,7 @@ EXPORTS = [
     "stencil_plan", "stencil_plan_set_option", "stencil_plan_get", "stencil_run",
     "stencil_run_batched", "stencil_sync", "stencil_folded_coeffs", "stencil_rel_l2",
     "stencil_fold_cost", "stencil_plan_destroy", "stencil_status_string", "stencil_last_error",
+    "stencil_run_1d_noalloc",
 ]
 
 
@@ -68,6 +69,9 @@ def lib():
         L.stencil_rel_l2.argtypes = [_vp, _c.c_int, _vp, _i64, ctypes.POINTER(_c.c_double), _vp]
         L.stencil_fold_cost.argtypes = [_c.c_int, _c.c_int, ctypes.POINTER(_c.c_double), _c.c_int,
                                         ctypes.POINTER(_i64)]
+        L.stencil_run_1d_noalloc.argtypes = [_vp, _vp, _i64, _c.c_int, ctypes.POINTER(_c.c_double),
+                                             _i64, _c.c_int, _vp]
+        L.stencil_run_1d_noalloc.restype = _c.c_int
         L.stencil_plan_destroy.argtypes = [_vp]
         L.stencil_plan_destroy.restype = None
         L.stencil_status_string.argtypes = [_c.c_int]
@@ -208,6 +212,18 @@ def fold_cost(coeffs, m: int):
     _check(lib().stencil_fold_cost(c.ndim, r, c.ctypes.data_as(ctypes.POINTER(_c.c_double)), int(m), out),
            "stencil_fold_cost")
     return int(out[0]), int(out[1])
+
+
+def run_1d_noalloc(x, y, coeffs, T: int, stream=None):
+    """y <- T plain 1D steps of x without any allocation (device tensors)."""
+    import torch
+    c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+    dt = F64 if x.dtype == torch.float64 else F32
+    _check(lib().stencil_run_1d_noalloc(_ptr(x), _ptr(y), x.numel(), (c.size - 1) // 2,
+                                        c.ctypes.data_as(ctypes.POINTER(_c.c_double)), int(T), dt,
+                                        _stream(stream)),
+           "stencil_run_1d_noalloc")
+    return y
 
 
 def status_string(code: int) -> str:
