@@ -88,6 +88,12 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
  *   "wait_limit_ms" bound of every device-side wait (default 2000).
  *   "autotune"      1 = time candidates when stencil_run gets fold_m = 0 (default 1).
+ *   "graph"         1 = capture each distinct run (pointers, T, m, options) once into
+ *                   a CUDA graph and replay it (default 1); 0 = launch kernel by kernel.
+ *                   A run on a stream that is itself being captured is never graphed.
+ *   "fault_withhold_copy"  test hook: 1 = the 2D CUDA-core sweep never issues its
+ *                   first tile copy, so its bounded wait runs out and stencil_sync
+ *                   reports STENCIL_ERR_TIMEOUT (no GPU fault; the context stays usable).
  * Errors: INVALID_ARG for an unknown key or an out-of-range value.
  */
 stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, int64_t value);

@@ -60,6 +60,7 @@ struct Sweep2DArgs {
     int dst_vec4;      // destination rows allow 16-byte stores
     int *status;
     unsigned long long wait_ns;
+    int fault_withhold_copy;  // test hook: never issue the first tile's copy
     float c[kMaxTaps2D];  // folded weights, (2R+1)^2, row-major (dy, dx)
 };
 

@@ -63,33 +63,98 @@ __device__ __forceinline__ void store_point(float *dst, int64_t py, int nx, int 
     }
 }
 
+template <int RB, int M, int PAT>
+struct Strip {
+    using TP = Taps<RB, M, PAT>;
+    static constexpr int R = TP::R, W = TP::W, RP = TP::RP;
+    static constexpr int NSEG = 4 + 2 * RP;
+    static constexpr int NNZ = [] {
+        int n = 0;
+        for (int a = -R; a <= R; ++a)
+            for (int b = -R; b <= R; ++b) n += TP::nz(a, b) ? 1 : 0;
+        return n;
+    }();
+    // rows of the steady loop unrolled together: a full turn of the window
+    // when the row's multiply-adds are few, so the window shift is renamed away
+    static constexpr int UNR = NNZ * 4 <= 200 ? W : 1;
+
+    __device__ __forceinline__ static void load(const float *rowp, float (&seg)[NSEG])
+    {
+        const float4 *rp = reinterpret_cast<const float4 *>(rowp);
+#pragma unroll
+        for (int q = 0; q < NSEG / 4; ++q) {
+            const float4 t = rp[q];
+            seg[4 * q + 0] = t.x;
+            seg[4 * q + 1] = t.y;
+            seg[4 * q + 2] = t.z;
+            seg[4 * q + 3] = t.w;
+        }
+    }
+
+    // input row into window slot i (output row j - R + i, row offset a = R - i)
+    __device__ __forceinline__ static void slot(float (&acc)[W][4], const float (&seg)[NSEG],
+                                                const Sweep2DArgs &a, int i)
+    {
+        const int aa = R - i;
+#pragma unroll
+        for (int bb = -R; bb <= R; ++bb) {
+            if (TP::nz(aa, bb)) {
+                const float w = a.c[(aa + R) * W + (bb + R)];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[i][v] = fmaf(w, seg[v + bb + RP], acc[i][v]);
+            }
+        }
+    }
+
+    __device__ __forceinline__ static void shift(float (&acc)[W][4])
+    {
+#pragma unroll
+        for (int i = 0; i < W - 1; ++i)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
+    }
+};
+
+__device__ __noinline__ void store_ghosts4(const Sweep2DArgs &a, int X, int Y, float v0, float v1,
+                                           float v2, float v3)
+{
+    const float v[4] = {v0, v1, v2, v3};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (X + k < a.nx) store_point(a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, X + k, Y, v[k]);
+}
+
 // One sweep over output rows [r0, r1) and 4-column strips [k0, k1) of a
 // shared-memory buffer S (row pitch SP).  FINAL writes to global memory;
 // otherwise the outputs go to the same coordinates of buffer D.
+//
+// A strip of rows [ya, yb) reads input rows ya-R .. yb+R-1.  The first 2R
+// rows only feed window slots whose output row is >= ya and the last 2R only
+// slots whose output row is < yb, so every output gets exactly its taps.
 template <int RB, int M, int PAT, bool FINAL>
 __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float *__restrict__ D,
                                              int SP, int r0, int r1, int k0, int k1,
                                              const Sweep2DArgs &a, int gx0, int gy0)
 {
-    using TP = Taps<RB, M, PAT>;
-    constexpr int R = TP::R, W = TP::W, RP = TP::RP;
-    constexpr int NSEG = 4 + 2 * RP;
+    using ST = Strip<RB, M, PAT>;
+    constexpr int R = ST::R, W = ST::W, RP = ST::RP, NSEG = ST::NSEG;
     const int nsx = k1 - k0;
     const int nr = r1 - r0;
     if (nsx <= 0 || nr <= 0) return;
+    // row groups: as many as the threads allow, each at least 2R rows tall
     int G = NT / nsx;
-    if (G < 1) G = 1;
-    if (G > nr) G = nr;
-    const int RY = (nr + G - 1) / G;
+    G = max(1, min(G, nr / (2 * R)));
     const int items = nsx * G;
 
     for (int it = threadIdx.x; it < items; it += NT) {
         const int k = k0 + it % nsx;
         const int g = it / nsx;
-        const int ya = r0 + g * RY;
-        const int yb = min(r1, ya + RY);
-        if (ya >= yb) continue;
+        const int ya = r0 + (g * nr) / G;
+        const int yb = r0 + ((g + 1) * nr) / G;
         const int cx = 4 * k;
+        const float *col = S + cx - RP;
 
         float acc[W][4];
 #pragma unroll
@@ -97,74 +162,84 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
 
-        const float *col = S + cx - RP;
-#pragma unroll 1
-        for (int j = ya - R; j < yb + R; ++j) {
-            float seg[NSEG];
-            const float4 *rp = reinterpret_cast<const float4 *>(col + j * SP);
-#pragma unroll
-            for (int q = 0; q < NSEG / 4; ++q) {
-                const float4 t = rp[q];
-                seg[4 * q + 0] = t.x;
-                seg[4 * q + 1] = t.y;
-                seg[4 * q + 2] = t.z;
-                seg[4 * q + 3] = t.w;
-            }
-            // input row j feeds output row j - R + i with row offset a = R - i
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                const int aa = R - i;
-#pragma unroll
-                for (int bb = -R; bb <= R; ++bb) {
-                    if (TP::nz(aa, bb)) {
-                        const float w = a.c[(aa + R) * W + (bb + R)];
+        auto emit = [&](int y) {
+            if constexpr (FINAL) {
+                const int X = gx0 + cx, Y = gy0 + y;
+                if (Y < a.ny && X < a.nx) {
+                    float *row = a.dst + Y * a.dst_py;
+                    if (a.dst_vec4 && X + 3 < a.nx) {
+                        *reinterpret_cast<float4 *>(row + X) =
+                            make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                    } else {
 #pragma unroll
                         for (int v = 0; v < 4; ++v)
-                            acc[i][v] = fmaf(w, seg[v + bb + RP], acc[i][v]);
+                            if (X + v < a.nx) row[X + v] = acc[0][v];
                     }
+                    if (a.dst_gw > 0 && (X < a.dst_gw || X + 3 >= a.nx - a.dst_gw ||
+                                         Y < a.dst_gw || Y >= a.ny - a.dst_gw))
+                        store_ghosts4(a, X, Y, acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
                 }
+            } else {
+                *reinterpret_cast<float4 *>(D + y * SP + cx) =
+                    make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
             }
-            const int y = j - R;
-            if (y >= ya) {
-                if constexpr (FINAL) {
-                    const int X = gx0 + cx, Y = gy0 + y;
-                    if (Y < a.ny && X < a.nx) {
-                        float *row = a.dst + Y * a.dst_py;
-                        if (a.dst_vec4 && X + 3 < a.nx) {
-                            *reinterpret_cast<float4 *>(row + X) =
-                                make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
-                        } else {
+        };
+
+        int j = ya - R;
+        if (yb - ya >= 2 * R) {
+            // ramp-up: rows ya-R .. ya+R-1 feed only slots i >= 2R - u
 #pragma unroll
-                            for (int v = 0; v < 4; ++v)
-                                if (X + v < a.nx) row[X + v] = acc[0][v];
-                        }
-                        if (a.dst_gw > 0 &&
-                            (X < a.dst_gw || X + 3 >= a.nx - a.dst_gw || Y < a.dst_gw ||
-                             Y >= a.ny - a.dst_gw)) {
+            for (int u = 0; u < 2 * R; ++u, ++j) {
+                float seg[NSEG];
+                ST::load(col + j * SP, seg);
 #pragma unroll
-                            for (int v = 0; v < 4; ++v)
-                                if (X + v < a.nx)
-                                    store_point(a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, X + v, Y,
-                                                acc[0][v]);
-                        }
-                    }
-                } else {
-                    *reinterpret_cast<float4 *>(D + y * SP + cx) =
-                        make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
-                }
+                for (int i = 0; i < W; ++i)
+                    if (i >= 2 * R - u) ST::slot(acc, seg, a, i);
+                ST::shift(acc);
             }
+            // steady rows: every slot, one finished output row each
+            const int jm = yb - R;
+#pragma unroll ST::UNR
+            for (; j < jm; ++j) {
+                float seg[NSEG];
+                ST::load(col + j * SP, seg);
 #pragma unroll
-            for (int i = 0; i < W - 1; ++i)
+                for (int i = 0; i < W; ++i) ST::slot(acc, seg, a, i);
+                emit(j - R);
+                ST::shift(acc);
+            }
+            // ramp-down: the last 2R rows feed only slots i <= v
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
+            for (int v = 2 * R - 1; v >= 0; --v, ++j) {
+                float seg[NSEG];
+                ST::load(col + j * SP, seg);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
+                for (int i = 0; i < W; ++i)
+                    if (i <= v) ST::slot(acc, seg, a, i);
+                emit(j - R);
+                ST::shift(acc);
+            }
+        } else {
+            // short strip: plain window over all rows
+#pragma unroll 1
+            for (; j < yb + R; ++j) {
+                float seg[NSEG];
+                ST::load(col + j * SP, seg);
+#pragma unroll
+                for (int i = 0; i < W; ++i) ST::slot(acc, seg, a, i);
+                if (j - R >= ya) emit(j - R);
+                ST::shift(acc);
+            }
         }
     }
 }
 
+// Plain radius-1 sweeps are memory-bound: keep three CTAs per SM resident.
+template <int RB, int M>
+constexpr int min_blocks() { return RB * M == 1 ? 3 : 1; }
+
 template <int RB, int M, int PAT>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, min_blocks<RB, M>())
     k_sweep2d(const __grid_constant__ CUtensorMap map, const __grid_constant__ Sweep2DArgs a)
 {
     constexpr int R = RB * M;
@@ -194,7 +269,9 @@ __global__ void __launch_bounds__(NT, 1)
     };
 
     int tile = blockIdx.x;
-    if (tid == 0 && tile < a.ntiles) issue(tile, 0);
+    // (fault_withhold_copy is a test hook: the first copy is never issued, so
+    // the bounded wait below must run out and report a timeout)
+    if (tid == 0 && tile < a.ntiles && !a.fault_withhold_copy) issue(tile, 0);
 
     for (int i = 0; tile < a.ntiles; ++i, tile += gridDim.x) {
         const int nxt = tile + gridDim.x;
@@ -229,27 +306,39 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
+// Opt every instantiation into the largest dynamic shared memory once, so
+// launches need no attribute call.
+template <int RB, int M, int PAT>
+cudaError_t prepare_t()
+{
+    static cudaError_t once = [] {
+        int dev = 0, maxs = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return cudaFuncSetAttribute(k_sweep2d<RB, M, PAT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    }();
+    return once;
+}
+
 template <int RB, int M, int PAT>
 cudaError_t launch_t(const CUtensorMap &map, const Sweep2DArgs &a, int grid, size_t smem,
                      cudaStream_t s)
 {
-    auto kern = k_sweep2d<RB, M, PAT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = prepare_t<RB, M, PAT>();
     if (e != cudaSuccess) return e;
-    kern<<<grid, NT, smem, s>>>(map, a);
+    k_sweep2d<RB, M, PAT><<<grid, NT, smem, s>>>(map, a);
     return cudaGetLastError();
 }
 
 template <int RB, int M, int PAT>
 int occupancy_t(size_t smem)
 {
-    auto kern = k_sweep2d<RB, M, PAT>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem)) != cudaSuccess)
-        return 0;
+    if (prepare_t<RB, M, PAT>() != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, NT, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep2d<RB, M, PAT>, NT, smem) !=
+        cudaSuccess)
+        return 0;
     return n;
 }
 

@@ -28,6 +28,7 @@ struct stencil_plan_s {
     int tc_center = 1;
     int autotune = 1;
     long long wait_ms = 2000;
+    int fault_withhold_copy = 0;  // test hook, see stencil_plan_set_option
 
     // FP64 folded weights computed on the GPU, by m
     std::map<int, std::vector<double>> folded;
@@ -41,6 +42,23 @@ struct stencil_plan_s {
     std::map<int, uint16_t *> panels;         // tensor-core Toeplitz panels by (m, tile_n) key
     std::map<std::tuple<const void *, int, int, int>, CUtensorMap> maps;
     size_t scratch_bytes = 0;
+
+    // cached launch facts
+    int sm_count = 0, max_smem = 0;
+    struct PassCfg {
+        int ty, bf, grid;
+        size_t smem;
+    };
+    std::map<std::tuple<int, int, int>, PassCfg> pass_cfg;  // (m, b, tile_y option)
+
+    // executable graphs of whole runs, keyed by everything a run enqueues
+    struct GraphEnt {
+        cudaGraphExec_t exec;
+        int launches;
+    };
+    std::map<std::vector<int64_t>, GraphEnt> graphs;
+    cudaStream_t cap_stream = nullptr;
+    int use_graph = 1;
 
     // bookkeeping
     long long launches = 0;
@@ -68,5 +86,54 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
 stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
                        cudaStream_t s);
 stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s);
+
+void clear_graphs(stencil_plan_s *p);
+void ensure_device_facts(stencil_plan_s *p);
+
+// Runs enqueue(stream, &kernels) on stream s.  With graphs enabled and s not
+// itself being captured, the work is captured once per key on a private
+// stream into an executable graph, which is then replayed on s: a run of many
+// short passes costs one graph launch on the host.
+template <class F>
+stencil_status_t run_maybe_graph(stencil_plan_s *p, const std::vector<int64_t> &key,
+                                 cudaStream_t s, F enqueue)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;
+    }
+    if (!p->use_graph || cs != cudaStreamCaptureStatusNone) {
+        int n = 0;
+        stencil_status_t st = enqueue(s, &n);
+        p->launches += n;
+        return st;
+    }
+    auto it = p->graphs.find(key);
+    if (it == p->graphs.end()) {
+        cudaError_t e = cudaSuccess;
+        if (!p->cap_stream) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture begin");
+        int n = 0;
+        stencil_status_t st = enqueue(p->cap_stream, &n);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(p->cap_stream, &g);
+        if (st != STENCIL_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        it = p->graphs.emplace(key, stencil_plan_s::GraphEnt{ex, n}).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second.exec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    p->launches += it->second.launches;
+    return STENCIL_OK;
+}
 
 }  // namespace sg

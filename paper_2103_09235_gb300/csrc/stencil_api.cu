@@ -270,6 +270,12 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "wait_limit_ms")) {
         if (v < 1 || v > 600000) goto bad;
         p->wait_ms = v;
+    } else if (!strcmp(key, "fault_withhold_copy")) {
+        if (v != 0 && v != 1) goto bad;
+        p->fault_withhold_copy = (int)v;
+    } else if (!strcmp(key, "graph")) {
+        if (v != 0 && v != 1) goto bad;
+        p->use_graph = (int)v;
     } else if (!strcmp(key, "autotune")) {
         if (v != 0 && v != 1) goto bad;
         p->autotune = (int)v;
@@ -277,6 +283,7 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
         set_error("stencil_plan_set_option: unknown key '%s'", key);
         return STENCIL_ERR_INVALID_ARG;
     }
+    clear_graphs(p);  // captured runs bake the options in
     return STENCIL_OK;
 bad:
     set_error("stencil_plan_set_option: value %lld out of range for '%s'", (long long)v, key);
@@ -430,6 +437,8 @@ void stencil_plan_destroy(stencil_plan_t p)
 {
     if (!p) return;
     cudaDeviceSynchronize();
+    clear_graphs(p);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (p->d_status) cudaFree(p->d_status);
     if (p->d_acc) cudaFree(p->d_acc);
     if (p->A.alloc) cudaFree(p->A.alloc);

@@ -210,3 +210,64 @@ def test_bad_fold_rejected(env):
     x = torch.zeros((20, 20), device="cuda")
     assert plan.run_status(x, x, 10, 10) == 1   # folded width 21 > 20
     assert plan.run_status(x, x, -1, 1) == 1
+
+
+def test_bounded_wait_reports_timeout(env):
+    """A copy that never arrives ends the kernel's wait with a status, not a hang."""
+    torch, binding, oracle = env
+    shape = (200, 260)
+    c = synth.dyadic_coeffs(21, 2, 1, "star")
+    x = synth.grid(22, shape, np.float32)
+    plan = binding.Plan(shape, c)
+    plan.set_option("wait_limit_ms", 50).set_option("fault_withhold_copy", 1)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, 3, fold_m=1)
+    assert plan.sync_status() == 5
+    assert plan.sync_status() == 0          # cleared
+    plan.set_option("fault_withhold_copy", 0)
+    plan.run(xd, yd, 3, fold_m=1)            # the context is still usable
+    plan.sync()
+    check(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, 3))
+
+
+def test_graph_replay_matches_direct_launches(env):
+    """A run replayed from its captured graph equals the same run launched kernel by kernel."""
+    torch, binding, oracle = env
+    shape = (300, 520)
+    c = synth.dyadic_coeffs(23, 2, 1, "box")
+    x = synth.grid(24, shape, np.float32)
+    xd = torch.from_numpy(x).cuda()
+    outs = []
+    for graph in (1, 1, 0):
+        plan = binding.Plan(shape, c).set_option("graph", graph).set_option("block_b", 2)
+        y = torch.empty_like(xd)
+        plan.run(xd, y, 37, fold_m=3)
+        plan.run(xd, y, 37, fold_m=3)     # second call replays the captured graph
+        plan.sync()
+        outs.append(y.cpu().numpy())
+        plan.close()
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[2])
+    check(outs[0], oracle.run(x.astype(np.float64), c, 37))
+
+
+def test_run_inside_user_stream_capture(env):
+    """stencil_run enqueued while the caller captures a CUDA graph (after a warm-up run)."""
+    torch, binding, oracle = env
+    shape = (200, 256)
+    c = synth.dyadic_coeffs(25, 2, 1, "star")
+    x = synth.grid(26, shape, np.float32)
+    plan = binding.Plan(shape, c)
+    xd = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xd)
+    plan.run(xd, y, 20, fold_m=2)
+    torch.cuda.synchronize()
+    y.zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.run(xd, y, 20, fold_m=2, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    check(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, 20))
