@@ -115,27 +115,44 @@ cudaError_t launch_rel_l2(const void *y, bool y_f64, const double *ref, long lon
                           double *acc, cudaStream_t s);
 
 // ---- tcgen05 folded 2D box sweep (BF16 hi/lo split) -----------------------
+// A tile is 128 grid rows x 32 output columns.  The contraction dimension K
+// is the 48-column window x0-R .. x0+32+R of the tile, padded with zero
+// weights; R = m*r <= 8 keeps 32 + 2R <= 48.
+constexpr int kTcM = 128;
+constexpr int kTcN = 32;
+constexpr int kTcK = 48;
+constexpr int kTcKC = kTcK / 8;                 // 16-byte K chunks
+constexpr int kTcMaxR = 8;
+constexpr int kTcPanelElems = 64 * kTcK;        // one row offset: C_hi (32 rows) over C_lo (32 rows)
+constexpr int kTcThreads = 384;
+
 struct TC2DArgs {
     int nx, ny;
-    int tiles_x, tiles_y, ntiles;
-    int R;                 // folded radius
-    int tile_n;            // output columns per tile (N of the MMA)
-    int kpad;              // K = tile_n + 2R rounded up to 16
-    int terms;             // 3 = hi*hi + lo*hi + hi*lo, 1 = hi*hi
-    int map_x0, map_y0;
-    float mu;              // value subtracted before the BF16 split and added back
-    float sum_c;           // sum of the folded weights
-    const uint16_t *panels;  // Toeplitz panels, see tc2d_panel_layout
+    int tiles_x, ntiles;
+    int R;                  // folded radius
+    int halo_x;             // R rounded up to a multiple of 4
+    int box_w;              // staging box width (floats)
+    int rows;               // 128 + 2R staged rows
+    int rows_p;             // A-operand rows per K chunk in shared memory (odd)
+    int terms;              // 3: hi*hi + hi*lo + lo*hi, 1: hi*hi
+    int map_x0, map_y0;     // tensor-map coordinates of the interior origin
+    const double *mean_sum; // grid sum; mu = mean_sum[0] * inv_n (null: mu = 0)
+    double inv_n;
+    float sum_c;            // sum of the split weights actually applied
+    const uint16_t *panels; // (2R+1) panels, tc2d panel layout
     float *dst;
     int64_t dst_py;
     int dst_gw;
+    int dst_vec4;
     int *status;
     unsigned long long wait_ns;
 };
-bool tc2d_supported(int R, int tile_n);
-size_t tc2d_smem_bytes(int R, int tile_n, int *layout_words);
-size_t tc2d_panel_elems(int R, int tile_n);
-void tc2d_build_panels(const double *cm, int R, int tile_n, uint16_t *host_out);
+bool tc2d_supported(int R);
+size_t tc2d_smem_bytes(int R);
+// Builds the (2R+1) BF16 Toeplitz panels of folded weights cm ((2R+1)^2,
+// row-major (dy, dx)) with the hi/lo split and the mass correction; returns
+// the sum of the applied weights.
+double tc2d_build_panels(const double *cm, int R, uint16_t *host_out);
 cudaError_t launch_tc2d(const CUtensorMap &map, const TC2DArgs &a, int grid, size_t smem,
                         cudaStream_t s);
 cudaError_t launch_grid_mean(const float *origin, int nx, int ny, int64_t py, double *acc,

@@ -1,0 +1,444 @@
+// Folded 2D box sweep on the tcgen05 tensor cores (BF16 hi/lo, FP32 accumulate).
+//
+// One sweep applies the folded weights c^(m) (radius R = m*r, Section 3.2):
+//   out[y][x0+n] = sum_{a=-R..R} sum_k X[y+a][x0-R+k] * T_a[n][k],
+// where T_a is the banded Toeplitz matrix holding row a of c^(m)
+// (T_a[n][k] = c[a][k-n-R] for 0 <= k-n <= 2R).  This is the paper's vertical
+// and horizontal folding (Section 3.3, Eq. vfold and Eq. horifold) written as
+// 2R+1 dense contractions over the tile's 48-column window, one per row
+// offset a; the partial sums the paper keeps in vector registers accumulate
+// in tensor memory instead.
+//
+// Tile: M = 128 grid rows (the MMA's M) x 32 output columns.  The FP32 tile
+// plus R halo rows arrives by TMA; converter warps subtract the grid mean mu,
+// split v = x - mu into v_hi = bf16(v) and v_lo = bf16(v - v_hi) and write both
+// in the no-swizzle K-major core-matrix layout, in which every row is 16 bytes
+// away from the next within a K chunk.  The operand "rows y+a" for offset a is
+// then the same matrix with its descriptor start moved by 16*(a+R) bytes, so
+// no shifted copies are made.  Per (a, K step) one MMA of N = 64 multiplies
+// v_hi by [T_a,hi ; T_a,lo] and one of N = 32 multiplies v_lo by T_a,hi; the
+// two halves of the accumulator are added in the epilogue together with
+// mu * sum(c).  Toeplitz panels stay resident in shared memory.
+//
+// Warp roles (384 threads): warp 0 issues TMA loads, warp 1 owns tensor
+// memory and issues the MMAs (one thread), warps 4-7 convert, warps 8-11
+// drain the accumulator to global memory.  Every wait is bounded; a wait that
+// runs out records a timeout, raises an abort flag that ends the other roles'
+// waits, lets in-flight copies and MMAs land, frees tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace sg {
+namespace {
+
+constexpr int NT = kTcThreads;
+constexpr int PANEL_BYTES = kTcPanelElems * 2;  // 6144
+constexpr int LBO_B = 64 * 16;                  // K-chunk stride of a panel (64 rows x 16 B)
+constexpr uint32_t TMEM_COLS = 128;             // two 64-column accumulators
+
+// ---- tcgen05 wrappers ------------------------------------------------------
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    // start address, leading (K-chunk) and stride (8-row group) byte offsets,
+    // all >> 4; bit 46 = descriptor version 1; swizzle mode 0 (none)
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- bounded waits shared by all roles --------------------------------------
+
+struct Ctl {
+    uint64_t stage_full[2], stage_empty[2], a_full[2], a_empty[2], d_full[2], d_empty[2];
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, Ctl *ctl,
+                                              const TC2DArgs &a)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int *)&ctl->abort) return false;
+        if (globaltimer_ns() - t0 > a.wait_ns) {
+            *(volatile int *)&ctl->abort = 1;
+            record_status(a.status, DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// A final bounded wait used while winding down after an abort.
+__device__ __forceinline__ void drain_wait(uint64_t *bar, uint32_t parity, const TC2DArgs &a)
+{
+    mbar_wait_bounded(bar, parity, a.wait_ns);
+}
+
+}  // namespace
+}  // namespace sg
+
+namespace sg {
+namespace {
+
+// Shared-memory layout (bytes from the 1024-aligned base):
+//   [0, 1024)           control block (barriers, tensor-memory address, abort flag)
+//   A operands          stage s, part h (0 = hi, 1 = lo) at off_a + (2s+h)*a_bytes
+//   FP32 staging        stage s at off_stage + s*stage_bytes (TMA boxes)
+//   Toeplitz panels     (2R+1) * 6144 bytes
+//   4 KB of slack, so that no descriptor can reach past the allocation
+struct TcLayout {
+    uint32_t a_bytes, off_a, stage_bytes, off_stage, off_b, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int R, int rows, int rows_p, int box_w)
+{
+    TcLayout L;
+    L.a_bytes = (uint32_t)(kTcKC * rows_p * 16);
+    L.off_a = 1024;
+    L.off_stage = (L.off_a + 4 * L.a_bytes + 127) / 128 * 128;
+    L.stage_bytes = ((uint32_t)(rows * box_w * 4) + 127) / 128 * 128;
+    L.off_b = L.off_stage + 2 * L.stage_bytes;
+    L.total = L.off_b + (uint32_t)(2 * R + 1) * PANEL_BYTES + 4096;
+    return L;
+}
+
+__device__ __forceinline__ void store_point_tc(const TC2DArgs &a, int X, int Y, float v)
+{
+    float *dst = a.dst;
+    const int64_t py = a.dst_py;
+    const int nx = a.nx, ny = a.ny, gw = a.dst_gw;
+    const bool xl = X < gw, xh = X >= nx - gw, yl = Y < gw, yh = Y >= ny - gw;
+    if (xl) dst[Y * py + X + nx] = v;
+    if (xh) dst[Y * py + X - nx] = v;
+    if (yl) {
+        dst[(Y + ny) * py + X] = v;
+        if (xl) dst[(Y + ny) * py + X + nx] = v;
+        if (xh) dst[(Y + ny) * py + X - nx] = v;
+    }
+    if (yh) {
+        dst[(Y - ny) * py + X] = v;
+        if (xl) dst[(Y - ny) * py + X + nx] = v;
+        if (xh) dst[(Y - ny) * py + X - nx] = v;
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1)
+    k_tc2d(const __grid_constant__ CUtensorMap map, const __grid_constant__ TC2DArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem);
+    const TcLayout L = tc_layout(a.R, a.rows, a.rows_p, a.box_w);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = smem_u32(smem);
+    const int R = a.R;
+
+    if (tid == 0) {
+        prefetch_tensormap(&map);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&ctl->stage_full[s], 1);
+            mbar_init(&ctl->stage_empty[s], 128);
+            mbar_init(&ctl->a_full[s], 128);
+            mbar_init(&ctl->a_empty[s], 1);
+            mbar_init(&ctl->d_full[s], 1);
+            mbar_init(&ctl->d_empty[s], 128);
+        }
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&ctl->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    {  // resident Toeplitz panels
+        const int n16 = (2 * R + 1) * PANEL_BYTES / 16;
+        const uint4 *gp = reinterpret_cast<const uint4 *>(a.panels);
+        uint4 *sp = reinterpret_cast<uint4 *>(smem + L.off_b);
+        for (int i = tid; i < n16; i += NT) sp[i] = gp[i];
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+    const int first = blockIdx.x, step = gridDim.x;
+
+    if (warp == 0) {
+        // ---- producer: FP32 tile + halo by TMA
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(a.rows * a.box_w * 4);
+            int i = 0, last = -1;
+            for (int tile = first; tile < a.ntiles; tile += step, ++i) {
+                const int s = i & 1, k = i >> 1;
+                if (!wait_or_abort(&ctl->stage_empty[s], (k & 1) ^ 1, ctl, a)) break;
+                const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+                mbar_arrive_expect_tx(&ctl->stage_full[s], bytes);
+                tma_load_2d(smem + L.off_stage + s * L.stage_bytes, &map, &ctl->stage_full[s],
+                            a.map_x0 + tx * kTcN - a.halo_x, a.map_y0 + ty * kTcM - R);
+                last = i;
+            }
+            if (ctl->abort && last >= 0)
+                drain_wait(&ctl->stage_full[last & 1], (last >> 1) & 1, a);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint32_t id64 = idesc_bf16(kTcM, 64), id32 = idesc_bf16(kTcM, 32);
+            const uint32_t lbo_a = (uint32_t)a.rows_p * 16;
+            int i = 0, last = -1;
+            for (int tile = first; tile < a.ntiles; tile += step, ++i) {
+                const int s = i & 1, k = i >> 1;
+                if (!wait_or_abort(&ctl->a_full[s], k & 1, ctl, a)) break;
+                if (!wait_or_abort(&ctl->d_empty[s], (k & 1) ^ 1, ctl, a)) break;
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(s * 64);
+                const uint32_t a_hi = sbase + L.off_a + (2 * s) * L.a_bytes;
+                const uint32_t a_lo = a_hi + L.a_bytes;
+                const uint32_t b0 = sbase + L.off_b;
+                uint32_t acc = 0;
+                for (int ai = 0; ai <= 2 * R; ++ai) {
+                    for (int kk = 0; kk < kTcK / 16; ++kk) {
+                        const uint64_t bd =
+                            smem_desc(b0 + ai * PANEL_BYTES + kk * 2 * LBO_B, LBO_B, 128);
+                        const uint64_t ah = smem_desc(a_hi + kk * 2 * lbo_a + ai * 16, lbo_a, 128);
+                        if (a.terms == 3) {
+                            mma_bf16(dt, ah, bd, id64, acc);
+                            const uint64_t al =
+                                smem_desc(a_lo + kk * 2 * lbo_a + ai * 16, lbo_a, 128);
+                            mma_bf16(dt, al, bd, id32, 1u);
+                        } else {
+                            mma_bf16(dt, ah, bd, id32, acc);
+                        }
+                        acc = 1u;
+                    }
+                }
+                mma_commit(&ctl->a_empty[s]);
+                mma_commit(&ctl->d_full[s]);
+                last = i;
+            }
+            if (ctl->abort && last >= 0) drain_wait(&ctl->d_full[last & 1], (last >> 1) & 1, a);
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ---- converters: FP32 staging -> centred BF16 hi/lo operands
+        const int ct = tid - 128;
+        const float mu = a.mean_sum ? (float)(a.mean_sum[0] * a.inv_n) : 0.f;
+        const int off = a.halo_x - R;
+        const uint32_t lbo_a = (uint32_t)a.rows_p * 16;
+        int i = 0;
+        for (int tile = first; tile < a.ntiles; tile += step, ++i) {
+            const int s = i & 1, k = i >> 1;
+            bool ok = wait_or_abort(&ctl->stage_full[s], k & 1, ctl, a);
+            ok = ok && wait_or_abort(&ctl->a_empty[s], (k & 1) ^ 1, ctl, a);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const float *st = reinterpret_cast<const float *>(smem + L.off_stage + s * L.stage_bytes);
+            unsigned char *ahi = smem + L.off_a + (2 * s) * L.a_bytes;
+            unsigned char *alo = ahi + L.a_bytes;
+            for (int it = ct; it < a.rows * kTcKC; it += 128) {
+                const int kc = it % kTcKC, r = it / kTcKC;
+                const float *src = st + r * a.box_w + kc * 8 + off;
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = src[e] - mu;
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * e + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 =
+                        __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
+                    hw[e] = (uint32_t)__bfloat16_as_ushort(h0) |
+                            ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    lw[e] = (uint32_t)__bfloat16_as_ushort(l0) |
+                            ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+                const uint32_t o = kc * lbo_a + r * 16;
+                *reinterpret_cast<uint4 *>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&ctl->stage_empty[s]);
+            mbar_arrive(&ctl->a_full[s]);
+        }
+    } else if (warp >= 8) {
+        // ---- epilogue: tensor memory -> registers -> global memory
+        const int q = warp - 8;
+        const float mu = a.mean_sum ? (float)(a.mean_sum[0] * a.inv_n) : 0.f;
+        const float musum = mu * a.sum_c;
+        int i = 0;
+        for (int tile = first; tile < a.ntiles; tile += step, ++i) {
+            const int s = i & 1, k = i >> 1;
+            const bool ok = wait_or_abort(&ctl->d_full[s], k & 1, ctl, a);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * 64);
+            float v0[32], v1[32];
+            tmem_ld32(taddr, v0);
+            if (a.terms == 3) tmem_ld32(taddr + 32, v1);
+            tmem_ld_wait();
+            tc_fence_before();
+            mbar_arrive(&ctl->d_empty[s]);
+            const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+            const int Y = ty * kTcM + 32 * q + lane;
+            const int X0 = tx * kTcN;
+            if (Y < a.ny) {
+                float o[32];
+#pragma unroll
+                for (int n = 0; n < 32; ++n) o[n] = v0[n] + (a.terms == 3 ? v1[n] : 0.f) + musum;
+                float *row = a.dst + Y * a.dst_py + X0;
+                if (a.dst_vec4 && X0 + 32 <= a.nx) {
+#pragma unroll
+                    for (int n = 0; n < 32; n += 4)
+                        *reinterpret_cast<float4 *>(row + n) =
+                            make_float4(o[n], o[n + 1], o[n + 2], o[n + 3]);
+                } else {
+#pragma unroll
+                    for (int n = 0; n < 32; ++n)
+                        if (X0 + n < a.nx) row[n] = o[n];
+                }
+                if (a.dst_gw > 0 && (X0 < a.dst_gw || X0 + 32 > a.nx - a.dst_gw ||
+                                     Y < a.dst_gw || Y >= a.ny - a.dst_gw)) {
+#pragma unroll
+                    for (int n = 0; n < 32; ++n)
+                        if (X0 + n < a.nx) store_point_tc(a, X0 + n, Y, o[n]);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+bool tc2d_supported(int R) { return R >= 1 && R <= kTcMaxR; }
+
+static void tc_geometry(int R, int *rows, int *rows_p, int *box_w, int *halo_x)
+{
+    *halo_x = round_up(R, 4);
+    *rows = kTcM + 2 * R;
+    *rows_p = *rows | 1;  // odd: consecutive K chunks fall in different bank groups
+    *box_w = round_up(kTcK + *halo_x - R, 4);
+}
+
+size_t tc2d_smem_bytes(int R)
+{
+    int rows, rows_p, box_w, hx;
+    tc_geometry(R, &rows, &rows_p, &box_w, &hx);
+    return tc_layout(R, rows, rows_p, box_w).total;
+}
+
+double tc2d_build_panels(const double *cm, int R, uint16_t *out)
+{
+    const int W = 2 * R + 1;
+    std::vector<double> hi(W * W), lo(W * W);
+    double target = 0.0, got = 0.0;
+    for (int i = 0; i < W * W; ++i) {
+        const __nv_bfloat16 h = __double2bfloat16(cm[i]);
+        hi[i] = (double)__bfloat162float(h);
+        lo[i] = (double)__bfloat162float(__double2bfloat16(cm[i] - hi[i]));
+        target += cm[i];
+        got += hi[i] + lo[i];
+    }
+    // mass correction: the centre tap's lo absorbs the rounding of the sum
+    const int c = R * W + R;
+    lo[c] = (double)__bfloat162float(__double2bfloat16(lo[c] + (target - got)));
+    double applied = 0.0;
+    for (int i = 0; i < W * W; ++i) applied += hi[i] + lo[i];
+    for (int ai = 0; ai < W; ++ai) {
+        uint16_t *panel = out + (size_t)ai * kTcPanelElems;
+        for (int n = 0; n < 64; ++n) {
+            const int nn = n & 31;
+            const std::vector<double> &src = n < 32 ? hi : lo;
+            for (int k = 0; k < kTcK; ++k) {
+                const int b = k - nn - R;  // column offset
+                double w = 0.0;
+                if (b >= -R && b <= R) w = src[ai * W + (b + R)];
+                const __nv_bfloat16 bw = __double2bfloat16(w);
+                panel[(k / 8) * 512 + n * 8 + (k % 8)] = __bfloat16_as_ushort(bw);
+            }
+        }
+    }
+    return applied;
+}
+
+cudaError_t launch_tc2d(const CUtensorMap &map, const TC2DArgs &a, int grid, size_t smem,
+                        cudaStream_t s)
+{
+    static cudaError_t once = [] {
+        int dev = 0, maxs = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return cudaFuncSetAttribute(k_tc2d, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    }();
+    if (once != cudaSuccess) return once;
+    k_tc2d<<<grid, NT, smem, s>>>(map, a);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

@@ -9,12 +9,6 @@ stencil_status_t run3d(stencil_plan_s *, const float *, float *, int64_t, int, c
     return STENCIL_ERR_UNSUPPORTED;
 }
 
-stencil_status_t run2d_tc(stencil_plan_s *, const float *, float *, int64_t, int, cudaStream_t)
-{
-    set_error("tensor-core sweeps are not built yet");
-    return STENCIL_ERR_UNSUPPORTED;
-}
-
 stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t)
 {
     p->tuned_m = 1;

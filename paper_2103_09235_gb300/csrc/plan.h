@@ -39,7 +39,8 @@ struct stencil_plan_s {
     void *d1a = nullptr, *d1b = nullptr;      // 1D working grids
     void *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
     double *d_acc = nullptr;                  // small FP64 reduction buffer
-    std::map<int, uint16_t *> panels;         // tensor-core Toeplitz panels by (m, tile_n) key
+    std::map<int, uint16_t *> panels;         // tensor-core Toeplitz panels by m
+    std::map<int, double> panel_sum;          // sum of the applied split weights by m
     std::map<std::tuple<const void *, int, int, int>, CUtensorMap> maps;
     size_t scratch_bytes = 0;
 
@@ -88,6 +89,10 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
 stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s);
 
 void clear_graphs(stencil_plan_s *p);
+stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b, stencil_plan_s::PassCfg *cfg);
+stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int b,
+                               const std::vector<double> &c, float *dst, int64_t dst_py,
+                               int dst_gw, bool dst_vec4, cudaStream_t s);
 void ensure_device_facts(stencil_plan_s *p);
 
 // Runs enqueue(stream, &kernels) on stream s.  With graphs enabled and s not

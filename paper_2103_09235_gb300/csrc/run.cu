@@ -122,7 +122,7 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
 }
 
 // Tile shape, shared memory and grid of a 2D CUDA-core pass (cached per plan).
-static stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
+stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
                                       stencil_plan_s::PassCfg *cfg)
 {
     auto key = std::make_tuple(m, b, p->tile_y);
@@ -156,7 +156,7 @@ static stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
 }
 
 // One CUDA-core 2D pass from padded grid `src` to `dst` (padded origin or dense).
-static stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int b,
+stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int b,
                                       const std::vector<double> &c, float *dst, int64_t dst_py,
                                       int dst_gw, bool dst_vec4, cudaStream_t s)
 {

@@ -1,0 +1,160 @@
+// Time-loop driver of the tensor-core path: floor(T/m) folded sweeps of a 2D
+// box stencil on tcgen05 (BF16 hi/lo split, FP32 accumulation), then T mod m
+// plain CUDA-core steps (Section 3.4: the skipped intermediate steps).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "plan.h"
+
+namespace sg {
+
+static stencil_status_t tc_panels(stencil_plan_s *p, int m, const uint16_t **out, double *sum)
+{
+    auto it = p->panels.find(m);
+    if (it == p->panels.end()) {
+        const std::vector<double> *cm = nullptr;
+        stencil_status_t st = plan_folded(p, m, &cm);
+        if (st != STENCIL_OK) return st;
+        const int R = m * p->r;
+        std::vector<uint16_t> host((size_t)(2 * R + 1) * kTcPanelElems);
+        const double applied = tc2d_build_panels(cm->data(), R, host.data());
+        uint16_t *d = nullptr;
+        cudaError_t e = cudaMalloc(&d, host.size() * sizeof(uint16_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d, host.data(), host.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (d) cudaFree(d);
+            return cuda_fail(e, "tensor-core panels");
+        }
+        p->scratch_bytes += host.size() * sizeof(uint16_t);
+        it = p->panels.emplace(m, d).first;
+        p->panel_sum[m] = applied;
+    }
+    *out = it->second;
+    *sum = p->panel_sum[m];
+    return STENCIL_OK;
+}
+
+static stencil_status_t launch_tc_pass(stencil_plan_s *p, const Padded &src, int m,
+                                       const uint16_t *panels, double sum_c, float *dst,
+                                       int64_t dst_py, int dst_gw, bool dst_vec4, cudaStream_t s)
+{
+    const int R = m * p->r;
+    TC2DArgs a;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.tiles_x = ceil_div(p->nx, kTcN);
+    a.ntiles = a.tiles_x * ceil_div(p->ny, kTcM);
+    a.R = R;
+    a.halo_x = round_up(R, 4);
+    a.rows = kTcM + 2 * R;
+    a.rows_p = a.rows | 1;
+    a.box_w = round_up(kTcK + a.halo_x - R, 4);
+    a.terms = p->precision == STENCIL_PREC_BF16X1 ? 1 : 3;
+    a.map_x0 = src.gx;
+    a.map_y0 = src.gy;
+    a.mean_sum = p->tc_center ? p->d_acc : nullptr;
+    a.inv_n = 1.0 / ((double)p->nx * p->ny);
+    a.sum_c = (float)sum_c;
+    a.panels = panels;
+    a.dst = dst;
+    a.dst_py = dst_py;
+    a.dst_gw = dst_gw;
+    a.dst_vec4 = dst_vec4 ? 1 : 0;
+    a.status = p->d_status;
+    a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
+    const int box[2] = {a.box_w, a.rows};
+    const CUtensorMap *map = plan_map(p, src, box);
+    if (!map) return STENCIL_ERR_CUDA;
+    const size_t smem = tc2d_smem_bytes(R);
+    const int grid = std::min(a.ntiles, p->sm_count);
+    cudaError_t e = launch_tc2d(*map, a, grid, smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core sweep launch");
+    return STENCIL_OK;
+}
+
+stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
+                          cudaStream_t s)
+{
+    const int R = m * p->r;
+    const int nmin = std::min(p->nx, p->ny);
+    if (2 * R + 1 > nmin) {
+        set_error("tensor-core sweep: folded width %d exceeds the grid", 2 * R + 1);
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    if (!tc2d_supported(R) || !sweep2d_supported(p->r, 1, p->pattern)) {
+        set_error("tensor-core sweep: folded radius %d unsupported (1..%d)", R, kTcMaxR);
+        return STENCIL_ERR_UNSUPPORTED;
+    }
+    ensure_device_facts(p);
+    if (tc2d_smem_bytes(R) > (size_t)p->max_smem) {
+        set_error("tensor-core sweep: shared memory");
+        return STENCIL_ERR_UNSUPPORTED;
+    }
+    const uint16_t *panels = nullptr;
+    double sum_c = 0.0;
+    const std::vector<double> *c1 = nullptr;
+    stencil_status_t st = tc_panels(p, m, &panels, &sum_c);
+    if (st == STENCIL_OK) st = plan_folded(p, 1, &c1);
+    if (st == STENCIL_OK) st = ensure_padded(p);
+    if (st != STENCIL_OK) return st;
+    const int64_t q = T / m, rem = T % m;
+    const int max_halo = std::min(kGhost, nmin);
+    const int bplain = std::max(1, max_halo / p->r);
+    std::vector<int> plain;  // fused plain steps per remainder pass
+    for (int64_t d = 0; d < rem; d += bplain) plain.push_back((int)std::min<int64_t>(bplain, rem - d));
+    int gw = q ? R : 0;
+    for (int b : plain) gw = std::max(gw, b * p->r);
+    for (int b : plain) {
+        stencil_plan_s::PassCfg cfg;
+        st = pass2d_config(p, 1, b, &cfg);
+        if (st != STENCIL_OK) return st;
+    }
+    const bool out_vec4 = (p->nx % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    const int64_t npass = q + (int64_t)plain.size();
+
+    auto enqueue = [&](cudaStream_t st_, int *nl) -> stencil_status_t {
+        cudaError_t e = launch_import(p->A, in, gw, st_);
+        if (e != cudaSuccess) return cuda_fail(e, "import launch");
+        *nl += 1;
+        if (p->tc_center && q > 0) {
+            e = cudaMemsetAsync(p->d_acc, 0, sizeof(double), st_);
+            if (e == cudaSuccess) e = launch_grid_mean(p->A.origin, p->nx, p->ny, p->A.py, p->d_acc, st_);
+            if (e != cudaSuccess) return cuda_fail(e, "grid mean");
+            *nl += 1;
+        }
+        const Padded *cur = &p->A, *oth = &p->B;
+        int64_t done = 0;
+        for (int64_t i = 0; i < q; ++i, ++done) {
+            const bool last = done + 1 == npass;
+            stencil_status_t r = launch_tc_pass(p, *cur, m, panels, sum_c, last ? out : oth->origin,
+                                                last ? (int64_t)p->nx : oth->py, last ? 0 : gw,
+                                                last ? out_vec4 : true, st_);
+            if (r != STENCIL_OK) return r;
+            *nl += 1;
+            std::swap(cur, oth);
+        }
+        for (int b : plain) {
+            const bool last = done + 1 == npass;
+            stencil_status_t r = launch_pass2d(p, *cur, 1, b, *c1, last ? out : oth->origin,
+                                               last ? (int64_t)p->nx : oth->py, last ? 0 : gw,
+                                               last ? out_vec4 : true, st_);
+            if (r != STENCIL_OK) return r;
+            *nl += 1;
+            ++done;
+            std::swap(cur, oth);
+        }
+        return STENCIL_OK;
+    };
+    std::vector<int64_t> key = {3, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m,
+                                p->precision, p->tc_center, p->wait_ms};
+    st = run_maybe_graph(p, key, s, enqueue);
+    p->last_m = m;
+    p->last_b = 1;
+    p->last_engine = 1;
+    return st;
+}
+
+}  // namespace sg
