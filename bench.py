@@ -28,13 +28,29 @@ if ROOT not in sys.path:
 
 from paper_2103_09235_gb300 import synth  # noqa: E402
 
-SHAPE = (4096, 4096)
-T_STEPS = 1000
-KIND = "star"
-SEED = synth.BASE_SEED + 2
 METRIC = "GStencil/s and % HBM roofline, folded TC vs plain FP32 at rel-L2 <= 1e-5"
 UNIT = "GStencil/s"
-WORKLOAD = "2D 5-point star 4096x4096 FP32, periodic, T=1000, dyadic coefficients (seeded)"
+# Workloads: the default is the 2D 5-point star; "box8192" is the 2D 9-point
+# box the tensor-core contraction targets.
+CONFIGS = {
+    "star4096": dict(shape=(4096, 4096), T=1000, kind="star", seed=synth.BASE_SEED + 2,
+                     workload="2D 5-point star 4096x4096 FP32, periodic, T=1000, "
+                              "dyadic coefficients (seeded)"),
+    "box8192": dict(shape=(8192, 8192), T=512, kind="box", seed=synth.BASE_SEED + 3,
+                    workload="2D 9-point box 8192x8192 FP32, periodic, T=512, "
+                             "dyadic coefficients (seeded)"),
+}
+SHAPE = CONFIGS["star4096"]["shape"]
+T_STEPS = CONFIGS["star4096"]["T"]
+KIND = CONFIGS["star4096"]["kind"]
+SEED = CONFIGS["star4096"]["seed"]
+WORKLOAD = CONFIGS["star4096"]["workload"]
+
+
+def select_config(name: str):
+    global SHAPE, T_STEPS, KIND, SEED, WORKLOAD
+    c = CONFIGS[name]
+    SHAPE, T_STEPS, KIND, SEED, WORKLOAD = c["shape"], c["T"], c["kind"], c["seed"], c["workload"]
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -177,9 +193,9 @@ def run_gpu(args):
     npts = float(np.prod(SHAPE))
     stream = torch.cuda.current_stream(dev)
 
-    def make_plan(m, b):
+    def make_plan(m, b, precision=0):
         plan = binding.Plan(SHAPE, c)
-        plan.set_option("block_b", b)
+        plan.set_option("block_b", b).set_option("precision", precision)
         return plan
 
     xd = torch.from_numpy(x_host).to(dev)
@@ -205,7 +221,7 @@ def run_gpu(args):
         return times, plan.get("launches") - launches0
 
     m_best, b_best = args.fold_m, args.block_b
-    plan = make_plan(m_best, b_best)
+    plan = make_plan(m_best, b_best, args.precision)
 
     # --- main timed region: whole job, inputs resident on the device
     if pg:
@@ -226,6 +242,7 @@ def run_gpu(args):
         ms_total = float(t.item())
     value = ws * npts * T_STEPS * args.steps / (ms_total * 1e-3) / 1e9
     used_m, used_b = plan.get("last_m"), plan.get("last_b")
+    engine = "tensor-core" if plan.get("last_engine") == 1 else "cuda-core"
     if args.ncu:
         # profiling run: only the timed loop above, nothing else
         if rank == 0:
@@ -251,7 +268,7 @@ def run_gpu(args):
         try:
             with open(tfile) as f:
                 tr = json.load(f)
-            key = "m%d_b%d" % (used_m, used_b)
+            key = "%s_%s_m%d_b%d" % (args.config, engine, used_m, used_b)
             traffic = tr.get(key)
         except Exception:
             traffic = None
@@ -301,12 +318,14 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(SHAPE), "T": T_STEPS,
-                       "fold_m": used_m, "block_b": used_b, "engine": "cuda-core",
+                       "fold_m": used_m, "block_b": used_b, "engine": engine,
+                       "precision": ["fp32", "bf16x3", "bf16x1"][args.precision],
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind, "kernel": "k_sweep2d",
+                         "peak_source": peak_kind,
+                         "kernel": "k_tc2d" if engine == "tensor-core" else "k_sweep2d",
                          "pass_ms": pass_ms, "alg_bytes_per_launch": alg_bytes},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(npts * 4),
@@ -327,14 +346,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="star4096", choices=sorted(CONFIGS))
     ap.add_argument("--fold-m", type=int, default=4)
     ap.add_argument("--block-b", type=int, default=2)
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
+                    help="0 = FP32 CUDA cores, 1 = BF16x3 tensor cores, 2 = BF16x1")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: timed loop only, no L2 flush buffer, no extra legs")
     args = ap.parse_args()
+    select_config(args.config)
     if args.impl == "reference":
         run_reference(args)
     else:

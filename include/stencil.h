@@ -80,7 +80,8 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
 
 /*
  * Sets a tuning option (all optional).  Keys:
- *   "precision"     stencil_precision_t; BF16 modes apply to 2D box stencils with m > 1.
+ *   "precision"     stencil_precision_t; BF16 modes run folded 2D sweeps (m > 1,
+ *                   m*r <= 8) on the tensor cores; plain steps stay on CUDA cores.
  *   "block_b"       temporal-blocking depth: folded sweeps per memory round trip
  *                   (0 = automatic).
  *   "tile_y"        rows per CTA tile of the 2D CUDA-core sweep (0 = automatic).

@@ -219,7 +219,9 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
         if (p->tile_y == 0) p->tile_y = p->tuned_ty;
     }
 
-    if (m > 1 && p->pattern == PAT_BOX && p->precision != STENCIL_PREC_FP32)
+    // any folded 2D stencil fits the Toeplitz contraction (a star's folded
+    // diamond just leaves zero weights in the panels)
+    if (m > 1 && p->precision != STENCIL_PREC_FP32)
         return run2d_tc(p, in, out, T, m, s);
     const int R = m * p->r;
     const int nmin = std::min(p->nx, p->ny);
