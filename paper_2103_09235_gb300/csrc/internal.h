@@ -144,17 +144,18 @@ struct TC2DArgs {
     int64_t dst_py;
     int dst_gw;
     int dst_vec4;
+    int tma_store;          // 1: the output tile leaves through a swizzled smem tile and a TMA store
     int *status;
     unsigned long long wait_ns;
 };
 bool tc2d_supported(int R);
-size_t tc2d_smem_bytes(int R);
+size_t tc2d_smem_bytes(int R, bool tma_store);
 // Builds the (2R+1) BF16 Toeplitz panels of folded weights cm ((2R+1)^2,
 // row-major (dy, dx)) with the hi/lo split and the mass correction; returns
 // the sum of the applied weights.
 double tc2d_build_panels(const double *cm, int R, uint16_t *host_out);
-cudaError_t launch_tc2d(const CUtensorMap &map, const TC2DArgs &a, int grid, size_t smem,
-                        cudaStream_t s);
+cudaError_t launch_tc2d(const CUtensorMap &map, const CUtensorMap &dmap, const TC2DArgs &a,
+                        int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_grid_mean(const float *origin, int nx, int ny, int64_t py, double *acc,
                              cudaStream_t s);
 
@@ -162,5 +163,9 @@ cudaError_t launch_grid_mean(const float *origin, int nx, int ny, int64_t py, do
 // Encodes a tiled FP32 tensor map over a padded grid's whole allocation.
 // box has P.ndim entries (x first).  Returns false if the driver refuses it.
 bool encode_padded_map(CUtensorMap *map, const Padded &P, const int *box);
+// Encodes a 2D FP32 store map over exactly nx x ny elements at base (row
+// stride pitch elements) with 128-byte swizzle; false if unaligned or refused.
+bool encode_store_map_2d(CUtensorMap *map, float *base, int nx, int ny, int64_t pitch, int box_x,
+                         int box_y);
 
 }  // namespace sg

@@ -221,6 +221,21 @@ EncodeTiledFn encode_fn()
 }
 }  // namespace
 
+bool encode_store_map_2d(CUtensorMap *map, float *base, int nx, int ny, int64_t pitch, int box_x,
+                         int box_y)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    if (((uintptr_t)base % 16) != 0 || (pitch * 4) % 16 != 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+    cuuint32_t bx[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y}, es[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, bx, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 bool encode_padded_map(CUtensorMap *map, const Padded &P, const int *box)
 {
     EncodeTiledFn fn = encode_fn();

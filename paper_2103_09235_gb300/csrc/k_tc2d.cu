@@ -106,6 +106,7 @@ struct Ctl {
     uint64_t stage_full[2], stage_empty[2], a_full[2], a_empty[2], d_full[2], d_empty[2];
     uint32_t tmem_base;
     int abort;
+    int epi_ok[2][4];  // per-iteration votes of the four epilogue warps
 };
 
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, Ctl *ctl,
@@ -142,11 +143,12 @@ namespace {
 //   FP32 staging        stage s at off_stage + s*stage_bytes (TMA boxes)
 //   Toeplitz panels     (2R+1) * 6144 bytes
 //   4 KB of slack, so that no descriptor can reach past the allocation
+//   output tile         128 x 32 FP32, 128-byte swizzled (only with the TMA store)
 struct TcLayout {
-    uint32_t a_bytes, off_a, stage_bytes, off_stage, off_b, total;
+    uint32_t a_bytes, off_a, stage_bytes, off_stage, off_b, off_out, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int R, int rows, int rows_p, int box_w)
+__host__ __device__ inline TcLayout tc_layout(int R, int rows, int rows_p, int box_w, int tma_store)
 {
     TcLayout L;
     L.a_bytes = (uint32_t)(kTcKC * rows_p * 16);
@@ -154,9 +156,24 @@ __host__ __device__ inline TcLayout tc_layout(int R, int rows, int rows_p, int b
     L.off_stage = (L.off_a + 4 * L.a_bytes + 127) / 128 * 128;
     L.stage_bytes = ((uint32_t)(rows * box_w * 4) + 127) / 128 * 128;
     L.off_b = L.off_stage + 2 * L.stage_bytes;
-    L.total = L.off_b + (uint32_t)(2 * R + 1) * PANEL_BYTES + 4096;
+    L.off_out = (L.off_b + (uint32_t)(2 * R + 1) * PANEL_BYTES + 1023) / 1024 * 1024;
+    L.total = tma_store ? L.off_out + kTcM * kTcN * 4 : L.off_b + (uint32_t)(2 * R + 1) * PANEL_BYTES;
     return L;
 }
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(x), "r"(y)
+        : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ void store_point_tc(const TC2DArgs &a, int X, int Y, float v)
 {
@@ -179,11 +196,12 @@ __device__ __forceinline__ void store_point_tc(const TC2DArgs &a, int X, int Y, 
 }
 
 __global__ void __launch_bounds__(NT, 1)
-    k_tc2d(const __grid_constant__ CUtensorMap map, const __grid_constant__ TC2DArgs a)
+    k_tc2d(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
+           const __grid_constant__ TC2DArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     Ctl *ctl = reinterpret_cast<Ctl *>(smem);
-    const TcLayout L = tc_layout(a.R, a.rows, a.rows_p, a.box_w);
+    const TcLayout L = tc_layout(a.R, a.rows, a.rows_p, a.box_w, a.tma_store);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = smem_u32(smem);
     const int R = a.R;
@@ -295,8 +313,24 @@ __global__ void __launch_bounds__(NT, 1)
                 const int kc = it % kTcKC, r = it / kTcKC;
                 const float *src = st + r * a.box_w + kc * 8 + off;
                 float v[8];
+                if (off == 0) {  // 16-byte aligned: two vector loads
+                    const float4 p0 = reinterpret_cast<const float4 *>(src)[0];
+                    const float4 p1 = reinterpret_cast<const float4 *>(src)[1];
+                    v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
+                    v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+                } else if ((off & 1) == 0) {
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = src[e] - mu;
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 p = reinterpret_cast<const float2 *>(src)[e];
+                        v[2 * e] = p.x;
+                        v[2 * e + 1] = p.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = src[e];
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] -= mu;
                 uint32_t hw[4], lw[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -326,8 +360,14 @@ __global__ void __launch_bounds__(NT, 1)
         int i = 0;
         for (int tile = first; tile < a.ntiles; tile += step, ++i) {
             const int s = i & 1, k = i >> 1;
-            const bool ok = wait_or_abort(&ctl->d_full[s], k & 1, ctl, a);
-            if (!__all_sync(0xffffffffu, ok)) break;
+            bool ok = wait_or_abort(&ctl->d_full[s], k & 1, ctl, a);
+            ok = __all_sync(0xffffffffu, ok);
+            // the four epilogue warps decide together, so that none of them is
+            // left waiting at a named barrier the others never reach
+            if (lane == 0) ctl->epi_ok[s][q] = ok ? 1 : 0;
+            epi_barrier();
+            const volatile int *votes = ctl->epi_ok[s];
+            if (!(votes[0] && votes[1] && votes[2] && votes[3])) break;
             tc_fence_after();
             const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * 64);
             float v0[32], v1[32];
@@ -339,12 +379,28 @@ __global__ void __launch_bounds__(NT, 1)
             const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
             const int Y = ty * kTcM + 32 * q + lane;
             const int X0 = tx * kTcN;
-            if (Y < a.ny) {
-                float o[32];
+            float o[32];
 #pragma unroll
-                for (int n = 0; n < 32; ++n) o[n] = v0[n] + (a.terms == 3 ? v1[n] : 0.f) + musum;
+            for (int n = 0; n < 32; ++n) o[n] = v0[n] + (a.terms == 3 ? v1[n] : 0.f) + musum;
+            if (a.tma_store) {
+                // row 32q+lane of the swizzled tile: 16-byte chunk j lands at j ^ (row & 7)
+                const int row = 32 * q + lane;
+                unsigned char *tile_s = smem + L.off_out;
+                if (tid == 256) bulk_wait_read();  // previous tile's store has read the buffer
+                epi_barrier();
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    *reinterpret_cast<float4 *>(tile_s + row * 128 + ((j ^ (row & 7)) * 16)) =
+                        make_float4(o[4 * j], o[4 * j + 1], o[4 * j + 2], o[4 * j + 3]);
+                fence_proxy_async_smem();
+                epi_barrier();
+                if (tid == 256) tma_store_2d(&dmap, tile_s, X0, ty * kTcM);
+            }
+            if (Y < a.ny) {
                 float *row = a.dst + Y * a.dst_py + X0;
-                if (a.dst_vec4 && X0 + 32 <= a.nx) {
+                if (a.tma_store) {
+                    // the bulk store wrote the interior; only ghost copies remain
+                } else if (a.dst_vec4 && X0 + 32 <= a.nx) {
 #pragma unroll
                     for (int n = 0; n < 32; n += 4)
                         *reinterpret_cast<float4 *>(row + n) =
@@ -364,6 +420,7 @@ __global__ void __launch_bounds__(NT, 1)
         }
     }
 
+    if (a.tma_store && tid == 256) bulk_wait_all();
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -386,11 +443,11 @@ static void tc_geometry(int R, int *rows, int *rows_p, int *box_w, int *halo_x)
     *box_w = round_up(kTcK + *halo_x - R, 4);
 }
 
-size_t tc2d_smem_bytes(int R)
+size_t tc2d_smem_bytes(int R, bool tma_store)
 {
     int rows, rows_p, box_w, hx;
     tc_geometry(R, &rows, &rows_p, &box_w, &hx);
-    return tc_layout(R, rows, rows_p, box_w).total;
+    return tc_layout(R, rows, rows_p, box_w, tma_store ? 1 : 0).total;
 }
 
 double tc2d_build_panels(const double *cm, int R, uint16_t *out)
@@ -427,8 +484,8 @@ double tc2d_build_panels(const double *cm, int R, uint16_t *out)
     return applied;
 }
 
-cudaError_t launch_tc2d(const CUtensorMap &map, const TC2DArgs &a, int grid, size_t smem,
-                        cudaStream_t s)
+cudaError_t launch_tc2d(const CUtensorMap &map, const CUtensorMap &dmap, const TC2DArgs &a,
+                        int grid, size_t smem, cudaStream_t s)
 {
     static cudaError_t once = [] {
         int dev = 0, maxs = 0;
@@ -437,7 +494,7 @@ cudaError_t launch_tc2d(const CUtensorMap &map, const TC2DArgs &a, int grid, siz
         return cudaFuncSetAttribute(k_tc2d, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
     }();
     if (once != cudaSuccess) return once;
-    k_tc2d<<<grid, NT, smem, s>>>(map, a);
+    k_tc2d<<<grid, NT, smem, s>>>(map, dmap, a);
     return cudaGetLastError();
 }
 

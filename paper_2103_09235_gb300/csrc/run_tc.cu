@@ -3,6 +3,8 @@
 // plain CUDA-core steps (Section 3.4: the skipped intermediate steps).
 #include <cuda_runtime.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -68,9 +70,17 @@ static stencil_status_t launch_tc_pass(stencil_plan_s *p, const Padded &src, int
     const int box[2] = {a.box_w, a.rows};
     const CUtensorMap *map = plan_map(p, src, box);
     if (!map) return STENCIL_ERR_CUDA;
-    const size_t smem = tc2d_smem_bytes(R);
+    // the output leaves by TMA store when the tile buffer fits and the
+    // destination rows are 16-byte aligned; otherwise by direct stores
+    CUtensorMap dmap;
+    memset(&dmap, 0, sizeof(dmap));
+    a.tma_store = 0;
+    if (tc2d_smem_bytes(R, true) <= (size_t)p->max_smem &&
+        encode_store_map_2d(&dmap, dst, p->nx, p->ny, dst_py, kTcN, kTcM))
+        a.tma_store = 1;
+    const size_t smem = tc2d_smem_bytes(R, a.tma_store != 0);
     const int grid = std::min(a.ntiles, p->sm_count);
-    cudaError_t e = launch_tc2d(*map, a, grid, smem, s);
+    cudaError_t e = launch_tc2d(*map, dmap, a, grid, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core sweep launch");
     return STENCIL_OK;
 }
@@ -89,7 +99,7 @@ stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_
         return STENCIL_ERR_UNSUPPORTED;
     }
     ensure_device_facts(p);
-    if (tc2d_smem_bytes(R) > (size_t)p->max_smem) {
+    if (tc2d_smem_bytes(R, false) > (size_t)p->max_smem) {
         set_error("tensor-core sweep: shared memory");
         return STENCIL_ERR_UNSUPPORTED;
     }

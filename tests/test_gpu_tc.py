@@ -79,3 +79,16 @@ def test_tc_without_centering(env):
     err = oracle.rel_l2(y, ref)
     print("TC no centering rel-L2 %.3e" % err)
     assert err <= TOL
+
+
+@pytest.mark.parametrize("shape,T,m", [((300, 520), 21, 4), ((256, 384), 14, 2)])
+def test_tc_star_parity(env, shape, T, m):
+    """A folded star is a diamond inside the (2R+1)^2 window: the panels carry its zeros."""
+    _, _, oracle = env
+    c = synth.dyadic_coeffs(800, 2, 1, "star")
+    x = synth.grid(801, shape, np.float32)
+    ref = oracle.run(x.astype(np.float64), c, T)
+    y = run_tc(env, shape, c, x, T, m, precision=1)
+    err = oracle.rel_l2(y, ref)
+    print("TC star %s T=%d m=%d rel-L2 %.3e" % (shape, T, m, err))
+    assert err <= TOL
