@@ -87,6 +87,8 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
  *   "tile_y"        rows per CTA tile of the 2D CUDA-core sweep (0 = automatic).
  *   "tc_tile_n"     output columns per tensor-core tile: 32, 64 or 128.
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
+ *   "tc_tma_store"  1 = tensor-core tiles leave through a TMA store when the
+ *                   destination allows it (default 1); 0 = direct stores.
  *   "wait_limit_ms" bound of every device-side wait (default 2000).
  *   "autotune"      1 = time candidates when stencil_run gets fold_m = 0 (default 1).
  *   "graph"         1 = capture each distinct run (pointers, T, m, options) once into

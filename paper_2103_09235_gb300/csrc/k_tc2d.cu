@@ -420,6 +420,7 @@ __global__ void __launch_bounds__(NT, 1)
         }
     }
 
+    __syncwarp();  // every warp reconverges after its role before the block barrier
     if (a.tma_store && tid == 256) bulk_wait_all();
     tc_fence_before();
     __syncthreads();

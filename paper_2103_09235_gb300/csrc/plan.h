@@ -26,6 +26,7 @@ struct stencil_plan_s {
     int tile_y = 0;
     int tc_tile_n = 64;
     int tc_center = 1;
+    int tc_tma_store = 1;
     int autotune = 1;
     long long wait_ms = 2000;
     int fault_withhold_copy = 0;  // test hook, see stencil_plan_set_option

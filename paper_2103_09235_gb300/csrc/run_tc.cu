@@ -75,7 +75,7 @@ static stencil_status_t launch_tc_pass(stencil_plan_s *p, const Padded &src, int
     CUtensorMap dmap;
     memset(&dmap, 0, sizeof(dmap));
     a.tma_store = 0;
-    if (tc2d_smem_bytes(R, true) <= (size_t)p->max_smem &&
+    if (p->tc_tma_store && tc2d_smem_bytes(R, true) <= (size_t)p->max_smem &&
         encode_store_map_2d(&dmap, dst, p->nx, p->ny, dst_py, kTcN, kTcM))
         a.tma_store = 1;
     const size_t smem = tc2d_smem_bytes(R, a.tma_store != 0);

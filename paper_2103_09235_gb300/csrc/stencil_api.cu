@@ -273,6 +273,9 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "fault_withhold_copy")) {
         if (v != 0 && v != 1) goto bad;
         p->fault_withhold_copy = (int)v;
+    } else if (!strcmp(key, "tc_tma_store")) {
+        if (v != 0 && v != 1) goto bad;
+        p->tc_tma_store = (int)v;
     } else if (!strcmp(key, "graph")) {
         if (v != 0 && v != 1) goto bad;
         p->use_graph = (int)v;
