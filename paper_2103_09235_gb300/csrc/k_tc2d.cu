@@ -60,12 +60,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n)
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t idesc, uint32_t accumulate)
 {
+    // no memory clobber: ordering with the operand writes comes from the
+    // mbarrier waits and fences around the issue loop
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
@@ -269,23 +270,31 @@ __global__ void __launch_bounds__(NT, 1)
                 tc_fence_after();
                 const uint32_t dt = tmem + (uint32_t)(s * 64);
                 const uint32_t a_hi = sbase + L.off_a + (2 * s) * L.a_bytes;
-                const uint32_t a_lo = a_hi + L.a_bytes;
-                const uint32_t b0 = sbase + L.off_b;
-                uint32_t acc = 0;
-                for (int ai = 0; ai <= 2 * R; ++ai) {
-                    for (int kk = 0; kk < kTcK / 16; ++kk) {
-                        const uint64_t bd =
-                            smem_desc(b0 + ai * PANEL_BYTES + kk * 2 * LBO_B, LBO_B, 128);
-                        const uint64_t ah = smem_desc(a_hi + kk * 2 * lbo_a + ai * 16, lbo_a, 128);
-                        if (a.terms == 3) {
-                            mma_bf16(dt, ah, bd, id64, acc);
-                            const uint64_t al =
-                                smem_desc(a_lo + kk * 2 * lbo_a + ai * 16, lbo_a, 128);
-                            mma_bf16(dt, al, bd, id32, 1u);
-                        } else {
-                            mma_bf16(dt, ah, bd, id32, acc);
+                // descriptors of the first (row offset, K step); the others differ
+                // only in the start-address field, by whole 16-byte units
+                const uint64_t dh0 = smem_desc(a_hi, lbo_a, 128);
+                const uint64_t dl0 = smem_desc(a_hi + L.a_bytes, lbo_a, 128);
+                const uint64_t db0 = smem_desc(sbase + L.off_b, LBO_B, 128);
+                const uint32_t kstep_a = (2 * lbo_a) >> 4, kstep_b = (2 * LBO_B) >> 4;
+                if (a.terms == 3) {
+                    mma_bf16(dt, dh0, db0, id64, 0u);
+                    mma_bf16(dt, dl0, db0, id32, 1u);
+                    for (int ai = 0; ai <= 2 * R; ++ai) {
+                        const uint32_t oa = (uint32_t)ai, ob = (uint32_t)ai * (PANEL_BYTES >> 4);
+#pragma unroll
+                        for (int kk = (ai == 0 ? 1 : 0); kk < kTcK / 16; ++kk) {
+                            const uint64_t d_a = oa + kk * kstep_a, d_b = ob + kk * kstep_b;
+                            mma_bf16(dt, dh0 + d_a, db0 + d_b, id64, 1u);
+                            mma_bf16(dt, dl0 + d_a, db0 + d_b, id32, 1u);
                         }
-                        acc = 1u;
+                    }
+                } else {
+                    mma_bf16(dt, dh0, db0, id32, 0u);
+                    for (int ai = 0; ai <= 2 * R; ++ai) {
+                        const uint32_t oa = (uint32_t)ai, ob = (uint32_t)ai * (PANEL_BYTES >> 4);
+#pragma unroll
+                        for (int kk = (ai == 0 ? 1 : 0); kk < kTcK / 16; ++kk)
+                            mma_bf16(dt, dh0 + oa + kk * kstep_a, db0 + ob + kk * kstep_b, id32, 1u);
                     }
                 }
                 mma_commit(&ctl->a_empty[s]);
