@@ -1,0 +1,248 @@
+// 3D CUDA-core stencil sweeps (plain m = 1 and folded m > 1), streaming along z.
+//
+// A CTA owns a 64 x 16 (x, y) column of the grid and a chunk of z planes.
+// Input planes arrive one per step by TMA (a 2D view of the padded 3D grid:
+// plane z, rows y-R .. y+16+R) into a four-slot ring, three planes ahead of
+// the compute.  Each thread owns a 4-point strip of one row and keeps a
+// register window of 2R+1 output planes: input plane z is read once from
+// shared memory and added, with the weights of plane offset a, into the
+// partial sums of output planes z - a (the counterparts of Section 3.3,
+// taken along z: the paper handles a 3D grid as a stack of 2D slices);
+// output plane z - R is then complete and stored.  The input plane's slot is
+// free as soon as it has been read, so the ring needs only the prefetch depth.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace sg {
+namespace {
+
+constexpr int TX3 = 64, TY3 = 16, NT3 = 256, NSLOT = 4;
+
+__host__ __device__ constexpr int cabs_div3(int v, int d) { return ((v < 0 ? -v : v) + d - 1) / d; }
+
+template <int RB, int M, int PAT>
+struct Taps3 {
+    static constexpr int R = RB * M;
+    static constexpr int W = 2 * R + 1;
+    static constexpr int RP = (R + 3) / 4 * 4;
+    __host__ __device__ static constexpr bool nz(int a, int b, int c)
+    {
+        return PAT == PAT_BOX ? true : (cabs_div3(a, RB) + cabs_div3(b, RB) + cabs_div3(c, RB) <= M);
+    }
+};
+
+__device__ __noinline__ void store_ghosts3(const Sweep3DArgs &a, int X, int Y, int Z, float v)
+{
+    const int gw = a.dst_gw;
+    int xs[3] = {X, 0, 0}, ys[3] = {Y, 0, 0}, zs[3] = {Z, 0, 0};
+    int nxs = 1, nys = 1, nzs = 1;
+    if (X < gw) xs[nxs++] = X + a.nx;
+    if (X >= a.nx - gw) xs[nxs++] = X - a.nx;
+    if (Y < gw) ys[nys++] = Y + a.ny;
+    if (Y >= a.ny - gw) ys[nys++] = Y - a.ny;
+    if (Z < gw) zs[nzs++] = Z + a.nz;
+    if (Z >= a.nz - gw) zs[nzs++] = Z - a.nz;
+    for (int i = 0; i < nzs; ++i)
+        for (int j = 0; j < nys; ++j)
+            for (int k = 0; k < nxs; ++k)
+                if (i | j | k) a.dst[zs[i] * a.dst_pz + ys[j] * a.dst_py + xs[k]] = v;
+}
+
+template <int RB, int M, int PAT>
+__global__ void __launch_bounds__(NT3)
+    k_sweep3d(const __grid_constant__ CUtensorMap map, const __grid_constant__ Sweep3DArgs a)
+{
+    using TP = Taps3<RB, M, PAT>;
+    constexpr int R = TP::R, W = TP::W, RP = TP::RP;
+    constexpr int NSEG = 4 + 2 * RP;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    float *slots = reinterpret_cast<float *>(smem + 1024);
+    const int HX = a.halo_x;
+    const int SP = TX3 + 2 * HX;   // shared row pitch
+    const int ROWS = TY3 + 2 * R;
+    const uint32_t slot_bytes = (uint32_t)(SP * ROWS * 4);
+    const int tid = threadIdx.x;
+
+    const int tile = blockIdx.x;
+    const int txy = tile % a.ntiles_xy, zc = tile / a.ntiles_xy;
+    const int tx = txy % a.tiles_x, ty = txy / a.tiles_x;
+    const int x0 = tx * TX3, y0 = ty * TY3;
+    const int z0 = zc * a.zchunk, z1 = min(a.nz, z0 + a.zchunk);
+    const int zin0 = z0 - R, nin = (z1 - z0) + 2 * R;  // input planes streamed
+    const int rows_per_plane = a.ny + 2 * a.map_y0;    // padded rows of one plane
+
+    if (tid == 0) {
+        prefetch_tensormap(&map);
+        for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int p) {  // input plane index p (0-based in this chunk)
+        const int s = p % NSLOT;
+        const int z = zin0 + p;
+        const int row = (z + a.map_z0) * rows_per_plane + (a.map_y0 + y0 - R);
+        mbar_arrive_expect_tx(&bars[s], slot_bytes);
+        tma_load_2d(slots + s * a.buf_floats, &map, &bars[s], a.map_x0 + x0 - HX, row);
+    };
+    if (tid == 0)
+        for (int p = 0; p < NSLOT - 1 && p < nin; ++p) issue(p);
+
+    // thread -> (4-column strip, row) of the tile
+    const int strip = tid % (TX3 / 4), yr = tid / (TX3 / 4);
+    const int X = x0 + 4 * strip, Y = y0 + yr;
+    const bool live = (Y < a.ny) && (X < a.nx);
+
+    float acc[W][4];
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
+
+    for (int p = 0; p < nin; ++p) {
+        if (tid == 0 && p + NSLOT - 1 < nin) issue(p + NSLOT - 1);
+        const int s = p % NSLOT;
+        const bool ok = mbar_wait_bounded(&bars[s], (p / NSLOT) & 1, a.wait_ns);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                record_status(a.status, DEV_TIMEOUT);
+                for (int q = p + 1; q < min(nin, p + NSLOT); ++q)
+                    mbar_wait_bounded(&bars[q % NSLOT], (q / NSLOT) & 1, a.wait_ns);
+            }
+            return;
+        }
+        const float *pl = slots + s * a.buf_floats + 4 * strip + HX - RP;
+        // this input plane feeds output plane z - R + i with plane offset a = R - i
+#pragma unroll
+        for (int dy = -R; dy <= R; ++dy) {
+            float seg[NSEG];
+            const float4 *rp = reinterpret_cast<const float4 *>(pl + (yr + R + dy) * SP);
+#pragma unroll
+            for (int q = 0; q < NSEG / 4; ++q) {
+                const float4 t = rp[q];
+                seg[4 * q] = t.x;
+                seg[4 * q + 1] = t.y;
+                seg[4 * q + 2] = t.z;
+                seg[4 * q + 3] = t.w;
+            }
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const int az = R - i;
+#pragma unroll
+                for (int dx = -R; dx <= R; ++dx) {
+                    if (TP::nz(az, dy, dx)) {
+                        const float w = a.c[((az + R) * W + (dy + R)) * W + (dx + R)];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            acc[i][v] = fmaf(w, seg[v + dx + RP], acc[i][v]);
+                    }
+                }
+            }
+        }
+        const int zo = zin0 + p - R;  // output plane completed by this input plane
+        if (zo >= z0 && live) {
+            float *row = a.dst + zo * a.dst_pz + Y * a.dst_py;
+            if (a.dst_vec4 && X + 3 < a.nx) {
+                *reinterpret_cast<float4 *>(row + X) =
+                    make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (X + v < a.nx) row[X + v] = acc[0][v];
+            }
+            if (a.dst_gw > 0 &&
+                (X < a.dst_gw || X + 3 >= a.nx - a.dst_gw || Y < a.dst_gw ||
+                 Y >= a.ny - a.dst_gw || zo < a.dst_gw || zo >= a.nz - a.dst_gw)) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (X + v < a.nx) store_ghosts3(a, X + v, Y, zo, acc[0][v]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < W - 1; ++i)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
+        __syncthreads();  // slot s is free for plane p + NSLOT
+    }
+}
+
+template <int RB, int M, int PAT>
+cudaError_t prepare3()
+{
+    static cudaError_t once = [] {
+        int dev = 0, maxs = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return cudaFuncSetAttribute(k_sweep3d<RB, M, PAT>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    }();
+    return once;
+}
+
+template <int RB, int M, int PAT>
+cudaError_t launch3(const CUtensorMap &map, const Sweep3DArgs &a, int grid, size_t smem,
+                   cudaStream_t s)
+{
+    cudaError_t e = prepare3<RB, M, PAT>();
+    if (e != cudaSuccess) return e;
+    k_sweep3d<RB, M, PAT><<<grid, NT3, smem, s>>>(map, a);
+    return cudaGetLastError();
+}
+
+template <int RB, int M, int PAT>
+int occ3(size_t smem)
+{
+    if (prepare3<RB, M, PAT>() != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep3d<RB, M, PAT>, NT3, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+#define SG_SWEEP3D_LIST(X)                                                                 \
+    X(1, 1, PAT_STAR) X(1, 2, PAT_STAR) X(2, 1, PAT_STAR) X(1, 1, PAT_BOX) X(1, 2, PAT_BOX) \
+    X(2, 1, PAT_BOX)
+
+}  // namespace
+
+bool sweep3d_supported(int rb, int m, int pattern)
+{
+#define SG_X(RB_, M_, P_) \
+    if (rb == RB_ && m == M_ && pattern == P_) return true;
+    SG_SWEEP3D_LIST(SG_X)
+#undef SG_X
+    return false;
+}
+
+size_t sweep3d_smem_bytes(int tile_y, int R, int *buf_floats)
+{
+    (void)tile_y;
+    const int HX = round_up(R, 4);
+    const int bf = round_up((TX3 + 2 * HX) * (TY3 + 2 * R), 32);
+    if (buf_floats) *buf_floats = bf;
+    return 1024 + (size_t)NSLOT * bf * 4;
+}
+
+int sweep3d_ctas_per_sm(int rb, int m, int pattern, size_t smem)
+{
+#define SG_X(RB_, M_, P_) \
+    if (rb == RB_ && m == M_ && pattern == P_) return occ3<RB_, M_, P_>(smem);
+    SG_SWEEP3D_LIST(SG_X)
+#undef SG_X
+    return 0;
+}
+
+cudaError_t launch_sweep3d(int rb, int m, int pattern, const CUtensorMap &map,
+                           const Sweep3DArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+#define SG_X(RB_, M_, P_) \
+    if (rb == RB_ && m == M_ && pattern == P_) return launch3<RB_, M_, P_>(map, a, grid, smem, s);
+    SG_SWEEP3D_LIST(SG_X)
+#undef SG_X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sg

@@ -3,12 +3,6 @@
 
 namespace sg {
 
-stencil_status_t run3d(stencil_plan_s *, const float *, float *, int64_t, int, cudaStream_t)
-{
-    set_error("3D sweeps are not built yet");
-    return STENCIL_ERR_UNSUPPORTED;
-}
-
 stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t)
 {
     p->tuned_m = 1;

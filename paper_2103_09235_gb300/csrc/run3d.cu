@@ -1,0 +1,111 @@
+// Time-loop driver of 3D runs: floor(T/m) folded sweeps and T mod m plain
+// steps, one z-streaming CUDA-core sweep per launch, ping-ponging between the
+// plan's padded grids (Section 3.3's two arrays) and ending in `out`.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "plan.h"
+
+namespace sg {
+
+namespace {
+constexpr int kTX3 = 64, kTY3 = 16, kZChunk = 64;
+}
+
+static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m,
+                                      const std::vector<double> &c, float *dst, int64_t dst_py,
+                                      int64_t dst_pz, int dst_gw, bool dst_vec4, cudaStream_t s)
+{
+    const int R = m * p->r;
+    Sweep3DArgs a;
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.nz = p->nz;
+    a.tiles_x = ceil_div(p->nx, kTX3);
+    a.tiles_y = ceil_div(p->ny, kTY3);
+    a.ntiles_xy = a.tiles_x * a.tiles_y;
+    a.zchunk = kZChunk;
+    a.zchunks = ceil_div(p->nz, kZChunk);
+    a.ntiles = a.ntiles_xy * a.zchunks;
+    a.tile_y = kTY3;
+    a.halo_x = round_up(R, 4);
+    a.map_x0 = src.gx;
+    a.map_y0 = src.gy;
+    a.map_z0 = src.gz;
+    int bf = 0;
+    const size_t smem = sweep3d_smem_bytes(kTY3, R, &bf);
+    a.buf_floats = bf;
+    a.dst = dst;
+    a.dst_py = dst_py;
+    a.dst_pz = dst_pz;
+    a.dst_gw = dst_gw;
+    a.dst_vec4 = dst_vec4 ? 1 : 0;
+    a.status = p->d_status;
+    a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
+    for (size_t k = 0; k < c.size(); ++k) a.c[k] = (float)c[k];
+    // the padded 3D grid seen as one tall 2D array: plane z, row y is row
+    // (z + gz) * (ny + 2 gy) + y + gy
+    Padded view = src;
+    view.ndim = 2;
+    view.ny = (src.ny + 2 * src.gy) * (src.nz + 2 * src.gz) - 2 * src.gy;
+    const int box[2] = {kTX3 + 2 * a.halo_x, kTY3 + 2 * R};
+    const CUtensorMap *map = plan_map(p, view, box);
+    if (!map) return STENCIL_ERR_CUDA;
+    cudaError_t e = launch_sweep3d(p->r, m, p->pattern, *map, a, a.ntiles, smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "3D sweep launch");
+    return STENCIL_OK;
+}
+
+stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
+                       cudaStream_t s)
+{
+    if (m == 0) m = 1;
+    const int R = m * p->r;
+    const int nmin = std::min(p->nx, std::min(p->ny, p->nz));
+    if (2 * R + 1 > nmin || R > kGhost) {
+        set_error("3D sweep: folded width %d exceeds the grid", 2 * R + 1);
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    if (!sweep3d_supported(p->r, m, p->pattern) || !sweep3d_supported(p->r, 1, p->pattern)) {
+        set_error("3D sweep: no kernel for r=%d m=%d", p->r, m);
+        return STENCIL_ERR_UNSUPPORTED;
+    }
+    const std::vector<double> *cm = nullptr, *c1 = nullptr;
+    stencil_status_t st = plan_folded(p, m, &cm);
+    if (st == STENCIL_OK) st = plan_folded(p, 1, &c1);
+    if (st == STENCIL_OK) st = ensure_padded(p);
+    if (st != STENCIL_OK) return st;
+    ensure_device_facts(p);
+    const int64_t q = T / m, rem = T % m;
+    const int64_t npass = q + rem;
+    const int gw = q ? R : p->r;
+    const bool out_vec4 = (p->nx % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    auto enqueue = [&](cudaStream_t st_, int *nl) -> stencil_status_t {
+        cudaError_t e = launch_import(p->A, in, gw, st_);
+        if (e != cudaSuccess) return cuda_fail(e, "import launch");
+        *nl += 1;
+        const Padded *cur = &p->A, *oth = &p->B;
+        for (int64_t i = 0; i < npass; ++i) {
+            const bool last = i + 1 == npass;
+            const int mm = i < q ? m : 1;
+            stencil_status_t r = launch_pass3d(
+                p, *cur, mm, mm == m ? *cm : *c1, last ? out : oth->origin,
+                last ? (int64_t)p->nx : oth->py, last ? (int64_t)p->nx * p->ny : oth->pz,
+                last ? 0 : gw, last ? out_vec4 : true, st_);
+            if (r != STENCIL_OK) return r;
+            *nl += 1;
+            std::swap(cur, oth);
+        }
+        return STENCIL_OK;
+    };
+    std::vector<int64_t> key = {4, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, p->wait_ms};
+    st = run_maybe_graph(p, key, s, enqueue);
+    p->last_m = m;
+    p->last_b = 1;
+    p->last_engine = 0;
+    return st;
+}
+
+}  // namespace sg

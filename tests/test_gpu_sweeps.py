@@ -271,3 +271,26 @@ def test_run_inside_user_stream_capture(env):
     g.replay()
     torch.cuda.synchronize()
     check(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, 20))
+
+
+CASES_3D = [
+    # shape (z, y, x), kind, r, T, m
+    ((100, 40, 70), "star", 1, 6, 1),
+    ((100, 40, 70), "box", 1, 5, 1),
+    ((100, 40, 70), "star", 1, 9, 2),
+    ((66, 33, 130), "box", 1, 7, 2),
+    ((40, 36, 64), "star", 2, 4, 1),
+    ((40, 36, 64), "box", 2, 3, 1),
+    ((12, 9, 11), "star", 1, 5, 2),
+]
+
+
+@pytest.mark.parametrize("shape,kind,r,T,m", CASES_3D)
+def test_sweep3d_parity(env, shape, kind, r, T, m):
+    _, _, oracle = env
+    c = synth.dyadic_coeffs(3100 + r, 3, r, kind)
+    x = synth.grid(3200 + T, shape, np.float32)
+    y, info = gpu_run(env, shape, c, x, T, m)
+    ref = oracle.run(x.astype(np.float64), c, T)
+    check(y, ref)
+    assert info["m"] == m
