@@ -70,6 +70,44 @@ int sweep2d_ctas_per_sm(int rb, int m, int pattern, size_t smem);
 cudaError_t launch_sweep2d(int rb, int m, int pattern, const CUtensorMap &map,
                            const Sweep2DArgs &a, int grid, size_t smem, cudaStream_t s);
 
+// ---- batched persistent 2D sweep --------------------------------------------
+// One pass of one grid of a batched run.
+struct BatchPass {
+    int variant;        // pattern * 8 + m (radius-1 base stencils)
+    int b, H, HX;       // fused sweeps, halo, halo rounded up to 4
+    int tiles_x, ntiles;
+    int map;            // index of the source tensor map
+    int coef, ncoef;    // weights in the coefficient pool
+    int dep;            // pass whose completion this one waits for (-1: none)
+    int nx, ny;
+    int map_x0, map_y0;
+    float *dst;
+    int64_t dst_py;
+    int dst_gw;
+    int dst_vec4;
+};
+struct BatchItem {
+    int pass;
+    int tile;
+};
+struct BatchArgs {
+    const BatchItem *items;
+    int nitems;
+    const BatchPass *passes;
+    const CUtensorMap *maps;  // 64-byte aligned, in global memory
+    const float *coefs;
+    int *done;                // tiles completed per pass (zeroed before the launch)
+    int *next;                // queue head (zeroed before the launch)
+    int tile_y;
+    int buf_floats;
+    int *status;
+    unsigned long long wait_ns;
+};
+bool batched_variant_supported(int rb, int m, int pattern);
+size_t batched_smem_bytes(int buf_floats);
+int batched_ctas_per_sm(size_t smem);
+cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s);
+
 // ---- 3D CUDA-core sweep (streaming along z) -------------------------------
 struct Sweep3DArgs {
     int nx, ny, nz;

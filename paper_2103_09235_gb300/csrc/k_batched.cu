@@ -1,0 +1,162 @@
+// Batched persistent sweep: many independent 2D grids of uneven size,
+// stencil (star / box) and step count advance in ONE launch.
+//
+// The host flattens every grid's time loop (its folded passes of b fused
+// sweeps, then its plain remainder passes, Section 3.4) into passes, and the
+// passes into a work list of (pass, tile) items ordered round by round: all
+// grids' first passes, then all grids' second passes, and so on.  Persistent
+// CTAs pop items from a device queue (one atomic counter).  Before loading
+// its tile a CTA waits, with a bounded spin, until every tile of the grid's
+// previous pass has been counted done; items only ever wait for items earlier
+// in the list, and every CTA is resident, so the queue cannot deadlock.  A
+// tile is the same TMA-staged, register-window, temporally blocked body as the
+// single-grid 2D sweep, with the grid's folded weights read from shared
+// memory.  Completion is published with a release fence and an atomic add;
+// the waiter acquires it and issues a proxy fence before its TMA load, so the
+// copy engine sees the other CTAs' stores.
+#include "sweep2d_tile.cuh"
+
+namespace sg {
+namespace {
+
+using namespace tile2d;
+
+struct SmemCoef {
+    const float *c;
+    __device__ __forceinline__ float operator()(int k) const { return c[k]; }
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Runs the tile body of the variant (pattern, m); radius-1 base stencils.
+__device__ __forceinline__ void run_variant(int variant, const float *stage, float *w0, float *w1,
+                                            int TY, int H, int HX, int b, const SmemCoef &cf,
+                                            const TileOut &o, int gx0, int gy0)
+{
+    switch (variant) {
+    case PAT_STAR * 8 + 1: process_tile<1, 1, PAT_STAR>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
+    case PAT_STAR * 8 + 2: process_tile<1, 2, PAT_STAR>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
+    case PAT_STAR * 8 + 3: process_tile<1, 3, PAT_STAR>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
+    case PAT_STAR * 8 + 4: process_tile<1, 4, PAT_STAR>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
+    case PAT_BOX * 8 + 1: process_tile<1, 1, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
+    case PAT_BOX * 8 + 2: process_tile<1, 2, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
+    case PAT_BOX * 8 + 3: process_tile<1, 3, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
+    case PAT_BOX * 8 + 4: process_tile<1, 4, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
+    default: break;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads2D, 1) k_batched(const __grid_constant__ BatchArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    int *s_item = reinterpret_cast<int *>(smem + 64);
+    int *s_ok = reinterpret_cast<int *>(smem + 68);
+    float *cs = reinterpret_cast<float *>(smem + 128);  // up to kMaxTaps2D weights
+    float *base = reinterpret_cast<float *>(smem + 128 + round_up(kMaxTaps2D * 4, 128)) + BUF_PAD;
+    float *stage = base, *w0 = base + a.buf_floats, *w1 = base + 2 * a.buf_floats;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    for (uint32_t it = 0;; ++it) {
+        if (tid == 0) *s_item = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int idx = *s_item;
+        if (idx >= a.nitems) break;
+        const BatchItem item = a.items[idx];
+        const BatchPass &ps = a.passes[item.pass];
+        for (int k = tid; k < ps.ncoef; k += kThreads2D) cs[k] = a.coefs[ps.coef + k];
+        const int tx = item.tile % ps.tiles_x, ty = item.tile / ps.tiles_x;
+        if (tid == 0) {
+            int ok = 1;
+            if (ps.dep >= 0) {
+                const int need = a.passes[ps.dep].ntiles;
+                if (ld_acquire(&a.done[ps.dep]) < need) {
+                    const uint64_t t0 = globaltimer_ns();
+                    while (ld_acquire(&a.done[ps.dep]) < need) {
+                        if (globaltimer_ns() - t0 > a.wait_ns) {
+                            ok = 0;
+                            break;
+                        }
+                    }
+                }
+            }
+            if (ok) {
+                fence_proxy_async_global();
+                const uint32_t bytes = (uint32_t)((kTileX2D + 2 * ps.HX) * (a.tile_y + 2 * ps.H) * 4);
+                mbar_arrive_expect_tx(bar, bytes);
+                tma_load_2d(stage, &a.maps[ps.map], bar, ps.map_x0 + tx * kTileX2D - ps.HX,
+                            ps.map_y0 + ty * a.tile_y - ps.H);
+            }
+            *s_ok = ok;
+        }
+        __syncthreads();
+        if (!*s_ok) {
+            if (tid == 0) record_status(a.status, DEV_TIMEOUT);
+            break;
+        }
+        const bool landed = mbar_wait_bounded(bar, it & 1, a.wait_ns);
+        if (__syncthreads_or(!landed)) {
+            if (tid == 0) record_status(a.status, DEV_TIMEOUT);
+            break;
+        }
+        const TileOut o{ps.dst, ps.dst_py, ps.nx, ps.ny, ps.dst_gw, ps.dst_vec4};
+        run_variant(ps.variant, stage, w0, w1, a.tile_y, ps.H, ps.HX, ps.b, SmemCoef{cs}, o,
+                    tx * kTileX2D - ps.HX, ty * a.tile_y - ps.H);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(&a.done[item.pass], 1);
+        }
+    }
+}
+
+}  // namespace
+
+bool batched_variant_supported(int rb, int m, int pattern)
+{
+    return rb == 1 && m >= 1 && m <= 4 && (pattern == PAT_STAR || pattern == PAT_BOX);
+}
+
+size_t batched_smem_bytes(int buf_floats)
+{
+    return 128 + round_up(kMaxTaps2D * 4, 128) + (size_t)3 * buf_floats * 4 + 2 * BUF_PAD * 4;
+}
+
+cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+    static cudaError_t once = [] {
+        int dev = 0, maxs = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    }();
+    if (once != cudaSuccess) return once;
+    k_batched<<<grid, kThreads2D, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+int batched_ctas_per_sm(size_t smem)
+{
+    int n = 0;
+    cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched, kThreads2D, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+}  // namespace sg

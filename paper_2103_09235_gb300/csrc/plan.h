@@ -61,6 +61,8 @@ struct stencil_plan_s {
     std::map<std::vector<int64_t>, GraphEnt> graphs;
     cudaStream_t cap_stream = nullptr;
     int use_graph = 1;
+    // device work lists of batched runs led by this plan, by batch key
+    std::map<std::vector<int64_t>, unsigned char *> batch_mem;
 
     // bookkeeping
     long long launches = 0;

@@ -451,6 +451,7 @@ void stencil_plan_destroy(stencil_plan_t p)
     if (p->stage_in) cudaFree(p->stage_in);
     if (p->stage_out) cudaFree(p->stage_out);
     for (auto &kv : p->panels) cudaFree(kv.second);
+    for (auto &kv : p->batch_mem) cudaFree(kv.second);
     delete p;
 }
 

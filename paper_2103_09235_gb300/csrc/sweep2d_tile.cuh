@@ -1,0 +1,266 @@
+// Per-tile body of the 2D CUDA-core sweep, shared by the single-grid kernel
+// and the batched persistent kernel: the register-window strip sweep over a
+// shared-memory tile (see k_sweep2d.cu) and the b-sweep temporal block.
+#pragma once
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace sg {
+namespace tile2d {
+
+// Where a tile's final sweep writes: a padded grid (with a ghost band to
+// refresh) or a dense grid.
+struct TileOut {
+    float *dst;      // interior origin
+    int64_t dst_py;  // row stride (elements)
+    int nx, ny;
+    int dst_gw;      // ghost band to refresh (0 = dense)
+    int dst_vec4;    // rows allow 16-byte stores
+};
+
+// Weight accessors: from the kernel parameter block (constant bank) or from
+// shared memory.
+struct ParamCoef {
+    const float *c;
+    __device__ __forceinline__ float operator()(int k) const { return c[k]; }
+};
+
+constexpr int TX = kTileX2D;
+constexpr int NT = kThreads2D;
+constexpr int BUF_PAD = 32;  // floats of slack before and after every buffer
+
+__host__ __device__ constexpr int cabs_div(int v, int d) { return ((v < 0 ? -v : v) + d - 1) / d; }
+
+template <int RB, int M, int PAT>
+struct Taps {
+    static constexpr int R = RB * M;
+    static constexpr int W = 2 * R + 1;
+    static constexpr int RP = (R + 3) / 4 * 4;  // halo columns loaded per side, 16-byte aligned
+    __host__ __device__ static constexpr bool nz(int a, int b)
+    {
+        return PAT == PAT_BOX ? true : (cabs_div(a, RB) + cabs_div(b, RB) <= M);
+    }
+};
+
+__device__ __forceinline__ void store_point(float *dst, int64_t py, int nx, int ny, int gw, int X,
+                                            int Y, float v)
+{
+    dst[Y * py + X] = v;
+    if (gw > 0) {
+        const bool xl = X < gw, xh = X >= nx - gw, yl = Y < gw, yh = Y >= ny - gw;
+        if (xl) dst[Y * py + X + nx] = v;
+        if (xh) dst[Y * py + X - nx] = v;
+        if (yl) {
+            dst[(Y + ny) * py + X] = v;
+            if (xl) dst[(Y + ny) * py + X + nx] = v;
+            if (xh) dst[(Y + ny) * py + X - nx] = v;
+        }
+        if (yh) {
+            dst[(Y - ny) * py + X] = v;
+            if (xl) dst[(Y - ny) * py + X + nx] = v;
+            if (xh) dst[(Y - ny) * py + X - nx] = v;
+        }
+    }
+}
+
+template <int RB, int M, int PAT>
+struct Strip {
+    using TP = Taps<RB, M, PAT>;
+    static constexpr int R = TP::R, W = TP::W, RP = TP::RP;
+    static constexpr int NSEG = 4 + 2 * RP;
+    static constexpr int NNZ = [] {
+        int n = 0;
+        for (int a = -R; a <= R; ++a)
+            for (int b = -R; b <= R; ++b) n += TP::nz(a, b) ? 1 : 0;
+        return n;
+    }();
+    // rows of the steady loop unrolled together: a full turn of the window
+    // when the row's multiply-adds are few, so the window shift is renamed away
+    static constexpr int UNR = NNZ * 4 <= 200 ? W : 1;
+
+    __device__ __forceinline__ static void load(const float *rowp, float (&seg)[NSEG])
+    {
+        const float4 *rp = reinterpret_cast<const float4 *>(rowp);
+#pragma unroll
+        for (int q = 0; q < NSEG / 4; ++q) {
+            const float4 t = rp[q];
+            seg[4 * q + 0] = t.x;
+            seg[4 * q + 1] = t.y;
+            seg[4 * q + 2] = t.z;
+            seg[4 * q + 3] = t.w;
+        }
+    }
+
+    // input row into window slot i (output row j - R + i, row offset a = R - i)
+    template <class Coef>
+    __device__ __forceinline__ static void slot(float (&acc)[W][4], const float (&seg)[NSEG],
+                                                const Coef &cf, int i)
+    {
+        const int aa = R - i;
+#pragma unroll
+        for (int bb = -R; bb <= R; ++bb) {
+            if (TP::nz(aa, bb)) {
+                const float w = cf((aa + R) * W + (bb + R));
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[i][v] = fmaf(w, seg[v + bb + RP], acc[i][v]);
+            }
+        }
+    }
+
+    __device__ __forceinline__ static void shift(float (&acc)[W][4])
+    {
+#pragma unroll
+        for (int i = 0; i < W - 1; ++i)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
+    }
+};
+
+static __device__ __noinline__ void store_ghosts4(const TileOut &a, int X, int Y, float v0, float v1,
+                                           float v2, float v3)
+{
+    const float v[4] = {v0, v1, v2, v3};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (X + k < a.nx) store_point(a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, X + k, Y, v[k]);
+}
+
+// One sweep over output rows [r0, r1) and 4-column strips [k0, k1) of a
+// shared-memory buffer S (row pitch SP).  FINAL writes to global memory;
+// otherwise the outputs go to the same coordinates of buffer D.
+//
+// A strip of rows [ya, yb) reads input rows ya-R .. yb+R-1.  The first 2R
+// rows only feed window slots whose output row is >= ya and the last 2R only
+// slots whose output row is < yb, so every output gets exactly its taps.
+template <int RB, int M, int PAT, bool FINAL, class Coef>
+__device__ __forceinline__ void sweep_region(const float *__restrict__ S, float *__restrict__ D,
+                                             int SP, int r0, int r1, int k0, int k1,
+                                             const Coef &cf, const TileOut &a, int gx0, int gy0)
+{
+    using ST = Strip<RB, M, PAT>;
+    constexpr int R = ST::R, W = ST::W, RP = ST::RP, NSEG = ST::NSEG;
+    const int nsx = k1 - k0;
+    const int nr = r1 - r0;
+    if (nsx <= 0 || nr <= 0) return;
+    // row groups: as many as the threads allow, each at least 2R rows tall
+    int G = NT / nsx;
+    G = max(1, min(G, nr / (2 * R)));
+    const int items = nsx * G;
+
+    for (int it = threadIdx.x; it < items; it += NT) {
+        const int k = k0 + it % nsx;
+        const int g = it / nsx;
+        const int ya = r0 + (g * nr) / G;
+        const int yb = r0 + ((g + 1) * nr) / G;
+        const int cx = 4 * k;
+        const float *col = S + cx - RP;
+
+        float acc[W][4];
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
+
+        auto emit = [&](int y) {
+            if constexpr (FINAL) {
+                const int X = gx0 + cx, Y = gy0 + y;
+                if (Y < a.ny && X < a.nx) {
+                    float *row = a.dst + Y * a.dst_py;
+                    if (a.dst_vec4 && X + 3 < a.nx) {
+                        *reinterpret_cast<float4 *>(row + X) =
+                            make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            if (X + v < a.nx) row[X + v] = acc[0][v];
+                    }
+                    if (a.dst_gw > 0 && (X < a.dst_gw || X + 3 >= a.nx - a.dst_gw ||
+                                         Y < a.dst_gw || Y >= a.ny - a.dst_gw))
+                        store_ghosts4(a, X, Y, acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                }
+            } else {
+                *reinterpret_cast<float4 *>(D + y * SP + cx) =
+                    make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+            }
+        };
+
+        int j = ya - R;
+        if (yb - ya >= 2 * R) {
+            // ramp-up: rows ya-R .. ya+R-1 feed only slots i >= 2R - u
+#pragma unroll
+            for (int u = 0; u < 2 * R; ++u, ++j) {
+                float seg[NSEG];
+                ST::load(col + j * SP, seg);
+#pragma unroll
+                for (int i = 0; i < W; ++i)
+                    if (i >= 2 * R - u) ST::slot(acc, seg, cf, i);
+                ST::shift(acc);
+            }
+            // steady rows: every slot, one finished output row each
+            const int jm = yb - R;
+#pragma unroll ST::UNR
+            for (; j < jm; ++j) {
+                float seg[NSEG];
+                ST::load(col + j * SP, seg);
+#pragma unroll
+                for (int i = 0; i < W; ++i) ST::slot(acc, seg, cf, i);
+                emit(j - R);
+                ST::shift(acc);
+            }
+            // ramp-down: the last 2R rows feed only slots i <= v
+#pragma unroll
+            for (int v = 2 * R - 1; v >= 0; --v, ++j) {
+                float seg[NSEG];
+                ST::load(col + j * SP, seg);
+#pragma unroll
+                for (int i = 0; i < W; ++i)
+                    if (i <= v) ST::slot(acc, seg, cf, i);
+                emit(j - R);
+                ST::shift(acc);
+            }
+        } else {
+            // short strip: plain window over all rows
+#pragma unroll 1
+            for (; j < yb + R; ++j) {
+                float seg[NSEG];
+                ST::load(col + j * SP, seg);
+#pragma unroll
+                for (int i = 0; i < W; ++i) ST::slot(acc, seg, cf, i);
+                if (j - R >= ya) emit(j - R);
+                ST::shift(acc);
+            }
+        }
+    }
+}
+
+// Plain radius-1 sweeps are memory-bound: keep three CTAs per SM resident.
+
+// b fused sweeps of one staged tile: stage -> work buffers -> destination.
+// The staged box covers rows [0, TY + 2H) and columns [0, TX + 2HX), with the
+// output tile at rows [H, H + TY) and columns [HX, HX + TX).
+template <int RB, int M, int PAT, class Coef>
+__device__ __forceinline__ void process_tile(const float *stage, float *work0, float *work1,
+                                             int TY, int H, int HX, int b, const Coef &cf,
+                                             const TileOut &o, int gx0, int gy0)
+{
+    constexpr int R = RB * M;
+    const int SP = TX + 2 * HX, ROWS = TY + 2 * H;
+    const float *src = stage;
+    for (int s = 0; s < b - 1; ++s) {
+        const int sh = (s + 1) * R;
+        const int c0 = HX - H + sh, c1 = SP - (HX - H) - sh;
+        float *dst = (s & 1) ? work1 : work0;
+        sweep_region<RB, M, PAT, false>(src, dst, SP, sh, ROWS - sh, c0 / 4, (c1 + 3) / 4, cf, o,
+                                        gx0, gy0);
+        __syncthreads();
+        src = dst;
+    }
+    sweep_region<RB, M, PAT, true>(src, nullptr, SP, H, H + TY, HX / 4, (HX + TX) / 4, cf, o, gx0,
+                                   gy0);
+}
+
+}  // namespace tile2d
+}  // namespace sg
