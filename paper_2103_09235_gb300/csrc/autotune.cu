@@ -1,0 +1,208 @@
+// Autotuner for stencil_run with fold_m = 0: times candidate (engine, m, b,
+// tile_y) configurations on the plan's own grid and keeps the fastest.
+//
+// The paper leaves the choice of blocking sizes and unrolling factor to hand
+// tuning and names automatic tuning as future work (Section 4.1).  Candidates
+// are pruned with the paper's scalar profitability index (Section 3.2,
+// Eq. pi): a fold depth m is tried only if P = |C(E)| / |C(E_lambda)| >= 1.
+// The choice is cached in the plan and in a line-per-entry JSON file keyed by
+// (ndim, shape, radius, pattern, coefficient hash, dtype, GPU name, library
+// version): $STENCIL_TUNE_CACHE, else $HOME/.cache/stencil_gb300/tune.jsonl.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <sys/stat.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+extern "C" stencil_status_t stencil_fold_cost(int ndim, int radius, const double *coeffs, int m,
+                                              int64_t *out);
+
+namespace sg {
+
+namespace {
+
+constexpr const char *kLibVersion = "1";
+
+struct Cand {
+    int engine;  // 0 CUDA core, 1 tensor core
+    int m, b, ty;
+};
+
+uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+std::string cache_key(const stencil_plan_s *p)
+{
+    cudaDeviceProp prop;
+    memset(&prop, 0, sizeof(prop));
+    cudaGetDeviceProperties(&prop, p->device);
+    char buf[512];
+    const uint64_t h = fnv1a(p->coeffs.data(), p->coeffs.size() * sizeof(double));
+    snprintf(buf, sizeof(buf), "%d|%lld,%lld,%lld|%d|%d|%016llx|%d|%d|%s|%s", p->ndim,
+             (long long)p->shape[0], (long long)p->shape[1], (long long)p->shape[2], p->r,
+             p->pattern, (unsigned long long)h, (int)p->dtype, p->precision, prop.name,
+             kLibVersion);
+    return buf;
+}
+
+std::string cache_path()
+{
+    const char *e = getenv("STENCIL_TUNE_CACHE");
+    if (e && *e) return e;
+    const char *home = getenv("HOME");
+    if (!home || !*home) return "";
+    std::string d = std::string(home) + "/.cache";
+    mkdir(d.c_str(), 0755);
+    d += "/stencil_gb300";
+    mkdir(d.c_str(), 0755);
+    return d + "/tune.jsonl";
+}
+
+bool cache_lookup(const std::string &key, Cand *c)
+{
+    const std::string path = cache_path();
+    if (path.empty()) return false;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    const std::string needle = "\"key\": \"" + key + "\"";
+    while (fgets(line, sizeof(line), f)) {
+        if (!strstr(line, needle.c_str())) continue;
+        Cand t;
+        const char *q = strstr(line, "\"engine\": ");
+        if (q && sscanf(q, "\"engine\": %d, \"m\": %d, \"b\": %d, \"tile_y\": %d", &t.engine, &t.m,
+                        &t.b, &t.ty) == 4) {
+            *c = t;  // the last entry for a key wins
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &key, const Cand &c, double gstencil)
+{
+    const std::string path = cache_path();
+    if (path.empty()) return;
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"engine\": %d, \"m\": %d, \"b\": %d, \"tile_y\": %d, \"gstencil_s\": %.1f}\n",
+            key.c_str(), c.engine, c.m, c.b, c.ty, gstencil);
+    fclose(f);
+}
+
+}  // namespace
+
+stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
+{
+    const std::string key = cache_key(p);
+    Cand best{0, 1, 1, 0};
+    if (cache_lookup(key, &best)) {
+        p->tuned_engine = best.engine;
+        p->tuned_m = best.m;
+        p->tuned_b = best.b;
+        p->tuned_ty = best.ty;
+        return STENCIL_OK;
+    }
+    // candidate list
+    const int nmin = p->ndim == 1 ? p->nx : std::min(p->nx, p->ndim == 3 ? std::min(p->ny, p->nz) : p->ny);
+    std::vector<Cand> cands;
+    for (int m = 1; m <= 8; ++m) {
+        const int R = m * p->r;
+        if (2 * R + 1 > nmin || R > kGhost) break;
+        if (m > 1) {
+            int64_t cost[2];
+            if (stencil_fold_cost(p->ndim, p->r, p->coeffs.data(), m, cost) != STENCIL_OK ||
+                cost[0] < cost[1])
+                continue;  // P = |C(E)| / |C(E_lambda)| < 1: folding is not profitable
+        }
+        if (p->ndim == 1) {
+            if (m <= 4 && sweep1d_supported(R, p->dtype == STENCIL_F64))
+                for (int b : {16, 32, 64}) cands.push_back({0, m, b, 0});
+        } else if (p->ndim == 3) {
+            if (sweep3d_supported(p->r, m, p->pattern)) cands.push_back({0, m, 1, 0});
+        } else {
+            if (sweep2d_supported(p->r, m, p->pattern))
+                for (int b : {1, 2, 3, 4, 6, 8})
+                    if (b * R <= std::min(kGhost, nmin) && (m > 1 || b <= 8))
+                        for (int ty : {32, 64, 96}) cands.push_back({0, m, b, ty});
+            if (m > 1 && p->precision != STENCIL_PREC_FP32 && tc2d_supported(R))
+                cands.push_back({1, m, 1, 0});
+        }
+    }
+    if (cands.empty()) cands.push_back({0, 1, 1, 0});
+    // timing on scratch copies of a seeded-free grid (all ones keeps values finite)
+    const size_t esz = p->dtype == STENCIL_F64 ? 8 : 4;
+    const size_t npts = (size_t)p->nx * p->ny * p->nz;
+    void *din = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc(&din, npts * esz);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, npts * esz);
+    if (e == cudaSuccess) e = cudaMemsetAsync(din, 0, npts * esz, s);
+    if (e != cudaSuccess) {
+        if (din) cudaFree(din);
+        return cuda_fail(e, "autotune scratch");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved_prec = p->precision, saved_b = p->block_b, saved_ty = p->tile_y;
+    const int saved_graph = p->use_graph;
+    p->use_graph = 0;  // tuning runs are not worth capturing
+    const int64_t T = 48;
+    double best_rate = -1.0;
+    for (const Cand &c : cands) {
+        p->precision = c.engine == 1 ? (saved_prec ? saved_prec : STENCIL_PREC_BF16X3) : STENCIL_PREC_FP32;
+        p->block_b = c.b;
+        p->tile_y = c.ty;
+        stencil_status_t st = STENCIL_OK;
+        auto once = [&]() {
+            if (p->ndim == 1) return run1d(p, din, dout, T, c.m, s);
+            if (p->ndim == 3) return run3d(p, (const float *)din, (float *)dout, T, c.m, s);
+            return run2d(p, (const float *)din, (float *)dout, T, c.m, s);
+        };
+        st = once();  // warm-up (also builds panels, maps and configs)
+        if (st != STENCIL_OK) continue;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 2 && st == STENCIL_OK; ++k) st = once();
+        cudaEventRecord(e1, s);
+        if (st != STENCIL_OK || cudaEventSynchronize(e1) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = ms > 0 ? 2.0 * (double)npts * T / (ms * 1e-3) / 1e9 : 0.0;
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = c;
+        }
+    }
+    p->precision = saved_prec;
+    p->block_b = saved_b;
+    p->tile_y = saved_ty;
+    p->use_graph = saved_graph;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(din);
+    cudaFree(dout);
+    cudaGetLastError();
+    p->tuned_engine = best.engine;
+    p->tuned_m = best.m;
+    p->tuned_b = best.b;
+    p->tuned_ty = best.ty;
+    cache_store(key, best, best_rate);
+    return STENCIL_OK;
+}
+
+}  // namespace sg

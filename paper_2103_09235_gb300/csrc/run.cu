@@ -52,7 +52,20 @@ void clear_graphs(stencil_plan_s *p)
 stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, int m,
                        cudaStream_t s)
 {
-    if (m == 0) m = 1;
+    const int saved_b = p->block_b;
+    struct RestoreB {
+        stencil_plan_s *p;
+        int b;
+        ~RestoreB() { p->block_b = b; }
+    } restore_b{p, saved_b};
+    if (m == 0) {
+        if (p->tuned_m == 0 && p->autotune) {
+            stencil_status_t st = autotune2d(p, s);
+            if (st != STENCIL_OK) return st;
+        }
+        m = p->tuned_m > 0 ? p->tuned_m : 1;
+        if (p->block_b == 0 && p->tuned_b > 0) p->block_b = p->tuned_b;
+    }
     const bool f64 = p->dtype == STENCIL_F64;
     const size_t esz = f64 ? 8 : 4;
     const int R = m * p->r;
@@ -205,6 +218,7 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
         int ty;
         ~Restore() { p->tile_y = ty; }
     } restore{p, p->tile_y};
+    bool cuda_core_only = false;
     if (m == 0) {
         if (p->tuned_m == 0 && p->autotune) {
             stencil_status_t st = autotune2d(p, s);
@@ -217,11 +231,12 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
         m = p->tuned_m;
         if (b == 0) b = p->tuned_b;
         if (p->tile_y == 0) p->tile_y = p->tuned_ty;
+        cuda_core_only = p->tuned_engine == 0;
     }
 
     // any folded 2D stencil fits the Toeplitz contraction (a star's folded
     // diamond just leaves zero weights in the panels)
-    if (m > 1 && p->precision != STENCIL_PREC_FP32)
+    if (m > 1 && p->precision != STENCIL_PREC_FP32 && !cuda_core_only)
         return run2d_tc(p, in, out, T, m, s);
     const int R = m * p->r;
     const int nmin = std::min(p->nx, p->ny);

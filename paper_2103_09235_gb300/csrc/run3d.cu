@@ -61,7 +61,13 @@ static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int 
 stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
                        cudaStream_t s)
 {
-    if (m == 0) m = 1;
+    if (m == 0) {
+        if (p->tuned_m == 0 && p->autotune) {
+            stencil_status_t st = autotune2d(p, s);
+            if (st != STENCIL_OK) return st;
+        }
+        m = p->tuned_m > 0 ? p->tuned_m : 1;
+    }
     const int R = m * p->r;
     const int nmin = std::min(p->nx, std::min(p->ny, p->nz));
     if (2 * R + 1 > nmin || R > kGhost) {

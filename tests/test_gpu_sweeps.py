@@ -294,3 +294,22 @@ def test_sweep3d_parity(env, shape, kind, r, T, m):
     ref = oracle.run(x.astype(np.float64), c, T)
     check(y, ref)
     assert info["m"] == m
+
+
+@pytest.mark.parametrize("shape,kind", [((300, 520), "star"), ((260, 300), "box"), ((6000,), "box"),
+                                        ((40, 36, 70), "star")])
+def test_autotune_choice_is_correct_and_cached(env, shape, kind, tmp_path, monkeypatch):
+    """fold_m = 0 times candidates, runs the fastest and caches the choice on disk."""
+    torch, binding, oracle = env
+    monkeypatch.setenv("STENCIL_TUNE_CACHE", str(tmp_path / "tune.jsonl"))
+    c = synth.dyadic_coeffs(27, len(shape), 1, kind)
+    x = synth.grid(28, shape, np.float32)
+    y, info = gpu_run(env, shape, c, x, 37, 0)
+    check(y, oracle.run(x.astype(np.float64), c, 37))
+    assert info["m"] >= 1
+    lines = (tmp_path / "tune.jsonl").read_text().strip().splitlines()
+    assert len(lines) == 1 and '"m": %d' % info["m"] in lines[0]
+    y2, info2 = gpu_run(env, shape, c, x, 37, 0)      # a new plan hits the file cache
+    assert info2["m"] == info["m"]
+    assert len((tmp_path / "tune.jsonl").read_text().strip().splitlines()) == 1
+    assert np.array_equal(y, y2)
