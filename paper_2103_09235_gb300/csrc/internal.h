@@ -54,6 +54,7 @@ struct Sweep2DArgs {
     int halo_x;        // H rounded up to a multiple of 4 (16-byte TMA column alignment)
     int map_x0, map_y0;  // tensor-map coordinates of the interior origin
     int buf_floats;    // floats between consecutive shared-memory buffers
+    int nstages;       // TMA stages in flight per CTA (2..6)
     float *dst;        // destination interior origin
     int64_t dst_py;    // destination row stride (elements)
     int dst_gw;        // ghost band of the destination to refresh (0 = dense output)
@@ -65,7 +66,7 @@ struct Sweep2DArgs {
 };
 
 bool sweep2d_supported(int rb, int m, int pattern);
-size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats);
+size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats, int nstages = 2);
 int sweep2d_ctas_per_sm(int rb, int m, int pattern, size_t smem);
 cudaError_t launch_sweep2d(int rb, int m, int pattern, const CUtensorMap &map,
                            const Sweep2DArgs &a, int grid, size_t smem, cudaStream_t s);

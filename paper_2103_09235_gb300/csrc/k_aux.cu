@@ -2,6 +2,8 @@
 // builder (the m-fold convolution power of Section 3.2), the FP64 relative-L2
 // reduction, the grid mean used by the tensor-core path, and tensor-map
 // encoding.
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -14,20 +16,32 @@ __device__ __forceinline__ int wrap_idx(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-// dst (padded, ghost band gw) <- src (dense).  One thread per padded point.
+// dst (padded, ghost band gw) <- src (dense).  One CTA per padded row
+// (z, y): the wrapped source row is found once, the interior is copied with
+// 16-byte accesses when the rows allow it, and the 2*gwx ghost columns of the
+// row are copied element by element.
 __global__ void k_import(float *__restrict__ origin, int64_t py, int64_t pz, int nx, int ny,
-                         int nz, int gwx, int gwy, int gwz, const float *__restrict__ src)
+                         int nz, int gwx, int gwy, int gwz, const float *__restrict__ src,
+                         int vec4)
 {
-    const int wx = nx + 2 * gwx, wy = ny + 2 * gwy, wz = nz + 2 * gwz;
-    const long long total = (long long)wx * wy * wz;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % wx) - gwx;
-        const long long r = i / wx;
-        const int y = (int)(r % wy) - gwy;
-        const int z = (int)(r / wy) - gwz;
-        const int sx = wrap_idx(x, nx), sy = wrap_idx(y, ny), sz = wrap_idx(z, nz);
-        origin[z * pz + y * py + x] = src[((long long)sz * ny + sy) * nx + sx];
+    const int wy = ny + 2 * gwy, wz = nz + 2 * gwz;
+    for (long long row = blockIdx.x; row < (long long)wy * wz; row += gridDim.x) {
+        const int y = (int)(row % wy) - gwy;
+        const int z = (int)(row / wy) - gwz;
+        const int sy = wrap_idx(y, ny), sz = wrap_idx(z, nz);
+        const float *srow = src + ((long long)sz * ny + sy) * nx;
+        float *drow = origin + z * pz + y * py;
+        if (vec4) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(srow);
+            float4 *d4 = reinterpret_cast<float4 *>(drow);
+            for (int i = threadIdx.x; i < nx / 4; i += blockDim.x) d4[i] = s4[i];
+        } else {
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) drow[i] = srow[i];
+        }
+        for (int i = threadIdx.x; i < 2 * gwx; i += blockDim.x) {
+            const int x = i < gwx ? i - gwx : nx + (i - gwx);
+            drow[x] = srow[wrap_idx(x, nx)];
+        }
     }
 }
 
@@ -161,8 +175,13 @@ int sm_count()
 cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_t s)
 {
     const int gwx = gw, gwy = P.ndim >= 2 ? gw : 0, gwz = P.ndim >= 3 ? gw : 0;
-    k_import<<<sm_count() * 8, 256, 0, s>>>(P.origin, P.py, P.pz, P.nx, P.ny, P.nz, gwx, gwy, gwz,
-                                            src);
+    // 16-byte interior copies need 16-byte aligned rows on both sides
+    const int vec4 = (P.nx % 4 == 0) && ((uintptr_t)src % 16 == 0) && (P.py % 4 == 0) &&
+                     ((uintptr_t)P.origin % 16 == 0);
+    const long long rows = (long long)(P.ny + 2 * gwy) * (P.nz + 2 * gwz);
+    const int grid = (int)std::min<long long>(rows, (long long)sm_count() * 16);
+    k_import<<<grid, 256, 0, s>>>(P.origin, P.py, P.pz, P.nx, P.ny, P.nz, gwx, gwy, gwz, src,
+                                  vec4);
     return cudaGetLastError();
 }
 

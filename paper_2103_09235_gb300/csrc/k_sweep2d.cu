@@ -3,9 +3,9 @@
 //
 // One persistent CTA walks its share of 128 x tile_y output tiles.  For every
 // tile one TMA box brings the tile plus a halo of H = b*m*r cells (columns
-// rounded up to 4) from the padded source grid into shared memory; the next
-// tile's box is already in flight while this one is computed (two stages,
-// one mbarrier each).  Sweeps 1..b-1 run shared memory to shared memory on a
+// rounded up to 4) from the padded source grid into shared memory; a ring of
+// 2-6 stages (one mbarrier each) keeps the next tiles' boxes in flight while
+// this one is computed.  Sweeps 1..b-1 run shared memory to shared memory on a
 // region that shrinks by R per sweep (overlapped tiles: the rim is computed
 // redundantly, the GPU analogue of Section 3.4's time-loop fusion inside a
 // tile); the last sweep writes the tile to global memory with 16-byte stores
@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(NT, min_blocks<RB, M>())
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *base = reinterpret_cast<float *>(smem + 1024) + BUF_PAD;
-    // buffers: stage 0, stage 1 (TMA targets), work 0, work 1 (intermediate sweeps)
+    // buffers: NS TMA stages, then work 0 and work 1 (intermediate sweeps)
+    const int NS = a.nstages;
     auto buf = [&](int k) { return base + k * a.buf_floats; };
 
     const int TY = a.tile_y, H = a.halo, HX = a.halo_x;
@@ -46,8 +47,7 @@ __global__ void __launch_bounds__(NT, min_blocks<RB, M>())
 
     if (tid == 0) {
         prefetch_tensormap(&map);
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -61,26 +61,37 @@ __global__ void __launch_bounds__(NT, min_blocks<RB, M>())
     int tile = blockIdx.x;
     // (fault_withhold_copy is a test hook: the first copy is never issued, so
     // the bounded wait below must run out and report a timeout)
-    if (tid == 0 && tile < a.ntiles && !a.fault_withhold_copy) issue(tile, 0);
+    // prologue: the first NS-1 tiles of this CTA are requested at once
+    if (tid == 0)
+        for (int k = 0; k < NS - 1; ++k) {
+            const int t = tile + k * gridDim.x;
+            if (t < a.ntiles && !(k == 0 && a.fault_withhold_copy)) issue(t, k);
+        }
 
     for (int i = 0; tile < a.ntiles; ++i, tile += gridDim.x) {
-        const int nxt = tile + gridDim.x;
-        if (tid == 0 && nxt < a.ntiles) issue(nxt, (i + 1) & 1);
+        // keep NS-1 tiles in flight: request the one NS-1 ahead into the stage
+        // the previous tile released
+        const int ahead = tile + (NS - 1) * gridDim.x;
+        if (tid == 0 && ahead < a.ntiles) issue(ahead, (i + NS - 1) % NS);
 
-        const bool ok = mbar_wait_bounded(&bars[i & 1], (i >> 1) & 1, a.wait_ns);
+        const bool ok = mbar_wait_bounded(&bars[i % NS], (i / NS) & 1, a.wait_ns);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 record_status(a.status, DEV_TIMEOUT);
-                // let the copy already issued for the next tile land before exiting
-                if (nxt < a.ntiles) mbar_wait_bounded(&bars[(i + 1) & 1], ((i + 1) >> 1) & 1, a.wait_ns);
+                // let the copies already requested land before exiting
+                for (int k = 1; k < NS; ++k) {
+                    const int q = i + k;
+                    if (tile + k * gridDim.x < a.ntiles)
+                        mbar_wait_bounded(&bars[q % NS], (q / NS) & 1, a.wait_ns);
+                }
             }
             return;
         }
 
         const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
         const TileOut o{a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, a.dst_vec4};
-        process_tile<RB, M, PAT>(buf(i & 1), buf(2), buf(3), TY, H, HX, a.b, ParamCoef{a.c}, o,
-                                 tx * TX - HX, ty * TY - H);
+        process_tile<RB, M, PAT>(buf(i % NS), buf(NS), buf(NS + 1), TY, H, HX, a.b,
+                                 ParamCoef{a.c}, o, tx * TX - HX, ty * TY - H);
         __syncthreads();
     }
 }
@@ -138,12 +149,12 @@ bool sweep2d_supported(int rb, int m, int pattern)
     return false;
 }
 
-size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats)
+size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats, int nstages)
 {
     const int H = b * R, HX = round_up(H, 4);
     const int SP = TX + 2 * HX, ROWS = tile_y + 2 * H;
     const int bf = round_up(SP * ROWS + 2 * BUF_PAD, 32);
-    const int nbuf = 2 + (b >= 3 ? 2 : (b == 2 ? 1 : 0));
+    const int nbuf = nstages + (b >= 3 ? 2 : (b == 2 ? 1 : 0));
     if (buf_floats) *buf_floats = bf;
     return 1024 + static_cast<size_t>(nbuf) * bf * 4;
 }

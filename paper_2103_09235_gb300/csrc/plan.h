@@ -24,7 +24,7 @@ struct stencil_plan_s {
     int precision = STENCIL_PREC_FP32;
     int block_b = 0;
     int tile_y = 0;
-    int tc_tile_n = 64;
+    int stages = 0;  // TMA stages per CTA of the 2D sweep (0 = automatic)
     int tc_center = 1;
     int tc_tma_store = 1;
     int autotune = 1;
@@ -48,7 +48,7 @@ struct stencil_plan_s {
     // cached launch facts
     int sm_count = 0, max_smem = 0;
     struct PassCfg {
-        int ty, bf, grid;
+        int ty, bf, grid, nstages;
         size_t smem;
     };
     std::map<std::tuple<int, int, int>, PassCfg> pass_cfg;  // (m, b, tile_y option)

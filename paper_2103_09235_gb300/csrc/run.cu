@@ -138,7 +138,7 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
 stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
                                       stencil_plan_s::PassCfg *cfg)
 {
-    auto key = std::make_tuple(m, b, p->tile_y);
+    auto key = std::make_tuple(m, b, p->tile_y * 8 + p->stages);
     auto it = p->pass_cfg.find(key);
     if (it != p->pass_cfg.end()) {
         *cfg = it->second;
@@ -147,12 +147,15 @@ stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
     ensure_device_facts(p);
     const int R = m * p->r;
     const int H = b * R;
-    int ty = p->tile_y > 0 ? p->tile_y : 64;
+    // plain single sweeps are memory-bound: small tiles, four in flight per
+    // CTA; temporally blocked passes keep taller tiles and double buffering
+    int ty = p->tile_y > 0 ? p->tile_y : (b == 1 ? 32 : 64);
+    const int ns = p->stages > 0 ? p->stages : (b == 1 ? 4 : 2);
     int bf = 0;
-    size_t smem = sweep2d_smem_bytes(ty, b, R, &bf);
+    size_t smem = sweep2d_smem_bytes(ty, b, R, &bf, ns);
     while ((smem > (size_t)p->max_smem || ty + 2 * H > 256) && ty > 16) {
         ty -= 8;
-        smem = sweep2d_smem_bytes(ty, b, R, &bf);
+        smem = sweep2d_smem_bytes(ty, b, R, &bf, ns);
     }
     if (smem > (size_t)p->max_smem) {
         set_error("2D sweep: halo %d needs too much shared memory", H);
@@ -161,6 +164,7 @@ stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
     const int ntiles = ceil_div(p->nx, kTileX2D) * ceil_div(p->ny, ty);
     const int occ = std::max(1, sweep2d_ctas_per_sm(p->r, m, p->pattern, smem));
     cfg->ty = ty;
+    cfg->nstages = ns;
     cfg->bf = bf;
     cfg->smem = smem;
     cfg->grid = std::min(ntiles, occ * p->sm_count);
@@ -190,6 +194,7 @@ stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int 
     a.map_x0 = src.gx;
     a.map_y0 = src.gy;
     a.buf_floats = cfg.bf;
+    a.nstages = cfg.nstages;
     a.dst = dst;
     a.dst_py = dst_py;
     a.dst_gw = dst_gw;

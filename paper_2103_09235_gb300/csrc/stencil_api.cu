@@ -261,9 +261,9 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "tile_y")) {
         if (v != 0 && (v < 8 || v > 192)) goto bad;
         p->tile_y = (int)v;
-    } else if (!strcmp(key, "tc_tile_n")) {
-        if (v != 32 && v != 64 && v != 128) goto bad;
-        p->tc_tile_n = (int)v;
+    } else if (!strcmp(key, "stages")) {
+        if (v < 0 || v > 6 || v == 1) goto bad;
+        p->stages = (int)v;
     } else if (!strcmp(key, "tc_center")) {
         if (v != 0 && v != 1) goto bad;
         p->tc_center = (int)v;
