@@ -119,13 +119,16 @@ struct Strip {
     }
 };
 
-static __device__ __noinline__ void store_ghosts4(const TileOut &a, int X, int Y, float v0, float v1,
-                                           float v2, float v3)
+// Ghost copies of four outputs; scalar arguments, so that the caller's
+// descriptor stays in registers instead of being spilled for an address.
+static __device__ __noinline__ void store_ghosts4(float *dst, int64_t py, int nx, int ny, int gw,
+                                                  int X, int Y, float v0, float v1, float v2,
+                                                  float v3)
 {
-    const float v[4] = {v0, v1, v2, v3};
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (X + k < a.nx) store_point(a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, X + k, Y, v[k]);
+    if (X < nx) store_point(dst, py, nx, ny, gw, X, Y, v0);
+    if (X + 1 < nx) store_point(dst, py, nx, ny, gw, X + 1, Y, v1);
+    if (X + 2 < nx) store_point(dst, py, nx, ny, gw, X + 2, Y, v2);
+    if (X + 3 < nx) store_point(dst, py, nx, ny, gw, X + 3, Y, v3);
 }
 
 // One sweep over output rows [r0, r1) and 4-column strips [k0, k1) of a
@@ -179,7 +182,8 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
                     }
                     if (a.dst_gw > 0 && (X < a.dst_gw || X + 3 >= a.nx - a.dst_gw ||
                                          Y < a.dst_gw || Y >= a.ny - a.dst_gw))
-                        store_ghosts4(a, X, Y, acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                        store_ghosts4(a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, X, Y, acc[0][0],
+                                      acc[0][1], acc[0][2], acc[0][3]);
                 }
             } else {
                 *reinterpret_cast<float4 *>(D + y * SP + cx) =
