@@ -1,0 +1,141 @@
+"""Parity at the full benchmark sizes, in the launch configurations the bench
+times.
+
+Every output is compared with the FP64 oracle: the plain time loop where the
+host finishes it in seconds (1D 2^20 x 100 steps), otherwise the oracle's
+per-Fourier-mode closed form (spectral_run), itself pinned against the time
+loop by the CPU tests.  Tolerance: relative L2 <= 1e-5 (FP32 / BF16x3 paths)
+and <= 1e-12 (FP64).
+"""
+
+import numpy as np
+import pytest
+
+from paper_2103_09235_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+BASE = synth.BASE_SEED
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod):
+    import torch
+    from paper_2103_09235_gb300 import build, binding
+    build.build()
+    assert torch.cuda.is_available()
+    torch.cuda.init()
+    return torch, binding, oracle_mod
+
+
+def run(env, shape, c, x, T, m, **opts):
+    torch, binding, _ = env
+    plan = binding.Plan(shape, c, "f64" if x.dtype == np.float64 else "f32")
+    for k, v in opts.items():
+        plan.set_option(k, v)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, T, fold_m=m)
+    plan.sync()
+    y = yd.cpu().numpy()
+    plan.close()
+    del xd, yd
+    torch.cuda.empty_cache()
+    return y
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_heat1d_2pow20(env, dt):
+    """1D 3-point heat stencil, N = 2^20, T = 100, plain steps (FP32 and FP64)."""
+    _, _, oracle = env
+    x = synth.grid(BASE + 1, (1 << 20,), np.float64 if dt == "f64" else np.float32)
+    c = synth.heat1d_coeffs()
+    y = run(env, x.shape, c, x, 100, 1)
+    ref = oracle.run(x.astype(np.float64), c, 100)
+    assert oracle.rel_l2(y, ref) <= (1e-12 if dt == "f64" else 1e-5)
+
+
+@pytest.fixture(scope="module")
+def star4096(env):
+    _, _, oracle = env
+    x = synth.grid(BASE + 2, (4096, 4096), np.float32)
+    c = synth.dyadic_coeffs(BASE + 2, 2, 1, "star")
+    return x, c, oracle.spectral_run(x.astype(np.float64), c, 1000)
+
+
+@pytest.mark.parametrize("m,opts", [(1, {"block_b": 1}), (4, {"block_b": 2}), (3, {"block_b": 3}),
+                                    (4, {"precision": 1})])
+def test_star4096_T1000(env, star4096, m, opts):
+    """2D 5-point star 4096^2, T = 1000: plain, folded + blocked, and tensor-core folded."""
+    _, _, oracle = env
+    x, c, ref = star4096
+    y = run(env, x.shape, c, x, 1000, m, **opts)
+    err = oracle.rel_l2(y, ref)
+    print("star4096 m=%d %s rel-L2 %.3e" % (m, opts, err))
+    assert err <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def box8192(env):
+    _, _, oracle = env
+    x = synth.grid(BASE + 3, (8192, 8192), np.float32)
+    c = synth.dyadic_coeffs(BASE + 3, 2, 1, "box")
+    return x, c, oracle.spectral_run(x.astype(np.float64), c, 512)
+
+
+@pytest.mark.parametrize("m,opts", [(1, {"block_b": 1}), (4, {"precision": 1}), (8, {"precision": 1}),
+                                    (4, {"precision": 2})])
+def test_box8192_T512(env, box8192, m, opts):
+    """2D 9-point box 8192^2, T = 512: plain, and folded m = 4 (9x9) / m = 8 (17x17)
+    on the tensor cores with the BF16 hi/lo split; the single-product BF16 error
+    is reported, not asserted."""
+    _, _, oracle = env
+    x, c, ref = box8192
+    y = run(env, x.shape, c, x, 512, m, **opts)
+    err = oracle.rel_l2(y, ref)
+    print("box8192 m=%d %s rel-L2 %.3e" % (m, opts, err))
+    if opts.get("precision") == 2:
+        assert err > 1e-7
+    else:
+        assert err <= 1e-5
+
+
+@pytest.mark.parametrize("shape,kind,m,seed", [((512, 512, 512), "star", 2, 4),
+                                               ((256, 256, 256), "box", 2, 5),
+                                               ((256, 256, 256), "box", 1, 5)])
+def test_3d_T200(env, shape, kind, m, seed):
+    """3D 7-point star 512^3 and 27-point box 256^3, T = 200, folded m = 2 (and plain)."""
+    _, _, oracle = env
+    x = synth.grid(BASE + seed, shape, np.float32)
+    c = synth.dyadic_coeffs(BASE + seed, 3, 1, kind)
+    y = run(env, shape, c, x, 200, m)
+    ref = oracle.spectral_run(x.astype(np.float64), c, 200)
+    err = oracle.rel_l2(y, ref)
+    print("3d %s %s m=%d rel-L2 %.3e" % (shape, kind, m, err))
+    assert err <= 1e-5
+
+
+def test_batched_256(env):
+    """256 grids, sides uniform in [64, 1024], star/box 50/50, T uniform in [10, 500],
+    one persistent launch; every grid within 1e-5 of its own closed form."""
+    torch, binding, oracle = env
+    grids = synth.batched_workload(BASE + 6)
+    plans, xs, ys, Ts, data = [], [], [], [], []
+    for g in grids:
+        c = synth.dyadic_coeffs(g["coeff_seed"], 2, 1, g["kind"])
+        x = synth.grid(g["value_seed"], g["shape"], np.float32)
+        plans.append(binding.Plan(g["shape"], c))
+        xs.append(torch.from_numpy(x).cuda())
+        ys.append(torch.empty_like(xs[-1]))
+        Ts.append(g["T"])
+        data.append((x, c, g["T"]))
+    binding.run_batched(plans, xs, ys, Ts)
+    plans[0].sync()
+    worst = 0.0
+    for (x, c, T), y in zip(data, ys):
+        ref = oracle.spectral_run(x.astype(np.float64), c, T)
+        worst = max(worst, oracle.rel_l2(y.cpu().numpy(), ref))
+    print("batched 256 worst rel-L2 %.3e" % worst)
+    assert worst <= 1e-5
+    for p in plans:
+        p.close()
