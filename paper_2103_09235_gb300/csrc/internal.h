@@ -177,7 +177,7 @@ struct TC2DArgs {
     int map_x0, map_y0;     // tensor-map coordinates of the interior origin
     const double *mean_sum; // grid sum; mu = mean_sum[0] * inv_n (null: mu = 0)
     double inv_n;
-    float sum_c;            // sum of the split weights actually applied
+    float sum_c;            // FP64 sum of the folded weights (rounded to FP32)
     const uint16_t *panels; // (2R+1) panels, tc2d panel layout
     float *dst;
     int64_t dst_py;
@@ -191,7 +191,7 @@ bool tc2d_supported(int R);
 size_t tc2d_smem_bytes(int R, bool tma_store);
 // Builds the (2R+1) BF16 Toeplitz panels of folded weights cm ((2R+1)^2,
 // row-major (dy, dx)) with the hi/lo split and the mass correction; returns
-// the sum of the applied weights.
+// the FP64 sum of cm, which the epilogue multiplies by mu.
 double tc2d_build_panels(const double *cm, int R, uint16_t *host_out);
 cudaError_t launch_tc2d(const CUtensorMap &map, const CUtensorMap &dmap, const TC2DArgs &a,
                         int grid, size_t smem, cudaStream_t s);
