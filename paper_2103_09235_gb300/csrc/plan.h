@@ -41,7 +41,7 @@ struct stencil_plan_s {
     void *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
     double *d_acc = nullptr;                  // small FP64 reduction buffer
     std::map<int, uint16_t *> panels;         // tensor-core Toeplitz panels by m
-    std::map<int, double> panel_sum;          // sum of the applied split weights by m
+    std::map<int, double> panel_sum;          // FP64 sum of the folded weights by m
     std::map<std::tuple<const void *, int, int, int>, CUtensorMap> maps;
     size_t scratch_bytes = 0;
 

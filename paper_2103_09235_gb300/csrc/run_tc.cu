@@ -21,7 +21,7 @@ static stencil_status_t tc_panels(stencil_plan_s *p, int m, const uint16_t **out
         if (st != STENCIL_OK) return st;
         const int R = m * p->r;
         std::vector<uint16_t> host((size_t)(2 * R + 1) * kTcPanelElems);
-        const double applied = tc2d_build_panels(cm->data(), R, host.data());
+        const double wsum = tc2d_build_panels(cm->data(), R, host.data());
         uint16_t *d = nullptr;
         cudaError_t e = cudaMalloc(&d, host.size() * sizeof(uint16_t));
         if (e == cudaSuccess)
@@ -32,7 +32,7 @@ static stencil_status_t tc_panels(stencil_plan_s *p, int m, const uint16_t **out
         }
         p->scratch_bytes += host.size() * sizeof(uint16_t);
         it = p->panels.emplace(m, d).first;
-        p->panel_sum[m] = applied;
+        p->panel_sum[m] = wsum;
     }
     *out = it->second;
     *sum = p->panel_sum[m];
