@@ -2,8 +2,8 @@
 //
 // A CTA owns a 64 x 16 (x, y) column of the grid and a chunk of z planes.
 // Input planes arrive one per step by TMA (a 2D view of the padded 3D grid:
-// plane z, rows y-R .. y+16+R) into a four-slot ring, three planes ahead of
-// the compute.  Each thread owns a 4-point strip of one row and keeps a
+// plane z, rows y-R .. y+16+R) into an eight-slot ring, seven planes ahead of
+// the compute (a plane slab is small, so depth, not size, hides latency).  Each thread owns a 4-point strip of one row and keeps a
 // register window of 2R+1 output planes: input plane z is read once from
 // shared memory and added, with the weights of plane offset a, into the
 // partial sums of output planes z - a (the counterparts of Section 3.3,
@@ -16,7 +16,7 @@
 namespace sg {
 namespace {
 
-constexpr int TX3 = 64, TY3 = 16, NT3 = 256, NSLOT = 4;
+constexpr int TX3 = 64, TY3 = 16, NT3 = 256, NSLOT = 8;
 
 __host__ __device__ constexpr int cabs_div3(int v, int d) { return ((v < 0 ? -v : v) + d - 1) / d; }
 
@@ -92,6 +92,10 @@ __global__ void __launch_bounds__(NT3)
     const int strip = tid % (TX3 / 4), yr = tid / (TX3 / 4);
     const int X = x0 + 4 * strip, Y = y0 + yr;
     const bool live = (Y < a.ny) && (X < a.nx);
+    const int gw = a.dst_gw;
+    // columns and row of this thread away from the edges and the ghost band
+    const bool fast_xy = live && a.dst_vec4 && X + 3 < a.nx &&
+                         (gw == 0 || (X >= gw && X + 3 < a.nx - gw && Y >= gw && Y < a.ny - gw));
 
     float acc[W][4];
 #pragma unroll
@@ -140,7 +144,10 @@ __global__ void __launch_bounds__(NT3)
             }
         }
         const int zo = zin0 + p - R;  // output plane completed by this input plane
-        if (zo >= z0 && live) {
+        if (zo >= z0 && fast_xy && (gw == 0 || (zo >= gw && zo < a.nz - gw))) {
+            *reinterpret_cast<float4 *>(a.dst + zo * a.dst_pz + Y * a.dst_py + X) =
+                make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+        } else if (zo >= z0 && live) {
             float *row = a.dst + zo * a.dst_pz + Y * a.dst_py;
             if (a.dst_vec4 && X + 3 < a.nx) {
                 *reinterpret_cast<float4 *>(row + X) =

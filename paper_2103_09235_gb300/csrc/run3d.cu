@@ -26,8 +26,12 @@ static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int 
     a.tiles_x = ceil_div(p->nx, kTX3);
     a.tiles_y = ceil_div(p->ny, kTY3);
     a.ntiles_xy = a.tiles_x * a.tiles_y;
-    a.zchunk = kZChunk;
-    a.zchunks = ceil_div(p->nz, kZChunk);
+    // z chunks of 64 planes, shortened (down to 16) until the launch covers
+    // four CTAs per SM; each chunk re-reads 2R planes of halo
+    int zc = kZChunk;
+    while (zc > 16 && (int64_t)a.ntiles_xy * ceil_div(p->nz, zc) < 4 * p->sm_count) zc /= 2;
+    a.zchunk = zc;
+    a.zchunks = ceil_div(p->nz, zc);
     a.ntiles = a.ntiles_xy * a.zchunks;
     a.tile_y = kTY3;
     a.halo_x = round_up(R, 4);

@@ -131,6 +131,27 @@ static __device__ __noinline__ void store_ghosts4(float *dst, int64_t py, int nx
     if (X + 3 < nx) store_point(dst, py, nx, ny, gw, X + 3, Y, v3);
 }
 
+// Four outputs of row Y starting at column X, with every check: grid bounds,
+// 16-byte alignment and the ghost copies.  Out of line: only edge strips and
+// ragged tiles come here.
+static __device__ __noinline__ void store_checked4(float *dst, int64_t py, int nx, int ny, int gw,
+                                                   int vec4, int X, int Y, float v0, float v1,
+                                                   float v2, float v3)
+{
+    if (Y >= ny || X >= nx) return;
+    float *row = dst + Y * py;
+    if (vec4 && X + 3 < nx) {
+        *reinterpret_cast<float4 *>(row + X) = make_float4(v0, v1, v2, v3);
+    } else {
+        row[X] = v0;
+        if (X + 1 < nx) row[X + 1] = v1;
+        if (X + 2 < nx) row[X + 2] = v2;
+        if (X + 3 < nx) row[X + 3] = v3;
+    }
+    if (gw > 0 && (X < gw || X + 3 >= nx - gw || Y < gw || Y >= ny - gw))
+        store_ghosts4(dst, py, nx, ny, gw, X, Y, v0, v1, v2, v3);
+}
+
 // One sweep over output rows [r0, r1) and 4-column strips [k0, k1) of a
 // shared-memory buffer S (row pitch SP).  FINAL writes to global memory;
 // otherwise the outputs go to the same coordinates of buffer D.
@@ -167,27 +188,35 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
 
+        // Output rows are emitted in order ya, ya+1, ...: a strip whose rows and
+        // columns are all interior and away from the ghost band (the common
+        // case) stores each row with one 16-byte store and a pointer step;
+        // any other strip takes the checked path.
+        float *orow = nullptr;
+        bool fast = false;
+        if constexpr (FINAL) {
+            const int X = gx0 + cx, Y0 = gy0 + ya, Y1 = gy0 + yb;
+            const int gw = a.dst_gw;
+            fast = a.dst_vec4 && X + 3 < a.nx && Y1 <= a.ny &&
+                   (gw == 0 || (X >= gw && X + 3 < a.nx - gw && Y0 >= gw && Y1 <= a.ny - gw));
+            orow = a.dst + (int64_t)Y0 * a.dst_py + X;
+        } else {
+            orow = D + ya * SP + cx;
+        }
         auto emit = [&](int y) {
             if constexpr (FINAL) {
-                const int X = gx0 + cx, Y = gy0 + y;
-                if (Y < a.ny && X < a.nx) {
-                    float *row = a.dst + Y * a.dst_py;
-                    if (a.dst_vec4 && X + 3 < a.nx) {
-                        *reinterpret_cast<float4 *>(row + X) =
-                            make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < 4; ++v)
-                            if (X + v < a.nx) row[X + v] = acc[0][v];
-                    }
-                    if (a.dst_gw > 0 && (X < a.dst_gw || X + 3 >= a.nx - a.dst_gw ||
-                                         Y < a.dst_gw || Y >= a.ny - a.dst_gw))
-                        store_ghosts4(a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, X, Y, acc[0][0],
-                                      acc[0][1], acc[0][2], acc[0][3]);
-                }
+                if (fast)
+                    *reinterpret_cast<float4 *>(orow) =
+                        make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                else
+                    store_checked4(a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, a.dst_vec4, gx0 + cx,
+                                   gy0 + y, acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                orow += a.dst_py;
             } else {
-                *reinterpret_cast<float4 *>(D + y * SP + cx) =
+                (void)y;
+                *reinterpret_cast<float4 *>(orow) =
                     make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                orow += SP;
             }
         };
 
