@@ -174,6 +174,77 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_runs(torch, stream, flush, fn, reps=3, warm=1):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def measure_variants(torch, binding, dev, stream, flush, args):
+    """GStencil/s of the plain baseline and the other configurations."""
+    out = {}
+
+    def single(name, shape, kind, seed, T, m, ndim=2, **opts):
+        c = synth.dyadic_coeffs(seed, ndim, 1, kind)
+        x = torch.from_numpy(synth.grid(seed, shape, np.float32)).to(dev)
+        y = torch.empty_like(x)
+        plan = binding.Plan(shape, c)
+        for k, v in opts.items():
+            plan.set_option(k, v)
+        ms = _time_runs(torch, stream, flush, lambda: plan.run(x, y, T, fold_m=m, stream=stream))
+        plan.sync(stream)
+        out[name] = {"gstencil_s": float(np.prod(shape)) * T / (ms * 1e-3) / 1e9, "ms": ms,
+                     "m": plan.get("last_m"), "b": plan.get("last_b"),
+                     "engine": "tensor-core" if plan.get("last_engine") else "cuda-core"}
+        plan.close()
+        del x, y
+        torch.cuda.empty_cache()
+
+    s2 = synth.BASE_SEED + 2
+    single("star4096_T1000_plain_fp32", (4096, 4096), "star", s2, 1000, 1, block_b=1)
+    single("star4096_T1000_tc_bf16x3_m4", (4096, 4096), "star", s2, 1000, 4, precision=1)
+    s3 = synth.BASE_SEED + 3
+    single("box8192_T512_plain_fp32", (8192, 8192), "box", s3, 512, 1, block_b=1)
+    single("box8192_T512_cuda_core_m2b2", (8192, 8192), "box", s3, 512, 2, block_b=2)
+    single("box8192_T512_tc_bf16x3_m4", (8192, 8192), "box", s3, 512, 4, precision=1)
+    single("box8192_T512_tc_bf16x3_m8", (8192, 8192), "box", s3, 512, 8, precision=1)
+    single("star512cube_T200_plain", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1, ndim=3)
+    single("star512cube_T200_m2", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 2, ndim=3)
+    single("box256cube_T200_plain", (256, 256, 256), "box", synth.BASE_SEED + 5, 200, 1, ndim=3)
+    single("box256cube_T200_m2", (256, 256, 256), "box", synth.BASE_SEED + 5, 200, 2, ndim=3)
+    # 256 independent grids in one persistent launch
+    grids = synth.batched_workload(synth.BASE_SEED + 6)
+    plans, xs, ys, Ts = [], [], [], []
+    for g in grids:
+        c = synth.dyadic_coeffs(g["coeff_seed"], 2, 1, g["kind"])
+        plans.append(binding.Plan(g["shape"], c))
+        xs.append(torch.from_numpy(synth.grid(g["value_seed"], g["shape"], np.float32)).to(dev))
+        ys.append(torch.empty_like(xs[-1]))
+        Ts.append(g["T"])
+    ms = _time_runs(torch, stream, flush,
+                    lambda: binding.run_batched(plans, xs, ys, Ts, stream=stream))
+    plans[0].sync(stream)
+    upd = sum(float(np.prod(g["shape"])) * g["T"] for g in grids)
+    out["batched256_T10to500"] = {"gstencil_s": upd / (ms * 1e-3) / 1e9, "ms": ms,
+                                  "grids": len(grids), "updates": upd}
+    for p in plans:
+        p.close()
+    del xs, ys
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_2103_09235_gb300 import build, binding
@@ -296,14 +367,12 @@ def run_gpu(args):
         e2e_total = float(t.item())
     e2e = ws * npts * T_STEPS * args.steps / (e2e_total * 1e-3) / 1e9
 
-    # --- plain FP32 sweep beside it (the comparison the metric names)
+    # --- the other configurations of the workload family, each timed the same
+    # way (events around whole runs, L2 flushed between runs); reported beside
+    # the headline, not folded into it
     variants = {}
     if not args.no_variants:
-        pplan = make_plan(1, 1)
-        pt, _ = timed_steps(pplan, 1, 200, 3, 2)
-        variants["plain_fp32_m1_b1"] = npts * 200 / (statistics.median(pt) * 1e-3) / 1e9
-        pplan.close()
-
+        variants = measure_variants(torch, binding, dev, stream, flush, args)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         Ts = calibrate_oracle_steps(args.cpu_seconds)
@@ -347,8 +416,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="star4096", choices=sorted(CONFIGS))
-    ap.add_argument("--fold-m", type=int, default=4)
-    ap.add_argument("--block-b", type=int, default=2)
+    ap.add_argument("--fold-m", type=int, default=0,
+                    help="fold depth; 0 = the library's autotuner chooses m, b and the tile")
+    ap.add_argument("--block-b", type=int, default=0)
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="0 = FP32 CUDA cores, 1 = BF16x3 tensor cores, 2 = BF16x1")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
