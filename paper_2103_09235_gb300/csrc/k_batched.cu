@@ -56,72 +56,110 @@ __device__ __forceinline__ void run_variant(int variant, const float *stage, flo
     }
 }
 
+__device__ __forceinline__ bool dep_met(const BatchArgs &a, const BatchPass &ps)
+{
+    return ps.dep < 0 || ld_acquire(&a.done[ps.dep]) >= a.passes[ps.dep].ntiles;
+}
+
+// Bounded wait for an item's dependency; false when the limit ran out.
+__device__ __forceinline__ bool dep_wait(const BatchArgs &a, const BatchPass &ps)
+{
+    if (dep_met(a, ps)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!dep_met(a, ps))
+        if (globaltimer_ns() - t0 > a.wait_ns) return false;
+    return true;
+}
+
+__device__ __forceinline__ void issue_item(const BatchArgs &a, int idx, float *stage,
+                                           uint64_t *bar)
+{
+    const BatchItem item = a.items[idx];
+    const BatchPass &ps = a.passes[item.pass];
+    const int tx = item.tile % ps.tiles_x, ty = item.tile / ps.tiles_x;
+    fence_proxy_async_global();  // other CTAs' stores, acquired above, before the copy reads them
+    const uint32_t bytes = (uint32_t)((kTileX2D + 2 * ps.HX) * (a.tile_y + 2 * ps.H) * 4);
+    mbar_arrive_expect_tx(bar, bytes);
+    tma_load_2d(stage, &a.maps[ps.map], bar, ps.map_x0 + tx * kTileX2D - ps.HX,
+                ps.map_y0 + ty * a.tile_y - ps.H);
+}
+
+// Each CTA keeps two items in flight: while it computes the current one, the
+// next item's tile is already being copied into the other stage if that
+// item's dependency is met; otherwise it is requested once the current item
+// is done (the current item may be one of its dependencies).
 __global__ void __launch_bounds__(kThreads2D, 1) k_batched(const __grid_constant__ BatchArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    int *s_item = reinterpret_cast<int *>(smem + 64);
-    int *s_ok = reinterpret_cast<int *>(smem + 68);
-    float *cs = reinterpret_cast<float *>(smem + 128);  // up to kMaxTaps2D weights
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // bar[0], bar[1]: one per stage
+    int *ctl = reinterpret_cast<int *>(smem + 64);       // cur, next, issued, ok
+    float *cs = reinterpret_cast<float *>(smem + 128);   // up to kMaxTaps2D weights
     float *base = reinterpret_cast<float *>(smem + 128 + round_up(kMaxTaps2D * 4, 128)) + BUF_PAD;
-    float *stage = base, *w0 = base + a.buf_floats, *w1 = base + 2 * a.buf_floats;
+    auto stage = [&](int i) { return base + i * a.buf_floats; };  // two TMA stages
+    float *w0 = base + 2 * a.buf_floats, *w1 = base + 3 * a.buf_floats;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_mbar_init();
+        int ok = 1;
+        const int cur = atomicAdd(a.next, 1);
+        if (cur < a.nitems) {
+            ok = dep_wait(a, a.passes[a.items[cur].pass]) ? 1 : 0;
+            if (ok) issue_item(a, cur, stage(0), &bar[0]);
+        }
+        ctl[0] = cur;
+        ctl[3] = ok;
     }
     __syncthreads();
 
-    for (uint32_t it = 0;; ++it) {
-        if (tid == 0) *s_item = atomicAdd(a.next, 1);
-        __syncthreads();
-        const int idx = *s_item;
-        if (idx >= a.nitems) break;
-        const BatchItem item = a.items[idx];
-        const BatchPass &ps = a.passes[item.pass];
-        for (int k = tid; k < ps.ncoef; k += kThreads2D) cs[k] = a.coefs[ps.coef + k];
-        const int tx = item.tile % ps.tiles_x, ty = item.tile / ps.tiles_x;
+    for (uint32_t k = 0;; ++k) {
+        const int cur = ctl[0];
+        if (cur >= a.nitems) break;
+        if (!ctl[3]) {
+            if (tid == 0) record_status(a.status, DEV_TIMEOUT);
+            break;
+        }
+        const int st = k & 1;
         if (tid == 0) {
-            int ok = 1;
-            if (ps.dep >= 0) {
-                const int need = a.passes[ps.dep].ntiles;
-                if (ld_acquire(&a.done[ps.dep]) < need) {
-                    const uint64_t t0 = globaltimer_ns();
-                    while (ld_acquire(&a.done[ps.dep]) < need) {
-                        if (globaltimer_ns() - t0 > a.wait_ns) {
-                            ok = 0;
-                            break;
-                        }
-                    }
-                }
+            const int nxt = atomicAdd(a.next, 1);
+            int issued = 0;
+            if (nxt < a.nitems && dep_met(a, a.passes[a.items[nxt].pass])) {
+                issue_item(a, nxt, stage(st ^ 1), &bar[st ^ 1]);
+                issued = 1;
             }
-            if (ok) {
-                fence_proxy_async_global();
-                const uint32_t bytes = (uint32_t)((kTileX2D + 2 * ps.HX) * (a.tile_y + 2 * ps.H) * 4);
-                mbar_arrive_expect_tx(bar, bytes);
-                tma_load_2d(stage, &a.maps[ps.map], bar, ps.map_x0 + tx * kTileX2D - ps.HX,
-                            ps.map_y0 + ty * a.tile_y - ps.H);
-            }
-            *s_ok = ok;
+            ctl[1] = nxt;
+            ctl[2] = issued;
         }
-        __syncthreads();
-        if (!*s_ok) {
-            if (tid == 0) record_status(a.status, DEV_TIMEOUT);
-            break;
-        }
-        const bool landed = mbar_wait_bounded(bar, it & 1, a.wait_ns);
+        const BatchItem item = a.items[cur];
+        const BatchPass &ps = a.passes[item.pass];
+        for (int i = tid; i < ps.ncoef; i += kThreads2D) cs[i] = a.coefs[ps.coef + i];
+        const bool landed = mbar_wait_bounded(&bar[st], (k >> 1) & 1, a.wait_ns);
         if (__syncthreads_or(!landed)) {
-            if (tid == 0) record_status(a.status, DEV_TIMEOUT);
+            if (tid == 0) {
+                record_status(a.status, DEV_TIMEOUT);
+                if (ctl[2]) mbar_wait_bounded(&bar[st ^ 1], ((k + 1) >> 1) & 1, a.wait_ns);
+            }
             break;
         }
+        const int tx = item.tile % ps.tiles_x, ty = item.tile / ps.tiles_x;
         const TileOut o{ps.dst, ps.dst_py, ps.nx, ps.ny, ps.dst_gw, ps.dst_vec4};
-        run_variant(ps.variant, stage, w0, w1, a.tile_y, ps.H, ps.HX, ps.b, SmemCoef{cs}, o,
+        run_variant(ps.variant, stage(st), w0, w1, a.tile_y, ps.H, ps.HX, ps.b, SmemCoef{cs}, o,
                     tx * kTileX2D - ps.HX, ty * a.tile_y - ps.H);
         __syncthreads();
         if (tid == 0) {
             __threadfence();
-            atomicAdd(&a.done[item.pass], 1);
+            atomicAdd(&a.done[item.pass], 1);  // publish this tile
+            const int nxt = ctl[1];
+            int ok = 1;
+            if (nxt < a.nitems && !ctl[2]) {
+                ok = dep_wait(a, a.passes[a.items[nxt].pass]) ? 1 : 0;
+                if (ok) issue_item(a, nxt, stage(st ^ 1), &bar[st ^ 1]);
+            }
+            ctl[0] = nxt;
+            ctl[3] = ok;
         }
+        __syncthreads();
     }
 }
 
@@ -134,7 +172,8 @@ bool batched_variant_supported(int rb, int m, int pattern)
 
 size_t batched_smem_bytes(int buf_floats)
 {
-    return 128 + round_up(kMaxTaps2D * 4, 128) + (size_t)3 * buf_floats * 4 + 2 * BUF_PAD * 4;
+    // two stages and two work buffers
+    return 128 + round_up(kMaxTaps2D * 4, 128) + (size_t)4 * buf_floats * 4 + 2 * BUF_PAD * 4;
 }
 
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s)

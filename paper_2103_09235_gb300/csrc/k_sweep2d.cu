@@ -26,11 +26,18 @@ namespace {
 
 using namespace tile2d;
 
+// Threads per CTA and resident CTAs per SM of each instance: plain radius-1
+// sweeps are memory-bound and keep three 256-thread CTAs per SM; folded
+// sweeps of at most 41 taps fit 512 threads (<= 128 registers each) in the
+// one CTA per SM their shared memory allows, doubling the warps that hide
+// FMA and shared-load latency; wider stencils keep 256 threads.
+template <int RB, int M, int PAT>
+constexpr int threads2d() { return RB * M == 1 ? 256 : (Strip<RB, M, PAT>::NNZ <= 41 ? 512 : 256); }
 template <int RB, int M>
 constexpr int min_blocks() { return RB * M == 1 ? 3 : 1; }
 
 template <int RB, int M, int PAT>
-__global__ void __launch_bounds__(NT, min_blocks<RB, M>())
+__global__ void __launch_bounds__(threads2d<RB, M, PAT>(), min_blocks<RB, M>())
     k_sweep2d(const __grid_constant__ CUtensorMap map, const __grid_constant__ Sweep2DArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -117,7 +124,7 @@ cudaError_t launch_t(const CUtensorMap &map, const Sweep2DArgs &a, int grid, siz
 {
     cudaError_t e = prepare_t<RB, M, PAT>();
     if (e != cudaSuccess) return e;
-    k_sweep2d<RB, M, PAT><<<grid, NT, smem, s>>>(map, a);
+    k_sweep2d<RB, M, PAT><<<grid, threads2d<RB, M, PAT>(), smem, s>>>(map, a);
     return cudaGetLastError();
 }
 
@@ -126,7 +133,8 @@ int occupancy_t(size_t smem)
 {
     if (prepare_t<RB, M, PAT>() != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep2d<RB, M, PAT>, NT, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep2d<RB, M, PAT>,
+                                                      threads2d<RB, M, PAT>(), smem) !=
         cudaSuccess)
         return 0;
     return n;

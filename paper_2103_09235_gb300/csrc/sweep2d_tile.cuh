@@ -170,11 +170,12 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
     const int nr = r1 - r0;
     if (nsx <= 0 || nr <= 0) return;
     // row groups: as many as the threads allow, each at least 2R rows tall
-    int G = NT / nsx;
+    const int nthr = blockDim.x;  // 256 or 512, chosen per kernel instance
+    int G = nthr / nsx;
     G = max(1, min(G, nr / (2 * R)));
     const int items = nsx * G;
 
-    for (int it = threadIdx.x; it < items; it += NT) {
+    for (int it = threadIdx.x; it < items; it += nthr) {
         const int k = k0 + it % nsx;
         const int g = it / nsx;
         const int ya = r0 + (g * nr) / G;
