@@ -21,6 +21,8 @@ namespace {
 
 using namespace tile2d;
 
+constexpr int kThreadsBatched = 512;
+
 struct SmemCoef {
     const float *c;
     __device__ __forceinline__ float operator()(int k) const { return c[k]; }
@@ -50,8 +52,6 @@ __device__ __forceinline__ void run_variant(int variant, const float *stage, flo
     case PAT_STAR * 8 + 4: process_tile<1, 4, PAT_STAR>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
     case PAT_BOX * 8 + 1: process_tile<1, 1, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
     case PAT_BOX * 8 + 2: process_tile<1, 2, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
-    case PAT_BOX * 8 + 3: process_tile<1, 3, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
-    case PAT_BOX * 8 + 4: process_tile<1, 4, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
     default: break;
     }
 }
@@ -88,7 +88,7 @@ __device__ __forceinline__ void issue_item(const BatchArgs &a, int idx, float *s
 // next item's tile is already being copied into the other stage if that
 // item's dependency is met; otherwise it is requested once the current item
 // is done (the current item may be one of its dependencies).
-__global__ void __launch_bounds__(kThreads2D, 1) k_batched(const __grid_constant__ BatchArgs a)
+__global__ void __launch_bounds__(kThreadsBatched, 1) k_batched(const __grid_constant__ BatchArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // bar[0], bar[1]: one per stage
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads2D, 1) k_batched(const __grid_constant
         }
         const BatchItem item = a.items[cur];
         const BatchPass &ps = a.passes[item.pass];
-        for (int i = tid; i < ps.ncoef; i += kThreads2D) cs[i] = a.coefs[ps.coef + i];
+        for (int i = tid; i < ps.ncoef; i += kThreadsBatched) cs[i] = a.coefs[ps.coef + i];
         const bool landed = mbar_wait_bounded(&bar[st], (k >> 1) & 1, a.wait_ns);
         if (__syncthreads_or(!landed)) {
             if (tid == 0) {
@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kThreads2D, 1) k_batched(const __grid_constant
 
 bool batched_variant_supported(int rb, int m, int pattern)
 {
-    return rb == 1 && m >= 1 && m <= 4 && (pattern == PAT_STAR || pattern == PAT_BOX);
+    // folded stencils of at most 41 taps: the kernel runs 512 threads per CTA
+    return rb == 1 && m >= 1 && ((pattern == PAT_STAR && m <= 4) || (pattern == PAT_BOX && m <= 2));
 }
 
 size_t batched_smem_bytes(int buf_floats)
@@ -185,7 +186,7 @@ cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream
         return cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
     }();
     if (once != cudaSuccess) return once;
-    k_batched<<<grid, kThreads2D, smem, s>>>(a);
+    k_batched<<<grid, kThreadsBatched, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -193,7 +194,7 @@ int batched_ctas_per_sm(size_t smem)
 {
     int n = 0;
     cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched, kThreads2D, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched, kThreadsBatched, smem) != cudaSuccess)
         return 0;
     return n;
 }

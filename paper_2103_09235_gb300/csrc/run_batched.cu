@@ -36,7 +36,9 @@ void choose_mb(const stencil_plan_s *p, int req_m, int *m_out, int *b_out)
     int m = req_m > 0 ? req_m : (p->pattern == PAT_STAR ? 3 : 2);
     int b = p->block_b > 0 ? p->block_b : (p->pattern == PAT_STAR ? 3 : 2);
     if (req_m == 1 && p->block_b == 0) b = 1;
-    while (m > 1 && (2 * m * p->r + 1 > nmin || m * p->r > kGhost)) --m;
+    while (m > 1 && (2 * m * p->r + 1 > nmin || m * p->r > kGhost ||
+                     !batched_variant_supported(p->r, m, p->pattern)))
+        --m;
     const int max_halo = std::min(kGhost, nmin);
     while (b > 1 && b * m * p->r > max_halo) --b;
     *m_out = m;
