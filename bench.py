@@ -64,6 +64,26 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def load_tensor_peak():
+    """Dense BF16 TFLOP/s measured with cuBLAS over seconds (MEASURED_PEAKS.json)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"])
+    except Exception:
+        return 1700.0
+
+
+def fp32_peak_tflops():
+    """CUDA-core FP32 peak: 152 SMs x 128 FMA/clk x 2 flop x the measured max SM clock."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
 class ClockSampler:
     """Samples nvidia-smi SM clocks and throttle reasons while running."""
 
@@ -333,6 +353,18 @@ def run_gpu(args):
     peak, peak_kind = load_peaks()
     alg_bytes = 2 * 4 * npts  # one read and one write of the grid per pass
     achieved = alg_bytes / (pass_ms * 1e-3) / 1e9
+    # algorithmic flops of one pass: b sweeps of the folded stencil, each
+    # 2*nnz(c^(m)) - 1 flops per point (its own multiply-adds, not the
+    # redundant rim, the Toeplitz zeros or the BF16 split)
+    nnz = int(np.count_nonzero(plan.folded_coeffs(used_m)))
+    alg_flops = npts * used_b * (2 * nnz - 1)
+    tflops = alg_flops / (pass_ms * 1e-3) / 1e12
+    if engine == "tensor-core":
+        bound, r_ach, r_peak, r_unit = "tensor", tflops, load_tensor_peak(), "TFLOP/s"
+    elif used_m == 1 and used_b == 1:
+        bound, r_ach, r_peak, r_unit = "hbm", achieved, peak, "GB/s"
+    else:
+        bound, r_ach, r_peak, r_unit = "alu", tflops, fp32_peak_tflops(), "TFLOP/s"
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -391,11 +423,16 @@ def run_gpu(args):
                        "precision": ["fp32", "bf16x3", "bf16x1"][args.precision],
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind,
+            "roofline": {"bound": bound, "achieved": r_ach, "peak": r_peak, "unit": r_unit,
+                         "frac": r_ach / r_peak, "traffic": traffic,
+                         "peak_source": peak_kind if bound == "hbm" else
+                         ("MEASURED_PEAKS.json bf16_tflops_sustained" if bound == "tensor" else
+                          "152 SMs x 128 FP32 FMA/clk x 2 flop x measured max SM clock"),
                          "kernel": "k_tc2d" if engine == "tensor-core" else "k_sweep2d",
-                         "pass_ms": pass_ms, "alg_bytes_per_launch": alg_bytes},
+                         "pass_ms": pass_ms, "alg_bytes_per_launch": alg_bytes,
+                         "alg_flops_per_launch": alg_flops,
+                         "hbm_view": {"achieved_gbs": achieved, "peak_gbs": peak,
+                                      "frac": achieved / peak}},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(npts * 4),
                     "d2h_bytes_per_step": int(npts * 4)},
