@@ -1,9 +1,9 @@
 // 3D CUDA-core stencil sweeps (plain m = 1 and folded m > 1), streaming along z.
 //
 // A CTA owns a 64 x 16 (x, y) column of the grid and a chunk of z planes.
-// Input planes arrive one per step by TMA (a 2D view of the padded 3D grid:
-// plane z, rows y-R .. y+16+R) into an eight-slot ring, seven planes ahead of
-// the compute (a plane slab is small, so depth, not size, hides latency).  Each thread owns a 4-point strip of one row and keeps a
+// Input planes arrive four at a time: one 3D TMA box (x-HX .. x+64+HX,
+// y-R .. y+16+R, four planes) per stage of a three-stage ring, so the CTA
+// synchronises once per four planes.  Each thread owns a 4-point strip of one row and keeps a
 // register window of 2R+1 output planes: input plane z is read once from
 // shared memory and added, with the weights of plane offset a, into the
 // partial sums of output planes z - a (the counterparts of Section 3.3,
@@ -16,7 +16,7 @@
 namespace sg {
 namespace {
 
-constexpr int TX3 = 64, TY3 = 16, NT3 = 256, NSLOT = 8;
+constexpr int TX3 = 64, TY3 = 16, NT3 = 256, ZC = 4, NST = 3;
 
 __host__ __device__ constexpr int cabs_div3(int v, int d) { return ((v < 0 ? -v : v) + d - 1) / d; }
 
@@ -57,11 +57,12 @@ __global__ void __launch_bounds__(NT3)
     constexpr int NSEG = 4 + 2 * RP;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    float *slots = reinterpret_cast<float *>(smem + 1024);
+    float *stages = reinterpret_cast<float *>(smem + 1024);
     const int HX = a.halo_x;
     const int SP = TX3 + 2 * HX;   // shared row pitch
     const int ROWS = TY3 + 2 * R;
-    const uint32_t slot_bytes = (uint32_t)(SP * ROWS * 4);
+    const int plane = SP * ROWS;   // floats of one staged plane
+    const uint32_t chunk_bytes = (uint32_t)(plane * ZC * 4);
     const int tid = threadIdx.x;
 
     const int tile = blockIdx.x;
@@ -70,23 +71,22 @@ __global__ void __launch_bounds__(NT3)
     const int x0 = tx * TX3, y0 = ty * TY3;
     const int z0 = zc * a.zchunk, z1 = min(a.nz, z0 + a.zchunk);
     const int zin0 = z0 - R, nin = (z1 - z0) + 2 * R;  // input planes streamed
-    const int rows_per_plane = a.ny + 2 * a.map_y0;    // padded rows of one plane
+    const int nchunks = (nin + ZC - 1) / ZC;
 
     if (tid == 0) {
         prefetch_tensormap(&map);
-        for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](int p) {  // input plane index p (0-based in this chunk)
-        const int s = p % NSLOT;
-        const int z = zin0 + p;
-        const int row = (z + a.map_z0) * rows_per_plane + (a.map_y0 + y0 - R);
-        mbar_arrive_expect_tx(&bars[s], slot_bytes);
-        tma_load_2d(slots + s * a.buf_floats, &map, &bars[s], a.map_x0 + x0 - HX, row);
+    auto issue = [&](int c) {  // chunk c: input planes 4c .. 4c+3 of this CTA
+        const int s = c % NST;
+        mbar_arrive_expect_tx(&bars[s], chunk_bytes);
+        tma_load_3d(stages + s * a.buf_floats, &map, &bars[s], a.map_x0 + x0 - HX,
+                    a.map_y0 + y0 - R, a.map_z0 + zin0 + c * ZC);
     };
     if (tid == 0)
-        for (int p = 0; p < NSLOT - 1 && p < nin; ++p) issue(p);
+        for (int c = 0; c < NST && c < nchunks; ++c) issue(c);
 
     // thread -> (4-column strip, row) of the tile
     const int strip = tid % (TX3 / 4), yr = tid / (TX3 / 4);
@@ -103,75 +103,80 @@ __global__ void __launch_bounds__(NT3)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
 
-    for (int p = 0; p < nin; ++p) {
-        if (tid == 0 && p + NSLOT - 1 < nin) issue(p + NSLOT - 1);
-        const int s = p % NSLOT;
-        const bool ok = mbar_wait_bounded(&bars[s], (p / NSLOT) & 1, a.wait_ns);
+    for (int c = 0; c < nchunks; ++c) {
+        const int s = c % NST;
+        const bool ok = mbar_wait_bounded(&bars[s], (c / NST) & 1, a.wait_ns);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 record_status(a.status, DEV_TIMEOUT);
-                for (int q = p + 1; q < min(nin, p + NSLOT); ++q)
-                    mbar_wait_bounded(&bars[q % NSLOT], (q / NSLOT) & 1, a.wait_ns);
+                for (int q = c + 1; q < min(nchunks, c + NST); ++q)
+                    mbar_wait_bounded(&bars[q % NST], (q / NST) & 1, a.wait_ns);
             }
             return;
         }
-        const float *pl = slots + s * a.buf_floats + 4 * strip + HX - RP;
-        // this input plane feeds output plane z - R + i with plane offset a = R - i
+        const float *chunk = stages + s * a.buf_floats + 4 * strip + HX - RP;
+#pragma unroll 1
+        for (int q = 0; q < ZC; ++q) {
+            const int p = c * ZC + q;
+            if (p >= nin) break;
+            const float *pl = chunk + q * plane;
+            // this input plane feeds output plane z - R + i with plane offset R - i
 #pragma unroll
-        for (int dy = -R; dy <= R; ++dy) {
-            float seg[NSEG];
-            const float4 *rp = reinterpret_cast<const float4 *>(pl + (yr + R + dy) * SP);
+            for (int dy = -R; dy <= R; ++dy) {
+                float seg[NSEG];
+                const float4 *rp = reinterpret_cast<const float4 *>(pl + (yr + R + dy) * SP);
 #pragma unroll
-            for (int q = 0; q < NSEG / 4; ++q) {
-                const float4 t = rp[q];
-                seg[4 * q] = t.x;
-                seg[4 * q + 1] = t.y;
-                seg[4 * q + 2] = t.z;
-                seg[4 * q + 3] = t.w;
-            }
+                for (int k = 0; k < NSEG / 4; ++k) {
+                    const float4 t = rp[k];
+                    seg[4 * k] = t.x;
+                    seg[4 * k + 1] = t.y;
+                    seg[4 * k + 2] = t.z;
+                    seg[4 * k + 3] = t.w;
+                }
 #pragma unroll
-            for (int i = 0; i < W; ++i) {
-                const int az = R - i;
+                for (int i = 0; i < W; ++i) {
+                    const int az = R - i;
 #pragma unroll
-                for (int dx = -R; dx <= R; ++dx) {
-                    if (TP::nz(az, dy, dx)) {
-                        const float w = a.c[((az + R) * W + (dy + R)) * W + (dx + R)];
+                    for (int dx = -R; dx <= R; ++dx) {
+                        if (TP::nz(az, dy, dx)) {
+                            const float w = a.c[((az + R) * W + (dy + R)) * W + (dx + R)];
 #pragma unroll
-                        for (int v = 0; v < 4; ++v)
-                            acc[i][v] = fmaf(w, seg[v + dx + RP], acc[i][v]);
+                            for (int v = 0; v < 4; ++v)
+                                acc[i][v] = fmaf(w, seg[v + dx + RP], acc[i][v]);
+                        }
                     }
                 }
             }
-        }
-        const int zo = zin0 + p - R;  // output plane completed by this input plane
-        if (zo >= z0 && fast_xy && (gw == 0 || (zo >= gw && zo < a.nz - gw))) {
-            *reinterpret_cast<float4 *>(a.dst + zo * a.dst_pz + Y * a.dst_py + X) =
-                make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
-        } else if (zo >= z0 && live) {
-            float *row = a.dst + zo * a.dst_pz + Y * a.dst_py;
-            if (a.dst_vec4 && X + 3 < a.nx) {
-                *reinterpret_cast<float4 *>(row + X) =
+            const int zo = zin0 + p - R;  // output plane completed by this input plane
+            if (zo >= z0 && fast_xy && (gw == 0 || (zo >= gw && zo < a.nz - gw))) {
+                *reinterpret_cast<float4 *>(a.dst + zo * a.dst_pz + Y * a.dst_py + X) =
                     make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
-            } else {
+            } else if (zo >= z0 && live) {
+                float *row = a.dst + zo * a.dst_pz + Y * a.dst_py;
+                if (a.dst_vec4 && X + 3 < a.nx) {
+                    *reinterpret_cast<float4 *>(row + X) =
+                        make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                } else {
 #pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    if (X + v < a.nx) row[X + v] = acc[0][v];
-            }
-            if (a.dst_gw > 0 &&
-                (X < a.dst_gw || X + 3 >= a.nx - a.dst_gw || Y < a.dst_gw ||
-                 Y >= a.ny - a.dst_gw || zo < a.dst_gw || zo >= a.nz - a.dst_gw)) {
+                    for (int v = 0; v < 4; ++v)
+                        if (X + v < a.nx) row[X + v] = acc[0][v];
+                }
+                if (gw > 0 && (X < gw || X + 3 >= a.nx - gw || Y < gw || Y >= a.ny - gw ||
+                               zo < gw || zo >= a.nz - gw)) {
 #pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    if (X + v < a.nx) store_ghosts3(a, X + v, Y, zo, acc[0][v]);
+                    for (int v = 0; v < 4; ++v)
+                        if (X + v < a.nx) store_ghosts3(a, X + v, Y, zo, acc[0][v]);
+                }
             }
+#pragma unroll
+            for (int i = 0; i < W - 1; ++i)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
         }
-#pragma unroll
-        for (int i = 0; i < W - 1; ++i)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
-        __syncthreads();  // slot s is free for plane p + NSLOT
+        __syncthreads();  // stage s is free: request the chunk NST ahead into it
+        if (tid == 0 && c + NST < nchunks) issue(c + NST);
     }
 }
 
@@ -228,9 +233,9 @@ size_t sweep3d_smem_bytes(int tile_y, int R, int *buf_floats)
 {
     (void)tile_y;
     const int HX = round_up(R, 4);
-    const int bf = round_up((TX3 + 2 * HX) * (TY3 + 2 * R), 32);
+    const int bf = round_up((TX3 + 2 * HX) * (TY3 + 2 * R) * ZC, 32);
     if (buf_floats) *buf_floats = bf;
-    return 1024 + (size_t)NSLOT * bf * 4;
+    return 1024 + (size_t)NST * bf * 4;
 }
 
 int sweep3d_ctas_per_sm(int rb, int m, int pattern, size_t smem)

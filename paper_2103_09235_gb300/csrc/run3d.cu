@@ -49,13 +49,9 @@ static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int 
     a.status = p->d_status;
     a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
     for (size_t k = 0; k < c.size(); ++k) a.c[k] = (float)c[k];
-    // the padded 3D grid seen as one tall 2D array: plane z, row y is row
-    // (z + gz) * (ny + 2 gy) + y + gy
-    Padded view = src;
-    view.ndim = 2;
-    view.ny = (src.ny + 2 * src.gy) * (src.nz + 2 * src.gz) - 2 * src.gy;
-    const int box[2] = {kTX3 + 2 * a.halo_x, kTY3 + 2 * R};
-    const CUtensorMap *map = plan_map(p, view, box);
+    // one 3D box per stage: 64+2HX columns, 16+2R rows, 4 planes
+    const int box[3] = {kTX3 + 2 * a.halo_x, kTY3 + 2 * R, 4};
+    const CUtensorMap *map = plan_map(p, src, box);
     if (!map) return STENCIL_ERR_CUDA;
     cudaError_t e = launch_sweep3d(p->r, m, p->pattern, *map, a, a.ntiles, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "3D sweep launch");
