@@ -215,8 +215,8 @@ int occ3(size_t smem)
 }
 
 #define SG_SWEEP3D_LIST(X)                                                                 \
-    X(1, 1, PAT_STAR) X(1, 2, PAT_STAR) X(2, 1, PAT_STAR) X(1, 1, PAT_BOX) X(1, 2, PAT_BOX) \
-    X(2, 1, PAT_BOX)
+    X(1, 1, PAT_STAR) X(1, 2, PAT_STAR) X(1, 3, PAT_STAR) X(1, 4, PAT_STAR) X(2, 1, PAT_STAR) \
+    X(2, 2, PAT_STAR) X(1, 1, PAT_BOX) X(1, 2, PAT_BOX) X(2, 1, PAT_BOX)
 
 }  // namespace
 

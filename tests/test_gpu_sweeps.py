@@ -313,3 +313,12 @@ def test_autotune_choice_is_correct_and_cached(env, shape, kind, tmp_path, monke
     assert info2["m"] == info["m"]
     assert len((tmp_path / "tune.jsonl").read_text().strip().splitlines()) == 1
     assert np.array_equal(y, y2)
+
+
+@pytest.mark.parametrize("shape,T,m", [((70, 40, 66), 10, 3), ((40, 36, 70), 9, 4)])
+def test_sweep3d_deeper_folds(env, shape, T, m):
+    _, _, oracle = env
+    c = synth.dyadic_coeffs(3300, 3, 1, "star")
+    x = synth.grid(3301, shape, np.float32)
+    y, info = gpu_run(env, shape, c, x, T, m)
+    check(y, oracle.run(x.astype(np.float64), c, T))
