@@ -4,16 +4,27 @@
 // The host flattens every grid's time loop (its folded passes of b fused
 // sweeps, then its plain remainder passes, Section 3.4) into passes, and the
 // passes into a work list of (pass, tile) items ordered round by round: all
-// grids' first passes, then all grids' second passes, and so on.  Persistent
-// CTAs pop items from a device queue (one atomic counter).  Before loading
-// its tile a CTA waits, with a bounded spin, until every tile of the grid's
-// previous pass has been counted done; items only ever wait for items earlier
-// in the list, and every CTA is resident, so the queue cannot deadlock.  A
-// tile is the same TMA-staged, register-window, temporally blocked body as the
-// single-grid 2D sweep, with the grid's folded weights read from shared
-// memory.  Completion is published with a release fence and an atomic add;
-// the waiter acquires it and issues a proxy fence before its TMA load, so the
-// copy engine sees the other CTAs' stores.
+// grids' first passes, then all grids' second passes, and so on.
+//
+// A CTA is 15 consumer warps that run the tile body and one producer warp
+// (one active lane) that feeds them through a two-stage ring:
+//   producer: pop an item from the device queue (one atomic counter), wait
+//             (bounded) until every tile of the grid's previous pass is
+//             counted done, write the item's description into the stage's
+//             slot, and request the tile (2D TMA box) and the grid's folded
+//             weights (bulk copy) on the stage's "full" mbarrier;
+//   consumers: wait on "full", run the TMA-staged, register-window,
+//             temporally blocked tile body (the same one as the single-grid
+//             sweep, weights from shared memory), then release the stage on
+//             its "empty" mbarrier;
+//   producer: once a stage is released, publish its item (release fence and
+//             an atomic add on the pass's done counter).
+// Scheduling therefore never stalls the consumers: while they compute one
+// item, the next one's copies are in flight.  Items only wait for items
+// earlier in the list, every CTA is resident, and a producer that waits on a
+// dependency keeps publishing the item its consumers are finishing, so the
+// queue cannot deadlock.  Every wait is bounded; on expiry the CTA records a
+// timeout, lets its requested copies land and exits.
 #include "sweep2d_tile.cuh"
 
 namespace sg {
@@ -21,7 +32,24 @@ namespace {
 
 using namespace tile2d;
 
-constexpr int kThreadsBatched = 512;
+// 15 consumer warps and the producer: 16 warps keep four per SM sub-partition,
+// so every thread may hold 128 registers.
+constexpr int kConsumers = 480;                    // threads that run the tile body
+constexpr int kThreadsBatched = kConsumers + 32;   // plus the producer warp
+constexpr int kCoefSlot = 96;                      // floats of weights per stage (>= 81)
+using ConsumerSync = NamedSync<kConsumers>;
+
+// One stage's work description, written by the producer before its arrive on
+// the stage's full barrier.
+struct StageMeta {
+    float *dst;
+    long long dst_py;
+    int nx, ny, dst_gw, dst_vec4;
+    int variant, b, H, HX;
+    int gx0, gy0, vx, vy;
+    int stop;  // 0: an item; 1: the queue is empty; 2: a dependency wait ran out
+};
+static_assert(64 + 2 * sizeof(StageMeta) <= 256, "stage slots overlap the weights");
 
 struct SmemCoef {
     const float *c;
@@ -40,126 +68,179 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Runs the tile body of the variant (pattern, m); radius-1 base stencils.
-__device__ __forceinline__ void run_variant(int variant, const float *stage, float *w0, float *w1,
-                                            int TY, int H, int HX, int b, const SmemCoef &cf,
-                                            const TileOut &o, int gx0, int gy0)
+// OR of a predicate over the consumer threads (named barrier 1).
+__device__ __forceinline__ bool consumers_any(bool v)
 {
-    switch (variant) {
-    case PAT_STAR * 8 + 1: process_tile<1, 1, PAT_STAR>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
-    case PAT_STAR * 8 + 2: process_tile<1, 2, PAT_STAR>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
-    case PAT_STAR * 8 + 3: process_tile<1, 3, PAT_STAR>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
-    case PAT_STAR * 8 + 4: process_tile<1, 4, PAT_STAR>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
-    case PAT_BOX * 8 + 1: process_tile<1, 1, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
-    case PAT_BOX * 8 + 2: process_tile<1, 2, PAT_BOX>(stage, w0, w1, TY, H, HX, b, cf, o, gx0, gy0); break;
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kConsumers)
+        : "memory");
+    return r != 0;
+}
+
+// Runs the tile body of the variant (pattern, m); radius-1 base stencils.
+__device__ __forceinline__ void run_variant(const StageMeta &md, const float *stage, float *w0,
+                                            float *w1, int TY, const SmemCoef &cf)
+{
+    const TileOut o{md.dst, md.dst_py, md.nx, md.ny, md.dst_gw, md.dst_vec4};
+#define SG_BATCHED_CASE(P_, M_)                                                                 \
+    case P_ * 8 + M_:                                                                           \
+        process_tile<1, M_, P_, ConsumerSync>(stage, w0, w1, TY, md.H, md.HX, md.b, cf, o,      \
+                                              md.gx0, md.gy0, md.vx, md.vy);                    \
+        break;
+    switch (md.variant) {
+        SG_BATCHED_CASE(PAT_STAR, 1)
+        SG_BATCHED_CASE(PAT_STAR, 2)
+        SG_BATCHED_CASE(PAT_STAR, 3)
+        SG_BATCHED_CASE(PAT_STAR, 4)
+        SG_BATCHED_CASE(PAT_BOX, 1)
+        SG_BATCHED_CASE(PAT_BOX, 2)
     default: break;
+    }
+#undef SG_BATCHED_CASE
+}
+
+// The producer: one thread.  Stage s = k & 1 carries the CTA's k-th item.
+__device__ __forceinline__ void produce(const BatchArgs &a, uint64_t *full, uint64_t *empty,
+                                        StageMeta *meta, float *cslot, float *st0, float *st1)
+{
+    // per stage: the pass of the item it holds, not yet published (-1: none),
+    // and that item's number k (registers, selected by stage)
+    int pp0 = -1, pp1 = -1, pk0 = 0, pk1 = 0;
+    auto pend_pass = [&](int s) { return s ? pp1 : pp0; };
+    auto pend_k = [&](int s) { return s ? pk1 : pk0; };
+    auto hold = [&](int s, int pass, int k) {
+        if (s) {
+            pp1 = pass;
+            pk1 = k;
+        } else {
+            pp0 = pass;
+            pk0 = k;
+        }
+    };
+    auto publish = [&](int s) {
+        __threadfence();  // the consumers' stores, acquired through the empty barrier
+        atomicAdd(&a.done[pend_pass(s)], 1);
+        hold(s, -1, pend_k(s));
+    };
+    bool ok = true;
+    for (int k = 0;; ++k) {
+        const int s = k & 1;
+        if (k >= 2) {
+            // refill stage s only after the consumers released item k - 2
+            if (!mbar_wait_bounded(&empty[s], ((k - 2) >> 1) & 1, a.wait_ns)) {
+                ok = false;
+                break;
+            }
+            if (pend_pass(s) >= 0) publish(s);
+        }
+        StageMeta &md = meta[s];
+        const int idx = atomicAdd(a.next, 1);
+        if (idx >= a.nitems) {
+            md.stop = 1;
+            mbar_arrive(&full[s]);
+            break;
+        }
+        const BatchItem item = a.items[idx];
+        const BatchPass &ps = a.passes[item.pass];
+        if (ps.dep >= 0) {
+            const int need = a.passes[ps.dep].ntiles;
+            const int *cnt = &a.done[ps.dep];
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_acquire(cnt) < need) {
+                // the item the consumers are finishing may be one this item waits for
+                const int o = s ^ 1;
+                if (pend_pass(o) >= 0 && mbar_test_wait(&empty[o], (pend_k(o) >> 1) & 1)) publish(o);
+                if (globaltimer_ns() - t0 > a.wait_ns) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (!ok) {
+                md.stop = 2;
+                mbar_arrive(&full[s]);
+                break;
+            }
+        }
+        const int tx = item.tile % ps.tiles_x, ty = item.tile / ps.tiles_x;
+        md.dst = ps.dst;
+        md.dst_py = ps.dst_py;
+        md.nx = ps.nx;
+        md.ny = ps.ny;
+        md.dst_gw = ps.dst_gw;
+        md.dst_vec4 = ps.dst_vec4;
+        md.variant = ps.variant;
+        md.b = ps.b;
+        md.H = ps.H;
+        md.HX = ps.HX;
+        md.gx0 = tx * kTileX2D - ps.HX;
+        md.gy0 = ty * a.tile_y - ps.H;
+        md.vx = min(kTileX2D, ps.nx - tx * kTileX2D);
+        md.vy = min(a.tile_y, ps.ny - ty * a.tile_y);
+        md.stop = 0;
+        const uint32_t tile_bytes =
+            (uint32_t)((kTileX2D + 2 * ps.HX) * (a.tile_y + 2 * ps.H) * 4);
+        const uint32_t coef_bytes = (uint32_t)(((ps.ncoef + 3) & ~3) * 4);
+        fence_proxy_async_global();  // other CTAs' stores, acquired above, before the copy reads them
+        mbar_arrive_expect_tx(&full[s], tile_bytes + coef_bytes);
+        tma_load_2d(s ? st1 : st0, &a.maps[ps.map], &full[s], ps.map_x0 + tx * kTileX2D - ps.HX,
+                    ps.map_y0 + ty * a.tile_y - ps.H);
+        bulk_load(cslot + s * kCoefSlot, a.coefs + ps.coef, coef_bytes, &full[s]);
+        hold(s, item.pass, k);
+    }
+    if (!ok) record_status(a.status, DEV_TIMEOUT);
+    // publish what the consumers still finish; if they stopped, let the
+    // requested copies land before the CTA exits
+    for (int s = 0; s < 2; ++s) {
+        if (pend_pass(s) < 0) continue;
+        const uint32_t par = (pend_k(s) >> 1) & 1;
+        if (mbar_wait_bounded(&empty[s], par, a.wait_ns))
+            publish(s);
+        else
+            mbar_wait_bounded(&full[s], par, a.wait_ns);
     }
 }
 
-__device__ __forceinline__ bool dep_met(const BatchArgs &a, const BatchPass &ps)
-{
-    return ps.dep < 0 || ld_acquire(&a.done[ps.dep]) >= a.passes[ps.dep].ntiles;
-}
-
-// Bounded wait for an item's dependency; false when the limit ran out.
-__device__ __forceinline__ bool dep_wait(const BatchArgs &a, const BatchPass &ps)
-{
-    if (dep_met(a, ps)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    while (!dep_met(a, ps))
-        if (globaltimer_ns() - t0 > a.wait_ns) return false;
-    return true;
-}
-
-__device__ __forceinline__ void issue_item(const BatchArgs &a, int idx, float *stage,
-                                           uint64_t *bar)
-{
-    const BatchItem item = a.items[idx];
-    const BatchPass &ps = a.passes[item.pass];
-    const int tx = item.tile % ps.tiles_x, ty = item.tile / ps.tiles_x;
-    fence_proxy_async_global();  // other CTAs' stores, acquired above, before the copy reads them
-    const uint32_t bytes = (uint32_t)((kTileX2D + 2 * ps.HX) * (a.tile_y + 2 * ps.H) * 4);
-    mbar_arrive_expect_tx(bar, bytes);
-    tma_load_2d(stage, &a.maps[ps.map], bar, ps.map_x0 + tx * kTileX2D - ps.HX,
-                ps.map_y0 + ty * a.tile_y - ps.H);
-}
-
-// Each CTA keeps two items in flight: while it computes the current one, the
-// next item's tile is already being copied into the other stage if that
-// item's dependency is met; otherwise it is requested once the current item
-// is done (the current item may be one of its dependencies).
 __global__ void __launch_bounds__(kThreadsBatched, 1) k_batched(const __grid_constant__ BatchArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);  // bar[0], bar[1]: one per stage
-    int *ctl = reinterpret_cast<int *>(smem + 64);       // cur, next, issued, ok
-    float *cs = reinterpret_cast<float *>(smem + 128);   // up to kMaxTaps2D weights
-    float *base = reinterpret_cast<float *>(smem + 128 + round_up(kMaxTaps2D * 4, 128)) + BUF_PAD;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // full[2], then empty[2]
+    uint64_t *empty = full + 2;
+    StageMeta *meta = reinterpret_cast<StageMeta *>(smem + 64);  // one slot per stage
+    float *cslot = reinterpret_cast<float *>(smem + 256);      // kCoefSlot weights per stage
+    float *base = reinterpret_cast<float *>(smem + 1024) + BUF_PAD;
     auto stage = [&](int i) { return base + i * a.buf_floats; };  // two TMA stages
     float *w0 = base + 2 * a.buf_floats, *w1 = base + 3 * a.buf_floats;
     const int tid = threadIdx.x;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-        int ok = 1;
-        const int cur = atomicAdd(a.next, 1);
-        if (cur < a.nitems) {
-            ok = dep_wait(a, a.passes[a.items[cur].pass]) ? 1 : 0;
-            if (ok) issue_item(a, cur, stage(0), &bar[0]);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
         }
-        ctl[0] = cur;
-        ctl[3] = ok;
+        fence_mbar_init();
     }
     __syncthreads();
-
-    for (uint32_t k = 0;; ++k) {
-        const int cur = ctl[0];
-        if (cur >= a.nitems) break;
-        if (!ctl[3]) {
+    if (tid >= kConsumers) {
+        if (tid == kConsumers) produce(a, full, empty, meta, cslot, stage(0), stage(1));
+        return;
+    }
+    for (int k = 0;; ++k) {
+        const int s = k & 1;
+        const bool landed = mbar_wait_bounded(&full[s], (k >> 1) & 1, a.wait_ns);
+        if (consumers_any(!landed)) {
             if (tid == 0) record_status(a.status, DEV_TIMEOUT);
             break;
         }
-        const int st = k & 1;
-        if (tid == 0) {
-            const int nxt = atomicAdd(a.next, 1);
-            int issued = 0;
-            if (nxt < a.nitems && dep_met(a, a.passes[a.items[nxt].pass])) {
-                issue_item(a, nxt, stage(st ^ 1), &bar[st ^ 1]);
-                issued = 1;
-            }
-            ctl[1] = nxt;
-            ctl[2] = issued;
-        }
-        const BatchItem item = a.items[cur];
-        const BatchPass &ps = a.passes[item.pass];
-        for (int i = tid; i < ps.ncoef; i += kThreadsBatched) cs[i] = a.coefs[ps.coef + i];
-        const bool landed = mbar_wait_bounded(&bar[st], (k >> 1) & 1, a.wait_ns);
-        if (__syncthreads_or(!landed)) {
-            if (tid == 0) {
-                record_status(a.status, DEV_TIMEOUT);
-                if (ctl[2]) mbar_wait_bounded(&bar[st ^ 1], ((k + 1) >> 1) & 1, a.wait_ns);
-            }
-            break;
-        }
-        const int tx = item.tile % ps.tiles_x, ty = item.tile / ps.tiles_x;
-        const TileOut o{ps.dst, ps.dst_py, ps.nx, ps.ny, ps.dst_gw, ps.dst_vec4};
-        run_variant(ps.variant, stage(st), w0, w1, a.tile_y, ps.H, ps.HX, ps.b, SmemCoef{cs}, o,
-                    tx * kTileX2D - ps.HX, ty * a.tile_y - ps.H);
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            atomicAdd(&a.done[item.pass], 1);  // publish this tile
-            const int nxt = ctl[1];
-            int ok = 1;
-            if (nxt < a.nitems && !ctl[2]) {
-                ok = dep_wait(a, a.passes[a.items[nxt].pass]) ? 1 : 0;
-                if (ok) issue_item(a, nxt, stage(st ^ 1), &bar[st ^ 1]);
-            }
-            ctl[0] = nxt;
-            ctl[3] = ok;
-        }
-        __syncthreads();
+        const StageMeta md = meta[s];
+        if (md.stop) break;
+        run_variant(md, stage(s), w0, w1, a.tile_y, SmemCoef{cslot + s * kCoefSlot});
+        ConsumerSync::sync();  // stage, slot and work buffers are free again
+        if (tid == 0) mbar_arrive(&empty[s]);
     }
 }
 
@@ -167,14 +248,15 @@ __global__ void __launch_bounds__(kThreadsBatched, 1) k_batched(const __grid_con
 
 bool batched_variant_supported(int rb, int m, int pattern)
 {
-    // folded stencils of at most 41 taps: the kernel runs 512 threads per CTA
+    // folded stencils of at most 41 taps (81 stored weights) within 128 registers
     return rb == 1 && m >= 1 && ((pattern == PAT_STAR && m <= 4) || (pattern == PAT_BOX && m <= 2));
 }
 
 size_t batched_smem_bytes(int buf_floats)
 {
-    // two stages and two work buffers
-    return 128 + round_up(kMaxTaps2D * 4, 128) + (size_t)4 * buf_floats * 4 + 2 * BUF_PAD * 4;
+    // barriers, stage slots and weights in the first KB; two stages and two
+    // work buffers after it
+    return 1024 + (size_t)4 * buf_floats * 4 + 2 * BUF_PAD * 4;
 }
 
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s)

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(threads2d<RB, M, PAT>(), min_blocks<RB, M>())
         const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
         const TileOut o{a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, a.dst_vec4};
         process_tile<RB, M, PAT>(buf(i % NS), buf(NS), buf(NS + 1), TY, H, HX, a.b,
-                                 ParamCoef{a.c}, o, tx * TX - HX, ty * TY - H);
+                                 ParamCoef{a.c}, o, tx * TX - HX, ty * TY - H,
+                                 min(TX, a.nx - tx * TX), min(TY, a.ny - ty * TY));
         __syncthreads();
     }
 }

@@ -114,10 +114,16 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
             if (st == STENCIL_OK) st = plan_folded(p, 1, &c1);
             if (st == STENCIL_OK) st = ensure_padded(p);
             if (st != STENCIL_OK) return st;
-            const int off_m = (int)coefs.size();
-            for (double v : *cm) coefs.push_back((float)v);
-            const int off_1 = (int)coefs.size();
-            for (double v : *c1) coefs.push_back((float)v);
+            // weight blocks start on 16-byte boundaries and are padded to a
+            // multiple of 4 floats: the kernel fetches them with a bulk copy
+            auto add_block = [&coefs](const std::vector<double> &c) {
+                const int off = (int)coefs.size();
+                for (double v : c) coefs.push_back((float)v);
+                while (coefs.size() % 4) coefs.push_back(0.f);
+                return off;
+            };
+            const int off_m = add_block(*cm);
+            const int off_1 = add_block(*c1);
             // passes: folded sweeps in groups of b, then the plain remainder
             const int64_t q = G.T / G.m, rem = G.T % G.m;
             const int max_halo = std::min(kGhost, std::min(p->nx, p->ny));

@@ -26,6 +26,18 @@ struct ParamCoef {
     __device__ __forceinline__ float operator()(int k) const { return c[k]; }
 };
 
+// Barrier over the threads that run the tile body: the whole CTA, or the
+// first N threads on named barrier 1 when the CTA has warps with other roles.
+struct CtaSync {
+    __device__ static int nthr() { return blockDim.x; }
+    __device__ static void sync() { __syncthreads(); }
+};
+template <int N>
+struct NamedSync {
+    __device__ static constexpr int nthr() { return N; }
+    __device__ static void sync() { asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory"); }
+};
+
 constexpr int TX = kTileX2D;
 constexpr int NT = kThreads2D;
 constexpr int BUF_PAD = 32;  // floats of slack before and after every buffer
@@ -159,7 +171,7 @@ static __device__ __noinline__ void store_checked4(float *dst, int64_t py, int n
 // A strip of rows [ya, yb) reads input rows ya-R .. yb+R-1.  The first 2R
 // rows only feed window slots whose output row is >= ya and the last 2R only
 // slots whose output row is < yb, so every output gets exactly its taps.
-template <int RB, int M, int PAT, bool FINAL, class Coef>
+template <int RB, int M, int PAT, bool FINAL, class Sync, class Coef>
 __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float *__restrict__ D,
                                              int SP, int r0, int r1, int k0, int k1,
                                              const Coef &cf, const TileOut &a, int gx0, int gy0)
@@ -170,7 +182,7 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
     const int nr = r1 - r0;
     if (nsx <= 0 || nr <= 0) return;
     // row groups: as many as the threads allow, each at least 2R rows tall
-    const int nthr = blockDim.x;  // 256 or 512, chosen per kernel instance
+    const int nthr = Sync::nthr();  // 256 or 512, chosen per kernel instance
     int G = nthr / nsx;
     G = max(1, min(G, nr / (2 * R)));
     const int items = nsx * G;
@@ -270,30 +282,31 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
     }
 }
 
-// Plain radius-1 sweeps are memory-bound: keep three CTAs per SM resident.
-
 // b fused sweeps of one staged tile: stage -> work buffers -> destination.
 // The staged box covers rows [0, TY + 2H) and columns [0, TX + 2HX), with the
-// output tile at rows [H, H + TY) and columns [HX, HX + TX).
-template <int RB, int M, int PAT, class Coef>
+// output tile at rows [H, H + TY) and columns [HX, HX + TX).  Only the first
+// vy rows and vx columns of the tile lie inside the grid (a ragged last tile):
+// every sweep's region is clipped to what those outputs need.
+template <int RB, int M, int PAT, class Sync = CtaSync, class Coef>
 __device__ __forceinline__ void process_tile(const float *stage, float *work0, float *work1,
                                              int TY, int H, int HX, int b, const Coef &cf,
-                                             const TileOut &o, int gx0, int gy0)
+                                             const TileOut &o, int gx0, int gy0, int vx, int vy)
 {
     constexpr int R = RB * M;
-    const int SP = TX + 2 * HX, ROWS = TY + 2 * H;
+    const int SP = TX + 2 * HX;
+    (void)TY;
     const float *src = stage;
     for (int s = 0; s < b - 1; ++s) {
-        const int sh = (s + 1) * R;
-        const int c0 = HX - H + sh, c1 = SP - (HX - H) - sh;
+        const int sh = (s + 1) * R;  // rim still needed: H - sh per side
+        const int c0 = HX - H + sh, c1 = HX + vx + H - sh;
         float *dst = (s & 1) ? work1 : work0;
-        sweep_region<RB, M, PAT, false>(src, dst, SP, sh, ROWS - sh, c0 / 4, (c1 + 3) / 4, cf, o,
-                                        gx0, gy0);
-        __syncthreads();
+        sweep_region<RB, M, PAT, false, Sync>(src, dst, SP, sh, 2 * H + vy - sh, c0 / 4,
+                                              (c1 + 3) / 4, cf, o, gx0, gy0);
+        Sync::sync();
         src = dst;
     }
-    sweep_region<RB, M, PAT, true>(src, nullptr, SP, H, H + TY, HX / 4, (HX + TX) / 4, cf, o, gx0,
-                                   gy0);
+    sweep_region<RB, M, PAT, true, Sync>(src, nullptr, SP, H, H + vy, HX / 4, (HX + vx + 3) / 4,
+                                         cf, o, gx0, gy0);
 }
 
 }  // namespace tile2d

@@ -54,6 +54,32 @@ def test_batched_parity(env, fold):
         p.close()
 
 
+@pytest.mark.parametrize("shapes", [[(300, 260)], [(300, 260), (33, 40)], [(64, 128)] * 3])
+def test_batched_dependency_chains(env, shapes):
+    """Few grids and many passes: nearly every item waits for the previous
+    pass of its own grid, often for the item its own CTA is finishing."""
+    torch, binding, oracle = env
+    plans, xs, ys, refs = [], [], [], []
+    for j, shape in enumerate(shapes):
+        c = synth.dyadic_coeffs(9100 + j, 2, 1, "star" if j % 2 == 0 else "box")
+        x = synth.grid(9200 + j, shape, np.float32)
+        plans.append(binding.Plan(shape, c))
+        xs.append(torch.from_numpy(x).cuda())
+        ys.append(torch.full_like(xs[-1], float("nan")))
+        refs.append(oracle.run(x.astype(np.float64), c, 37 + 5 * j))
+    Ts = [37 + 5 * j for j in range(len(shapes))]
+    binding.run_batched(plans, xs, ys, Ts, [1] * len(shapes))
+    plans[0].sync()
+    for y, ref in zip(ys, refs):
+        assert oracle.rel_l2(y.cpu().numpy(), ref) <= 1e-5
+    binding.run_batched(plans, xs, ys, Ts)
+    plans[0].sync()
+    for y, ref in zip(ys, refs):
+        assert oracle.rel_l2(y.cpu().numpy(), ref) <= 1e-5
+    for p in plans:
+        p.close()
+
+
 def test_batched_rejects_non_2d(env):
     torch, binding, _ = env
     p1 = binding.Plan((100,), synth.heat1d_coeffs())
