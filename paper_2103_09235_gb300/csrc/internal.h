@@ -145,6 +145,18 @@ cudaError_t launch_sweep1d(int R, bool f64, const Sweep1DArgs &a, cudaStream_t s
 
 // ---- layout conversion, coefficient folding, error reduction --------------
 cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_t s);
+// One 2D grid's import within a batch: padded rows [row0, row0 + ny + 2 gw)
+// of the batch's row space.
+struct ImportJob {
+    float *origin;
+    int64_t py;
+    const float *src;
+    long long row0;
+    int nx, ny, gw, vec4;
+};
+ImportJob make_import_job(const Padded &P, const float *src, int gw, long long row0);
+// All jobs (device array, ordered by row0) in one launch; rows = the total.
+cudaError_t launch_import_batch(const ImportJob *d_jobs, int njobs, long long rows, cudaStream_t s);
 cudaError_t launch_export(const Padded &P, float *dst, cudaStream_t s);
 // c^(m) by m-1 convolutions with c (FP64 on the GPU); work holds 2*(2mr+1)^ndim doubles.
 cudaError_t launch_fold_power(int ndim, int r, int m, const double *d_c, double *d_out,

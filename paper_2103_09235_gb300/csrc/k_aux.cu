@@ -45,6 +45,38 @@ __global__ void k_import(float *__restrict__ origin, int64_t py, int64_t pz, int
     }
 }
 
+// The imports of a whole batch of 2D grids in one launch: one warp per padded
+// row, the row's grid found by binary search over the jobs' first rows.
+__global__ void k_import_batch(const ImportJob *__restrict__ jobs, int njobs, long long rows)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long row = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); row < rows;
+         row += nwarps) {
+        int lo = 0, hi = njobs - 1;  // last job with row0 <= row
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].row0 <= row) lo = mid;
+            else hi = mid - 1;
+        }
+        const ImportJob &J = jobs[lo];
+        const int y = (int)(row - J.row0) - J.gw;
+        const float *srow = J.src + (long long)wrap_idx(y, J.ny) * J.nx;
+        float *drow = J.origin + y * J.py;
+        if (J.vec4) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(srow);
+            float4 *d4 = reinterpret_cast<float4 *>(drow);
+            for (int i = lane; i < J.nx / 4; i += 32) d4[i] = s4[i];
+        } else {
+            for (int i = lane; i < J.nx; i += 32) drow[i] = srow[i];
+        }
+        for (int i = lane; i < 2 * J.gw; i += 32) {
+            const int x = i < J.gw ? i - J.gw : J.nx + (i - J.gw);
+            drow[x] = srow[wrap_idx(x, J.nx)];
+        }
+    }
+}
+
 __global__ void k_export(const float *__restrict__ origin, int64_t py, int64_t pz, int nx, int ny,
                          int nz, float *__restrict__ dst)
 {
@@ -182,6 +214,29 @@ cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_
     const int grid = (int)std::min<long long>(rows, (long long)sm_count() * 16);
     k_import<<<grid, 256, 0, s>>>(P.origin, P.py, P.pz, P.nx, P.ny, P.nz, gwx, gwy, gwz, src,
                                   vec4);
+    return cudaGetLastError();
+}
+
+ImportJob make_import_job(const Padded &P, const float *src, int gw, long long row0)
+{
+    ImportJob j;
+    j.origin = P.origin;
+    j.py = P.py;
+    j.src = src;
+    j.row0 = row0;
+    j.nx = P.nx;
+    j.ny = P.ny;
+    j.gw = gw;
+    j.vec4 = (P.nx % 4 == 0) && ((uintptr_t)src % 16 == 0) && (P.py % 4 == 0) &&
+             ((uintptr_t)P.origin % 16 == 0);
+    return j;
+}
+
+cudaError_t launch_import_batch(const ImportJob *d_jobs, int njobs, long long rows, cudaStream_t s)
+{
+    if (njobs == 0 || rows == 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((rows + 7) / 8, (long long)sm_count() * 16);
+    k_import_batch<<<grid, 256, 0, s>>>(d_jobs, njobs, rows);
     return cudaGetLastError();
 }
 

@@ -1,7 +1,7 @@
 // stencil_run_batched: flattens every grid's time loop into passes and
 // (pass, tile) work items, uploads them once per distinct batch, and runs the
-// whole batch as one persistent kernel (after one layout-import launch per
-// grid), captured into a CUDA graph that later calls replay.
+// whole batch as one persistent kernel (after one layout-import launch for all
+// grids), captured into a CUDA graph that later calls replay.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -187,18 +187,28 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
             for (auto &G : gp)
                 if (r < G.npass)
                     for (int t = 0; t < G.ntiles; ++t) items.push_back({G.first_pass + r, t});
-        // one device block: maps | passes | items | coefs | done | next
+        // imports of every grid that steps, in one launch
+        std::vector<ImportJob> jobs;
+        long long import_rows = 0;
+        for (const GridPlan &G : gp) {
+            if (G.T == 0) continue;
+            jobs.push_back(make_import_job(G.p->A, G.in, G.gw, import_rows));
+            import_rows += G.p->ny + 2 * G.gw;
+        }
+        // one device block: maps | passes | items | coefs | import jobs | done | next
         const size_t o_maps = 0;
         const size_t o_pass = round_up((int)(maps.size() * sizeof(CUtensorMap)), 256);
         const size_t o_item = o_pass + round_up((int)(passes.size() * sizeof(BatchPass) + 1), 256);
         const size_t o_coef = o_item + round_up((int)(items.size() * sizeof(BatchItem) + 1), 256);
-        const size_t o_done = o_coef + round_up((int)(coefs.size() * sizeof(float) + 1), 256);
+        const size_t o_jobs = o_coef + round_up((int)(coefs.size() * sizeof(float) + 1), 256);
+        const size_t o_done = o_jobs + round_up((int)(jobs.size() * sizeof(ImportJob) + 1), 256);
         const size_t total = o_done + (passes.size() + 1) * sizeof(int) + 256;
         std::vector<unsigned char> host(total, 0);
         if (!maps.empty()) memcpy(host.data() + o_maps, maps.data(), maps.size() * sizeof(CUtensorMap));
         if (!passes.empty()) memcpy(host.data() + o_pass, passes.data(), passes.size() * sizeof(BatchPass));
         if (!items.empty()) memcpy(host.data() + o_item, items.data(), items.size() * sizeof(BatchItem));
         if (!coefs.empty()) memcpy(host.data() + o_coef, coefs.data(), coefs.size() * sizeof(float));
+        if (!jobs.empty()) memcpy(host.data() + o_jobs, jobs.data(), jobs.size() * sizeof(ImportJob));
         auto old = p0->batch_mem.find(key);
         if (old != p0->batch_mem.end()) {
             cudaFree(old->second);
@@ -233,17 +243,19 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
         const int grid = std::max(1, std::min(a.nitems, occ * p0->sm_count));
         const size_t counters = (passes.size() + 1) * sizeof(int);
 
+        const ImportJob *d_jobs = reinterpret_cast<const ImportJob *>(dev + o_jobs);
+        const int njobs = (int)jobs.size();
         auto enqueue = [=](cudaStream_t st_, int *nl) -> stencil_status_t {
             for (const GridPlan &G : gp) {
-                cudaError_t err;
-                if (G.T == 0) {
-                    err = cudaMemcpyAsync(G.out, G.in, sizeof(float) * (size_t)G.p->nx * G.p->ny,
-                                          cudaMemcpyDeviceToDevice, st_);
-                } else {
-                    err = launch_import(G.p->A, G.in, G.gw, st_);
-                    *nl += 1;
-                }
+                if (G.T != 0) continue;
+                const cudaError_t err = cudaMemcpyAsync(
+                    G.out, G.in, sizeof(float) * (size_t)G.p->nx * G.p->ny, cudaMemcpyDeviceToDevice, st_);
+                if (err != cudaSuccess) return cuda_fail(err, "batched copy");
+            }
+            if (njobs > 0) {
+                const cudaError_t err = launch_import_batch(d_jobs, njobs, import_rows, st_);
                 if (err != cudaSuccess) return cuda_fail(err, "batched import");
+                *nl += 1;
             }
             if (a.nitems > 0) {
                 cudaError_t err = cudaMemsetAsync(a.done, 0, counters, st_);

@@ -3,6 +3,8 @@
 // shared-memory tile (see k_sweep2d.cu) and the b-sweep temporal block.
 #pragma once
 
+#include <climits>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -54,27 +56,6 @@ struct Taps {
         return PAT == PAT_BOX ? true : (cabs_div(a, RB) + cabs_div(b, RB) <= M);
     }
 };
-
-__device__ __forceinline__ void store_point(float *dst, int64_t py, int nx, int ny, int gw, int X,
-                                            int Y, float v)
-{
-    dst[Y * py + X] = v;
-    if (gw > 0) {
-        const bool xl = X < gw, xh = X >= nx - gw, yl = Y < gw, yh = Y >= ny - gw;
-        if (xl) dst[Y * py + X + nx] = v;
-        if (xh) dst[Y * py + X - nx] = v;
-        if (yl) {
-            dst[(Y + ny) * py + X] = v;
-            if (xl) dst[(Y + ny) * py + X + nx] = v;
-            if (xh) dst[(Y + ny) * py + X - nx] = v;
-        }
-        if (yh) {
-            dst[(Y - ny) * py + X] = v;
-            if (xl) dst[(Y - ny) * py + X + nx] = v;
-            if (xh) dst[(Y - ny) * py + X - nx] = v;
-        }
-    }
-}
 
 template <int RB, int M, int PAT>
 struct Strip {
@@ -131,37 +112,23 @@ struct Strip {
     }
 };
 
-// Ghost copies of four outputs; scalar arguments, so that the caller's
-// descriptor stays in registers instead of being spilled for an address.
-static __device__ __noinline__ void store_ghosts4(float *dst, int64_t py, int nx, int ny, int gw,
-                                                  int X, int Y, float v0, float v1, float v2,
-                                                  float v3)
+// Four outputs of row Y starting at column X of a row that ends at column nx
+// or is not 16-byte aligned: only the columns inside the grid are stored.
+// Out of line, with scalar arguments: only the last strip of a ragged tile
+// (or an unaligned destination) comes here, and the caller's descriptor stays
+// in registers.
+static __device__ __noinline__ void store_masked4(float *dst, int64_t py, int nx, int vec4, int X,
+                                                  int Y, float v0, float v1, float v2, float v3)
 {
-    if (X < nx) store_point(dst, py, nx, ny, gw, X, Y, v0);
-    if (X + 1 < nx) store_point(dst, py, nx, ny, gw, X + 1, Y, v1);
-    if (X + 2 < nx) store_point(dst, py, nx, ny, gw, X + 2, Y, v2);
-    if (X + 3 < nx) store_point(dst, py, nx, ny, gw, X + 3, Y, v3);
-}
-
-// Four outputs of row Y starting at column X, with every check: grid bounds,
-// 16-byte alignment and the ghost copies.  Out of line: only edge strips and
-// ragged tiles come here.
-static __device__ __noinline__ void store_checked4(float *dst, int64_t py, int nx, int ny, int gw,
-                                                   int vec4, int X, int Y, float v0, float v1,
-                                                   float v2, float v3)
-{
-    if (Y >= ny || X >= nx) return;
     float *row = dst + Y * py;
     if (vec4 && X + 3 < nx) {
         *reinterpret_cast<float4 *>(row + X) = make_float4(v0, v1, v2, v3);
-    } else {
-        row[X] = v0;
-        if (X + 1 < nx) row[X + 1] = v1;
-        if (X + 2 < nx) row[X + 2] = v2;
-        if (X + 3 < nx) row[X + 3] = v3;
+        return;
     }
-    if (gw > 0 && (X < gw || X + 3 >= nx - gw || Y < gw || Y >= ny - gw))
-        store_ghosts4(dst, py, nx, ny, gw, X, Y, v0, v1, v2, v3);
+    if (X < nx) row[X] = v0;
+    if (X + 1 < nx) row[X + 1] = v1;
+    if (X + 2 < nx) row[X + 2] = v2;
+    if (X + 3 < nx) row[X + 3] = v3;
 }
 
 // One sweep over output rows [r0, r1) and 4-column strips [k0, k1) of a
@@ -201,17 +168,15 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
 
-        // Output rows are emitted in order ya, ya+1, ...: a strip whose rows and
-        // columns are all interior and away from the ghost band (the common
-        // case) stores each row with one 16-byte store and a pointer step;
-        // any other strip takes the checked path.
+        // Output rows are emitted in order ya, ya+1, ...: a strip whose four
+        // columns lie inside the grid (all but a ragged tile's last strip)
+        // stores each row with one 16-byte store and a pointer step.
         float *orow = nullptr;
         bool fast = false;
         if constexpr (FINAL) {
-            const int X = gx0 + cx, Y0 = gy0 + ya, Y1 = gy0 + yb;
-            const int gw = a.dst_gw;
-            fast = a.dst_vec4 && X + 3 < a.nx && Y1 <= a.ny &&
-                   (gw == 0 || (X >= gw && X + 3 < a.nx - gw && Y0 >= gw && Y1 <= a.ny - gw));
+            // rows [ya, yb) all lie inside the grid (the region is clipped to it)
+            const int X = gx0 + cx, Y0 = gy0 + ya;
+            fast = a.dst_vec4 && X + 3 < a.nx;
             orow = a.dst + (int64_t)Y0 * a.dst_py + X;
         } else {
             orow = D + ya * SP + cx;
@@ -222,8 +187,8 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
                     *reinterpret_cast<float4 *>(orow) =
                         make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
                 else
-                    store_checked4(a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, a.dst_vec4, gx0 + cx,
-                                   gy0 + y, acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                    store_masked4(a.dst, a.dst_py, a.nx, a.dst_vec4, gx0 + cx, gy0 + y, acc[0][0],
+                                  acc[0][1], acc[0][2], acc[0][3]);
                 orow += a.dst_py;
             } else {
                 (void)y;
@@ -282,6 +247,62 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
     }
 }
 
+// Ghost band of a padded destination: every output within gw cells of an edge
+// is repeated across that edge (across both at a corner), so that the next
+// pass's TMA boxes read periodic neighbours without wrapping.  Run after the
+// tile's final sweep by the tiles that touch the band: the outputs are read
+// back from the destination after a barrier (the CTA's own stores) and copied
+// with one thread per band cell.  A cell in a row band and a column band is
+// handled twice, writing the same values.
+template <class Sync>
+__device__ __forceinline__ void refresh_ghosts(const TileOut &o, int x0, int y0, int vx, int vy)
+{
+    const int gw = o.dst_gw, nx = o.nx, ny = o.ny;
+    if (gw <= 0) return;
+    const int nt = y0 < gw ? min(y0 + vy, gw) - y0 : 0;                  // top band rows
+    const int yb0 = max(y0, ny - gw), nb = y0 + vy > yb0 ? y0 + vy - yb0 : 0;
+    const int nl = x0 < gw ? min(x0 + vx, gw) - x0 : 0;                  // left band columns
+    const int xr0 = max(x0, nx - gw), nr = x0 + vx > xr0 ? x0 + vx - xr0 : 0;
+    const int n_rows = (nt + nb) * vx, total = n_rows + vy * (nl + nr);
+    if (total == 0) return;  // the same for every thread of the tile
+    Sync::sync();
+    float *d = o.dst;
+    const int64_t py = o.dst_py;
+    for (int it = threadIdx.x; it < total; it += Sync::nthr()) {
+        int X, Y;
+        if (it < nt * vx) {
+            Y = y0 + it / vx;
+            X = x0 + it % vx;
+        } else if (it < n_rows) {
+            const int j = it - nt * vx;
+            Y = yb0 + j / vx;
+            X = x0 + j % vx;
+        } else if (it < n_rows + vy * nl) {
+            const int j = it - n_rows;
+            Y = y0 + j / nl;
+            X = x0 + j % nl;
+        } else {
+            const int j = it - n_rows - vy * nl;
+            Y = y0 + j / nr;
+            X = xr0 + j % nr;
+        }
+        const float v = d[Y * py + X];
+        const int xs[2] = {X < gw ? X + nx : INT_MIN, X >= nx - gw ? X - nx : INT_MIN};
+        const int ys[2] = {Y < gw ? Y + ny : INT_MIN, Y >= ny - gw ? Y - ny : INT_MIN};
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+            if (xs[i] != INT_MIN) d[Y * py + xs[i]] = v;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (ys[j] == INT_MIN) continue;
+            d[ys[j] * py + X] = v;
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+                if (xs[i] != INT_MIN) d[ys[j] * py + xs[i]] = v;
+        }
+    }
+}
+
 // b fused sweeps of one staged tile: stage -> work buffers -> destination.
 // The staged box covers rows [0, TY + 2H) and columns [0, TX + 2HX), with the
 // output tile at rows [H, H + TY) and columns [HX, HX + TX).  Only the first
@@ -307,6 +328,7 @@ __device__ __forceinline__ void process_tile(const float *stage, float *work0, f
     }
     sweep_region<RB, M, PAT, true, Sync>(src, nullptr, SP, H, H + vy, HX / 4, (HX + vx + 3) / 4,
                                          cf, o, gx0, gy0);
+    refresh_ghosts<Sync>(o, gx0 + HX, gy0 + H, vx, vy);
 }
 
 }  // namespace tile2d
