@@ -10,13 +10,17 @@
 // taken along z: the paper handles a 3D grid as a stack of 2D slices);
 // output plane z - R is then complete and stored.  The input plane's slot is
 // free as soon as it has been read, so the ring needs only the prefetch depth.
+#include <climits>
+
 #include "device_common.cuh"
 #include "internal.h"
 
 namespace sg {
 namespace {
 
-constexpr int TX3 = 64, TY3 = 16, NT3 = 256, ZC = 4, NST = 3;
+// 8 consumer warps (one 4-column strip of one row per thread) and one
+// producer warp that keeps the ring full.
+constexpr int TX3 = 64, TY3 = 16, NC3 = 256, NT3 = NC3 + 32, ZC = 4, NST = 3;
 
 __host__ __device__ constexpr int cabs_div3(int v, int d) { return ((v < 0 ? -v : v) + d - 1) / d; }
 
@@ -31,21 +35,98 @@ struct Taps3 {
     }
 };
 
-__device__ __noinline__ void store_ghosts3(const Sweep3DArgs &a, int X, int Y, int Z, float v)
+// Copies of output (X, Y, Z) across every edge of the ghost band it lies
+// within (up to seven: faces, edges and corners of the periodic box).
+__device__ __forceinline__ void mirror3(const Sweep3DArgs &a, int X, int Y, int Z, float v)
 {
     const int gw = a.dst_gw;
-    int xs[3] = {X, 0, 0}, ys[3] = {Y, 0, 0}, zs[3] = {Z, 0, 0};
-    int nxs = 1, nys = 1, nzs = 1;
-    if (X < gw) xs[nxs++] = X + a.nx;
-    if (X >= a.nx - gw) xs[nxs++] = X - a.nx;
-    if (Y < gw) ys[nys++] = Y + a.ny;
-    if (Y >= a.ny - gw) ys[nys++] = Y - a.ny;
-    if (Z < gw) zs[nzs++] = Z + a.nz;
-    if (Z >= a.nz - gw) zs[nzs++] = Z - a.nz;
-    for (int i = 0; i < nzs; ++i)
-        for (int j = 0; j < nys; ++j)
-            for (int k = 0; k < nxs; ++k)
-                if (i | j | k) a.dst[zs[i] * a.dst_pz + ys[j] * a.dst_py + xs[k]] = v;
+    // per axis: the cell itself, its copy past the high edge, past the low edge
+    const int xs[3] = {X, X < gw ? X + a.nx : INT_MIN, X >= a.nx - gw ? X - a.nx : INT_MIN};
+    const int ys[3] = {Y, Y < gw ? Y + a.ny : INT_MIN, Y >= a.ny - gw ? Y - a.ny : INT_MIN};
+    const int zs[3] = {Z, Z < gw ? Z + a.nz : INT_MIN, Z >= a.nz - gw ? Z - a.nz : INT_MIN};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if ((i | j | k) && zs[i] != INT_MIN && ys[j] != INT_MIN && xs[k] != INT_MIN)
+                    a.dst[zs[i] * a.dst_pz + ys[j] * a.dst_py + xs[k]] = v;
+}
+
+// Ghost band of a padded destination, for the CTA's block of outputs
+// (columns x0.., rows y0.., planes z0..z1): after a barrier over the consumer
+// threads, the outputs within gw cells of an edge are read back (the CTA's own
+// stores) and mirrored, one thread per cell.  The cells are the x/y band of
+// every plane, then every cell of the planes in the z band; all planes are
+// handled at once, each thread loading four cells before it stores.  Only
+// CTAs that touch the band have work; a cell in two bands is handled twice,
+// writing the same values.
+__device__ __forceinline__ void refresh_ghosts3(const Sweep3DArgs &a, int x0, int y0, int z0,
+                                                int z1, int tid)
+{
+    const int gw = a.dst_gw, nx = a.nx, ny = a.ny, nz = a.nz;
+    const int vx = min(TX3, nx - x0), vy = min(TY3, ny - y0);
+    const int nt = y0 < gw ? min(y0 + vy, gw) - y0 : 0;  // band rows and columns of the tile
+    const int yb0 = max(y0, ny - gw), nb = y0 + vy > yb0 ? y0 + vy - yb0 : 0;
+    const int nl = x0 < gw ? min(x0 + vx, gw) - x0 : 0;
+    const int xr0 = max(x0, nx - gw), nr = x0 + vx > xr0 ? x0 + vx - xr0 : 0;
+    const int n_rows = (nt + nb) * vx, n_xy = n_rows + vy * (nl + nr);
+    const int zl = max(0, min(z1, gw) - z0);           // planes z0 .. z0+zl-1 in the low z band
+    const int zh0 = max(z0, nz - gw), zh = max(0, z1 - zh0);
+    const int total1 = (z1 - z0) * n_xy, total = total1 + (zl + zh) * vx * vy;
+    constexpr int U = 4;
+    for (int base = tid; base < total; base += U * NC3) {
+        float v[U];
+        int X[U], Y[U], Z[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int it = base + u * NC3;
+            if (it >= total) continue;
+            if (it < total1) {
+                const int c = it % n_xy;
+                Z[u] = z0 + it / n_xy;
+                if (c < nt * vx) {
+                    Y[u] = y0 + c / vx;
+                    X[u] = x0 + c % vx;
+                } else if (c < n_rows) {
+                    Y[u] = yb0 + (c - nt * vx) / vx;
+                    X[u] = x0 + (c - nt * vx) % vx;
+                } else if (c < n_rows + vy * nl) {
+                    Y[u] = y0 + (c - n_rows) / nl;
+                    X[u] = x0 + (c - n_rows) % nl;
+                } else {
+                    Y[u] = y0 + (c - n_rows - vy * nl) / nr;
+                    X[u] = xr0 + (c - n_rows - vy * nl) % nr;
+                }
+            } else {
+                const int j = it - total1, pl = j / (vx * vy), c = j % (vx * vy);
+                Z[u] = pl < zl ? z0 + pl : zh0 + (pl - zl);
+                Y[u] = y0 + c / vx;
+                X[u] = x0 + c % vx;
+            }
+            v[u] = a.dst[Z[u] * a.dst_pz + Y[u] * a.dst_py + X[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (base + u * NC3 < total) mirror3(a, X[u], Y[u], Z[u], v[u]);
+    }
+}
+
+// OR of a predicate over the consumer threads (named barrier 1); also orders
+// their memory accesses like a barrier.
+__device__ __forceinline__ bool consumers_any3(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(NC3)
+        : "memory");
+    return r != 0;
 }
 
 template <int RB, int M, int PAT>
@@ -73,29 +154,42 @@ __global__ void __launch_bounds__(NT3)
     const int zin0 = z0 - R, nin = (z1 - z0) + 2 * R;  // input planes streamed
     const int nchunks = (nin + ZC - 1) / ZC;
 
+    uint64_t *empty = bars + NST;  // released by the 8 consumer warps
     if (tid == 0) {
         prefetch_tensormap(&map);
-        for (int s = 0; s < NST; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&bars[s], 1);
+            mbar_init(&empty[s], NC3 / 32);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](int c) {  // chunk c: input planes 4c .. 4c+3 of this CTA
-        const int s = c % NST;
-        mbar_arrive_expect_tx(&bars[s], chunk_bytes);
-        tma_load_3d(stages + s * a.buf_floats, &map, &bars[s], a.map_x0 + x0 - HX,
-                    a.map_y0 + y0 - R, a.map_z0 + zin0 + c * ZC);
-    };
-    if (tid == 0)
-        for (int c = 0; c < NST && c < nchunks; ++c) issue(c);
+    if (tid >= NC3) {
+        // producer: chunk c (input planes 4c .. 4c+3 of this CTA) into stage
+        // c % NST once the consumers released the chunk NST earlier
+        if (tid != NC3) return;
+        int c = 0;
+        for (; c < nchunks; ++c) {
+            const int s = c % NST;
+            if (c >= NST && !mbar_wait_bounded(&empty[s], ((c / NST) - 1) & 1, a.wait_ns)) {
+                record_status(a.status, DEV_TIMEOUT);
+                break;
+            }
+            mbar_arrive_expect_tx(&bars[s], chunk_bytes);
+            tma_load_3d(stages + s * a.buf_floats, &map, &bars[s], a.map_x0 + x0 - HX,
+                        a.map_y0 + y0 - R, a.map_z0 + zin0 + c * ZC);
+        }
+        // the copies still in flight land before the CTA may exit
+        for (int q = max(0, c - NST); q < c; ++q)
+            mbar_wait_bounded(&bars[q % NST], (q / NST) & 1, a.wait_ns);
+        return;
+    }
 
     // thread -> (4-column strip, row) of the tile
     const int strip = tid % (TX3 / 4), yr = tid / (TX3 / 4);
     const int X = x0 + 4 * strip, Y = y0 + yr;
     const bool live = (Y < a.ny) && (X < a.nx);
-    const int gw = a.dst_gw;
-    // columns and row of this thread away from the edges and the ghost band
-    const bool fast_xy = live && a.dst_vec4 && X + 3 < a.nx &&
-                         (gw == 0 || (X >= gw && X + 3 < a.nx - gw && Y >= gw && Y < a.ny - gw));
+    const bool vec4 = a.dst_vec4 && X + 3 < a.nx;  // one 16-byte store per plane
 
     float acc[W][4];
 #pragma unroll
@@ -103,16 +197,13 @@ __global__ void __launch_bounds__(NT3)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
 
+    bool failed = false;
     for (int c = 0; c < nchunks; ++c) {
         const int s = c % NST;
-        const bool ok = mbar_wait_bounded(&bars[s], (c / NST) & 1, a.wait_ns);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                record_status(a.status, DEV_TIMEOUT);
-                for (int q = c + 1; q < min(nchunks, c + NST); ++q)
-                    mbar_wait_bounded(&bars[q % NST], (q / NST) & 1, a.wait_ns);
-            }
-            return;
+        if (!mbar_wait_bounded(&bars[s], (c / NST) & 1, a.wait_ns)) {
+            record_status(a.status, DEV_TIMEOUT);
+            failed = true;
+            break;
         }
         const float *chunk = stages + s * a.buf_floats + 4 * strip + HX - RP;
 #pragma unroll 1
@@ -148,24 +239,15 @@ __global__ void __launch_bounds__(NT3)
                 }
             }
             const int zo = zin0 + p - R;  // output plane completed by this input plane
-            if (zo >= z0 && fast_xy && (gw == 0 || (zo >= gw && zo < a.nz - gw))) {
-                *reinterpret_cast<float4 *>(a.dst + zo * a.dst_pz + Y * a.dst_py + X) =
-                    make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
-            } else if (zo >= z0 && live) {
+            if (zo >= z0 && live) {
                 float *row = a.dst + zo * a.dst_pz + Y * a.dst_py;
-                if (a.dst_vec4 && X + 3 < a.nx) {
+                if (vec4) {
                     *reinterpret_cast<float4 *>(row + X) =
                         make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
                 } else {
 #pragma unroll
                     for (int v = 0; v < 4; ++v)
                         if (X + v < a.nx) row[X + v] = acc[0][v];
-                }
-                if (gw > 0 && (X < gw || X + 3 >= a.nx - gw || Y < gw || Y >= a.ny - gw ||
-                               zo < gw || zo >= a.nz - gw)) {
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        if (X + v < a.nx) store_ghosts3(a, X + v, Y, zo, acc[0][v]);
                 }
             }
 #pragma unroll
@@ -175,9 +257,13 @@ __global__ void __launch_bounds__(NT3)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
         }
-        __syncthreads();  // stage s is free: request the chunk NST ahead into it
-        if (tid == 0 && c + NST < nchunks) issue(c + NST);
+        __syncwarp();  // this warp is done with stage s
+        if ((tid & 31) == 0) mbar_arrive(&empty[s]);
     }
+    // every consumer gets here (all waits are bounded); the ghost band is
+    // refreshed once all of the CTA's outputs are stored
+    if (consumers_any3(failed) || a.dst_gw <= 0) return;
+    refresh_ghosts3(a, x0, y0, z0, z1, tid);
 }
 
 template <int RB, int M, int PAT>

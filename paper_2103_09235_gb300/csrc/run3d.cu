@@ -11,7 +11,7 @@
 namespace sg {
 
 namespace {
-constexpr int kTX3 = 64, kTY3 = 16, kZChunk = 64;
+constexpr int kTX3 = 64, kTY3 = 16;
 }
 
 static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m,
@@ -26,10 +26,11 @@ static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int 
     a.tiles_x = ceil_div(p->nx, kTX3);
     a.tiles_y = ceil_div(p->ny, kTY3);
     a.ntiles_xy = a.tiles_x * a.tiles_y;
-    // z chunks of 64 planes, shortened (down to 16) until the launch covers
-    // four CTAs per SM; each chunk re-reads 2R planes of halo
-    int zc = kZChunk;
-    while (zc > 16 && (int64_t)a.ntiles_xy * ceil_div(p->nz, zc) < 4 * p->sm_count) zc /= 2;
+    // z chunks of 16 planes for radius 1 and 32 for wider stencils (each chunk
+    // re-reads 2R planes of halo): many short CTAs balance the SMs and bound
+    // the tail; measured on GB300 at 512^3 and 256^3
+    int zc = R <= 1 ? 16 : 32;
+    while (zc > 8 && (int64_t)a.ntiles_xy * ceil_div(p->nz, zc) < 4 * p->sm_count) zc /= 2;
     a.zchunk = zc;
     a.zchunks = ceil_div(p->nz, zc);
     a.ntiles = a.ntiles_xy * a.zchunks;

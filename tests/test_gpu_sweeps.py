@@ -282,6 +282,10 @@ CASES_3D = [
     ((40, 36, 64), "star", 2, 4, 1),
     ((40, 36, 64), "box", 2, 3, 1),
     ((12, 9, 11), "star", 1, 5, 2),
+    # ghost bands overlapping in every axis; many z chunks per tile column
+    ((7, 6, 9), "box", 1, 4, 2),
+    ((150, 20, 24), "star", 1, 5, 2),
+    ((150, 20, 24), "box", 1, 4, 1),
 ]
 
 
