@@ -39,6 +39,12 @@ CONFIGS = {
     "box8192": dict(shape=(8192, 8192), T=512, kind="box", seed=synth.BASE_SEED + 3,
                     workload="2D 9-point box 8192x8192 FP32, periodic, T=512, "
                              "dyadic coefficients (seeded)"),
+    "star512cube": dict(shape=(512, 512, 512), T=200, kind="star", seed=synth.BASE_SEED + 4,
+                        workload="3D 7-point star 512^3 FP32, periodic, T=200, "
+                                 "dyadic coefficients (seeded)"),
+    "box256cube": dict(shape=(256, 256, 256), T=200, kind="box", seed=synth.BASE_SEED + 5,
+                       workload="3D 27-point box 256^3 FP32, periodic, T=200, "
+                                "dyadic coefficients (seeded)"),
 }
 SHAPE = CONFIGS["star4096"]["shape"]
 T_STEPS = CONFIGS["star4096"]["T"]
@@ -149,10 +155,11 @@ def dist_env():
     return ws, rank, local
 
 
-def oracle_sample(T_sample: int, shape=SHAPE):
+def oracle_sample(T_sample: int, shape=None):
     """Times the FP64 oracle on a bounded sample: the full grid, T_sample steps."""
     import oracle
-    c = synth.dyadic_coeffs(SEED, 2, 1, KIND)
+    shape = SHAPE if shape is None else shape
+    c = synth.dyadic_coeffs(SEED, len(shape), 1, KIND)
     x = synth.grid(SEED, shape, np.float32).astype(np.float64)
     t0 = time.perf_counter()
     oracle.run(x, c, T_sample)
@@ -180,8 +187,8 @@ def run_reference(args):
         secs.append(dt)
     value = statistics.median(vals)
     ms = 1e3 * float(np.prod(SHAPE)) * T_STEPS / (value * 1e9)
-    sample = "full %dx%d grid, %d of the %d steps per timed step (FP64 C oracle, OpenMP)" % (
-        SHAPE[0], SHAPE[1], T_sample, T_STEPS)
+    sample = "full %s grid, %d of the %d steps per timed step (FP64 C oracle, OpenMP)" % (
+        "x".join(map(str, SHAPE)), T_sample, T_STEPS)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -279,7 +286,7 @@ def run_gpu(args):
         pg = dist
     build.build()
 
-    c = synth.dyadic_coeffs(SEED, 2, 1, KIND)
+    c = synth.dyadic_coeffs(SEED, len(SHAPE), 1, KIND)
     x_host = synth.grid(SEED, SHAPE, np.float32)
     npts = float(np.prod(SHAPE))
     stream = torch.cuda.current_stream(dev)
@@ -410,8 +417,8 @@ def run_gpu(args):
         Ts = calibrate_oracle_steps(args.cpu_seconds)
         v, dt, cores = oracle_sample(Ts)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "full %dx%d grid, %d steps (%.1f s), FP64 C oracle" % (
-                   SHAPE[0], SHAPE[1], Ts, dt)}
+               "sample": "full %s grid, %d steps (%.1f s), FP64 C oracle" % (
+                   "x".join(map(str, SHAPE)), Ts, dt)}
 
     if rank == 0:
         line = {
@@ -428,7 +435,8 @@ def run_gpu(args):
                          "peak_source": peak_kind if bound == "hbm" else
                          ("MEASURED_PEAKS.json bf16_tflops_sustained" if bound == "tensor" else
                           "152 SMs x 128 FP32 FMA/clk x 2 flop x measured max SM clock"),
-                         "kernel": "k_tc2d" if engine == "tensor-core" else "k_sweep2d",
+                         "kernel": "k_tc2d" if engine == "tensor-core" else
+                                   ("k_sweep3d" if len(SHAPE) == 3 else "k_sweep2d"),
                          "pass_ms": pass_ms, "alg_bytes_per_launch": alg_bytes,
                          "alg_flops_per_launch": alg_flops,
                          "hbm_view": {"achieved_gbs": achieved, "peak_gbs": peak,
