@@ -222,11 +222,12 @@ def measure_variants(torch, binding, dev, stream, flush, args):
     """GStencil/s of the plain baseline and the other configurations."""
     out = {}
 
-    def single(name, shape, kind, seed, T, m, ndim=2, **opts):
-        c = synth.dyadic_coeffs(seed, ndim, 1, kind)
-        x = torch.from_numpy(synth.grid(seed, shape, np.float32)).to(dev)
+    def single(name, shape, kind, seed, T, m, ndim=2, dtype="f32", **opts):
+        c = synth.heat1d_coeffs() if kind == "heat" else synth.dyadic_coeffs(seed, ndim, 1, kind)
+        npdt = np.float64 if dtype == "f64" else np.float32
+        x = torch.from_numpy(synth.grid(seed, shape, npdt)).to(dev)
         y = torch.empty_like(x)
-        plan = binding.Plan(shape, c)
+        plan = binding.Plan(shape, c, dtype=dtype)
         for k, v in opts.items():
             plan.set_option(k, v)
         ms = _time_runs(torch, stream, flush, lambda: plan.run(x, y, T, fold_m=m, stream=stream))
@@ -238,6 +239,9 @@ def measure_variants(torch, binding, dev, stream, flush, args):
         del x, y
         torch.cuda.empty_cache()
 
+    s1 = synth.BASE_SEED + 1
+    single("heat1d_2pow20_T100_fp32", (1 << 20,), "heat", s1, 100, 1, ndim=1)
+    single("heat1d_2pow20_T100_fp64", (1 << 20,), "heat", s1, 100, 1, ndim=1, dtype="f64")
     s2 = synth.BASE_SEED + 2
     single("star4096_T1000_plain_fp32", (4096, 4096), "star", s2, 1000, 1, block_b=1)
     single("star4096_T1000_tc_bf16x3_m4", (4096, 4096), "star", s2, 1000, 4, precision=1)
