@@ -85,8 +85,11 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
  *   "block_b"       temporal-blocking depth: folded sweeps per memory round trip
  *                   (0 = automatic).
  *   "tile_y"        rows per CTA tile of the 2D CUDA-core sweep (0 = automatic).
- *   "stages"        TMA tile loads in flight per CTA of the 2D CUDA-core sweep,
- *                   2..6 (0 = automatic: 4 for single sweeps, 2 for blocked ones).
+ *   "stages"        TMA stages per CTA of the 2D CUDA-core sweep, 1..6 (0 =
+ *                   automatic: 4 for single sweeps; 2 for blocked ones, or 1 when
+ *                   two do not fit the tile).  A blocked pass refills a stage
+ *                   after the tile's first sweep, so 1 still overlaps copies with
+ *                   compute; a single-sweep pass with 1 stage does not.
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
  *   "tc_tma_store"  1 = tensor-core tiles leave through a TMA store when the
  *                   destination allows it (default 1); 0 = direct stores.

@@ -27,7 +27,7 @@ namespace sg {
 
 namespace {
 
-constexpr const char *kLibVersion = "1";
+constexpr const char *kLibVersion = "2";
 
 struct Cand {
     int engine;  // 0 CUDA core, 1 tensor core
@@ -139,7 +139,8 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
             if (sweep2d_supported(p->r, m, p->pattern))
                 for (int b : {1, 2, 3, 4, 6, 8})
                     if (b * R <= std::min(kGhost, nmin) && (m > 1 || b <= 8))
-                        for (int ty : {32, 64, 96}) cands.push_back({0, m, b, ty});
+                        for (int ty : {32, 64, 96, 128, 160})
+                            if (ty + 2 * b * R <= 256) cands.push_back({0, m, b, ty});
             if (m > 1 && p->precision != STENCIL_PREC_FP32 && tc2d_supported(R))
                 cands.push_back({1, m, 1, 0});
         }

@@ -66,26 +66,33 @@ __global__ void __launch_bounds__(threads2d<RB, M, PAT>(), min_blocks<RB, M>())
     };
 
     int tile = blockIdx.x;
+    // b == 1: the only sweep reads the stage, so NS-1 tiles are in flight
+    // while one is computed and a stage is refilled once its tile is done.
+    // b >= 2: the stage is free after the tile's first sweep, so it is
+    // refilled with the tile NS ahead right then (NS tiles in flight, and a
+    // single stage already overlaps the copy with sweeps 2..b).
+    const bool early = a.b >= 2;
     // (fault_withhold_copy is a test hook: the first copy is never issued, so
     // the bounded wait below must run out and report a timeout)
-    // prologue: the first NS-1 tiles of this CTA are requested at once
     if (tid == 0)
-        for (int k = 0; k < NS - 1; ++k) {
+        for (int k = 0; k < (early ? NS : NS - 1); ++k) {
             const int t = tile + k * gridDim.x;
             if (t < a.ntiles && !(k == 0 && a.fault_withhold_copy)) issue(t, k);
         }
 
     for (int i = 0; tile < a.ntiles; ++i, tile += gridDim.x) {
-        // keep NS-1 tiles in flight: request the one NS-1 ahead into the stage
-        // the previous tile released
-        const int ahead = tile + (NS - 1) * gridDim.x;
-        if (tid == 0 && ahead < a.ntiles) issue(ahead, (i + NS - 1) % NS);
+        if (!early) {
+            // request the tile NS-1 ahead into the stage the previous tile released
+            const int ahead = tile + (NS - 1) * gridDim.x;
+            if (tid == 0 && ahead < a.ntiles) issue(ahead, (i + NS - 1) % NS);
+        }
 
         const bool ok = mbar_wait_bounded(&bars[i % NS], (i / NS) & 1, a.wait_ns);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 record_status(a.status, DEV_TIMEOUT);
-                // let the copies already requested land before exiting
+                // let the copies already requested land before exiting: in
+                // both modes those are the tiles i+1 .. i+NS-1 of this CTA
                 for (int k = 1; k < NS; ++k) {
                     const int q = i + k;
                     if (tile + k * gridDim.x < a.ntiles)
@@ -97,9 +104,14 @@ __global__ void __launch_bounds__(threads2d<RB, M, PAT>(), min_blocks<RB, M>())
 
         const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
         const TileOut o{a.dst, a.dst_py, a.nx, a.ny, a.dst_gw, a.dst_vec4};
-        process_tile<RB, M, PAT>(buf(i % NS), buf(NS), buf(NS + 1), TY, H, HX, a.b,
-                                 ParamCoef{a.c}, o, tx * TX - HX, ty * TY - H,
-                                 min(TX, a.nx - tx * TX), min(TY, a.ny - ty * TY));
+        const int refill = tile + NS * gridDim.x;
+        const int st = i % NS;
+        auto stage_free = [&]() {
+            if (tid == 0 && refill < a.ntiles) issue(refill, st);
+        };
+        process_tile<RB, M, PAT>(buf(st), buf(NS), buf(NS + 1), TY, H, HX, a.b, ParamCoef{a.c},
+                                 o, tx * TX - HX, ty * TY - H, min(TX, a.nx - tx * TX),
+                                 min(TY, a.ny - ty * TY), stage_free);
         __syncthreads();
     }
 }

@@ -150,9 +150,16 @@ stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
     // plain single sweeps are memory-bound: small tiles, four in flight per
     // CTA; temporally blocked passes keep taller tiles and double buffering
     int ty = p->tile_y > 0 ? p->tile_y : (b == 1 ? 32 : 64);
-    const int ns = p->stages > 0 ? p->stages : (b == 1 ? 4 : 2);
+    int ns = p->stages > 0 ? p->stages : (b == 1 ? 4 : 2);
     int bf = 0;
     size_t smem = sweep2d_smem_bytes(ty, b, R, &bf, ns);
+    // a blocked pass refills its stage right after a tile's first sweep, so
+    // one stage still overlaps the copy with the other sweeps: drop the
+    // second stage before shrinking the tile
+    if (p->stages <= 0 && b >= 2 && smem > (size_t)p->max_smem) {
+        ns = 1;
+        smem = sweep2d_smem_bytes(ty, b, R, &bf, ns);
+    }
     while ((smem > (size_t)p->max_smem || ty + 2 * H > 256) && ty > 16) {
         ty -= 8;
         smem = sweep2d_smem_bytes(ty, b, R, &bf, ns);

@@ -262,7 +262,7 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
         if (v != 0 && (v < 8 || v > 192)) goto bad;
         p->tile_y = (int)v;
     } else if (!strcmp(key, "stages")) {
-        if (v < 0 || v > 6 || v == 1) goto bad;
+        if (v < 0 || v > 6) goto bad;
         p->stages = (int)v;
     } else if (!strcmp(key, "tc_center")) {
         if (v != 0 && v != 1) goto bad;

@@ -303,15 +303,23 @@ __device__ __forceinline__ void refresh_ghosts(const TileOut &o, int x0, int y0,
     }
 }
 
+// A callback that does nothing (see process_tile's stage_free).
+struct NoHook {
+    __device__ void operator()() const {}
+};
+
 // b fused sweeps of one staged tile: stage -> work buffers -> destination.
 // The staged box covers rows [0, TY + 2H) and columns [0, TX + 2HX), with the
 // output tile at rows [H, H + TY) and columns [HX, HX + TX).  Only the first
 // vy rows and vx columns of the tile lie inside the grid (a ragged last tile):
-// every sweep's region is clipped to what those outputs need.
-template <int RB, int M, int PAT, class Sync = CtaSync, class Coef>
+// every sweep's region is clipped to what those outputs need.  When b >= 2
+// only the first sweep reads the stage: stage_free() runs right after the
+// barrier that ends it, so the caller can refill the stage during the others.
+template <int RB, int M, int PAT, class Sync = CtaSync, class Coef, class Hook = NoHook>
 __device__ __forceinline__ void process_tile(const float *stage, float *work0, float *work1,
                                              int TY, int H, int HX, int b, const Coef &cf,
-                                             const TileOut &o, int gx0, int gy0, int vx, int vy)
+                                             const TileOut &o, int gx0, int gy0, int vx, int vy,
+                                             const Hook &stage_free = Hook())
 {
     constexpr int R = RB * M;
     const int SP = TX + 2 * HX;
@@ -324,6 +332,7 @@ __device__ __forceinline__ void process_tile(const float *stage, float *work0, f
         sweep_region<RB, M, PAT, false, Sync>(src, dst, SP, sh, 2 * H + vy - sh, c0 / 4,
                                               (c1 + 3) / 4, cf, o, gx0, gy0);
         Sync::sync();
+        if (s == 0) stage_free();
         src = dst;
     }
     sweep_region<RB, M, PAT, true, Sync>(src, nullptr, SP, H, H + vy, HX / 4, (HX + vx + 3) / 4,
