@@ -101,11 +101,13 @@ struct BatchArgs {
     int *next;                // queue head (zeroed before the launch)
     int tile_y;
     int buf_floats;
+    int nwork;                // work buffers: 2 if a pass fuses >= 3 sweeps, 1 for 2, else 0
     int *status;
     unsigned long long wait_ns;
 };
 bool batched_variant_supported(int rb, int m, int pattern);
-size_t batched_smem_bytes(int buf_floats);
+// Two TMA stages plus nwork (0..2) work buffers of buf_floats each.
+size_t batched_smem_bytes(int buf_floats, int nwork);
 int batched_ctas_per_sm(size_t smem);
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s);
 

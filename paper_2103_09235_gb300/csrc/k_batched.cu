@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(kThreadsBatched, 1) k_batched(const __grid_con
     float *cslot = reinterpret_cast<float *>(smem + 256);      // kCoefSlot weights per stage
     float *base = reinterpret_cast<float *>(smem + 1024) + BUF_PAD;
     auto stage = [&](int i) { return base + i * a.buf_floats; };  // two TMA stages
-    float *w0 = base + 2 * a.buf_floats, *w1 = base + 3 * a.buf_floats;
+    // work buffers after the stages (a pass of b fused sweeps touches b - 1 of them)
+    float *w0 = base + 2 * a.buf_floats, *w1 = a.nwork >= 2 ? base + 3 * a.buf_floats : w0;
     const int tid = threadIdx.x;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -252,11 +253,11 @@ bool batched_variant_supported(int rb, int m, int pattern)
     return rb == 1 && m >= 1 && ((pattern == PAT_STAR && m <= 4) || (pattern == PAT_BOX && m <= 2));
 }
 
-size_t batched_smem_bytes(int buf_floats)
+size_t batched_smem_bytes(int buf_floats, int nwork)
 {
-    // barriers, stage slots and weights in the first KB; two stages and two
+    // barriers, stage slots and weights in the first KB; two stages and the
     // work buffers after it
-    return 1024 + (size_t)4 * buf_floats * 4 + 2 * BUF_PAD * 4;
+    return 1024 + (size_t)(2 + nwork) * buf_floats * 4 + 2 * BUF_PAD * 4;
 }
 
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s)

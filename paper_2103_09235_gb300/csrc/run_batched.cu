@@ -14,7 +14,7 @@
 namespace sg {
 namespace {
 
-constexpr int kBatchTileY = 64;
+constexpr int kBatchTileYMax = 96;  // tallest tile tried; shortened until shared memory fits
 
 struct GridPlan {
     stencil_plan_s *p;
@@ -28,13 +28,14 @@ struct GridPlan {
 };
 
 // Fold depth and temporal-blocking depth for a grid of a batch, chosen from
-// the stencil pattern (measured on GB300: the folded star prefers m = 3 with
-// three fused sweeps, the box m = 2 with two) and clamped to the grid.
+// the stencil pattern (measured on GB300 with 96-row tiles: the folded star
+// prefers m = 3, the box m = 2, both with two fused sweeps) and clamped to
+// the grid.
 void choose_mb(const stencil_plan_s *p, int req_m, int *m_out, int *b_out)
 {
     const int nmin = std::min(p->nx, p->ny);
     int m = req_m > 0 ? req_m : (p->pattern == PAT_STAR ? 3 : 2);
-    int b = p->block_b > 0 ? p->block_b : (p->pattern == PAT_STAR ? 3 : 2);
+    int b = p->block_b > 0 ? p->block_b : 2;
     if (req_m == 1 && p->block_b == 0) b = 1;
     while (m > 1 && (2 * m * p->r + 1 > nmin || m * p->r > kGhost ||
                      !batched_variant_supported(p->r, m, p->pattern)))
@@ -43,6 +44,19 @@ void choose_mb(const stencil_plan_s *p, int req_m, int *m_out, int *b_out)
     while (b > 1 && b * m * p->r > max_halo) --b;
     *m_out = m;
     *b_out = b;
+}
+
+// The passes of one grid as (m, b) pairs: floor(T/m) folded sweeps in groups
+// of b, then the T mod m plain steps in groups of up to the ghost width.
+std::vector<std::pair<int, int>> grid_passes(const stencil_plan_s *p, int64_t T, int m, int b)
+{
+    std::vector<std::pair<int, int>> mb;
+    const int64_t q = T / m, rem = T % m;
+    const int max_halo = std::min(kGhost, std::min(p->nx, p->ny));
+    for (int64_t d = 0; d < q; d += b) mb.push_back({m, (int)std::min<int64_t>(b, q - d)});
+    for (int64_t d = 0; d < rem; d += max_halo)
+        mb.push_back({1, (int)std::min<int64_t>(max_halo, rem - d)});
+    return mb;
 }
 
 }  // namespace
@@ -92,6 +106,27 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
         std::vector<CUtensorMap> maps;
         std::vector<float> coefs;
         std::map<std::tuple<const void *, int, int>, int> map_index;
+        // one tile height for the whole batch: the tallest (up to 96 rows)
+        // whose two stages and work buffers fit for the widest halo
+        int max_h = 1, nwork = 0;
+        for (int g = 0; g < n; ++g) {
+            if (T[g] == 0) continue;
+            int m = 1, b = 1;
+            choose_mb(plans[g], fold_m ? fold_m[g] : 0, &m, &b);
+            for (auto &x : grid_passes(plans[g], T[g], m, b)) {
+                max_h = std::max(max_h, x.first * x.second);
+                nwork = std::max(nwork, x.second >= 3 ? 2 : x.second - 1);
+            }
+        }
+        int tile_y = kBatchTileYMax;
+        auto smem_for = [&](int ty, int *bf) {
+            sweep2d_smem_bytes(ty, max_h, 1, bf);
+            return batched_smem_bytes(*bf, nwork);
+        };
+        int bf_probe = 0;
+        while (tile_y > 16 && (smem_for(tile_y, &bf_probe) > (size_t)p0->max_smem ||
+                               tile_y + 2 * max_h > 256))
+            tile_y -= 16;
         int buf_floats = 0;
         for (int g = 0; g < n; ++g) {
             stencil_plan_s *p = plans[g];
@@ -103,7 +138,7 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
             choose_mb(p, fold_m ? fold_m[g] : 0, &G.m, &G.b);
             G.first_pass = (int)passes.size();
             G.npass = 0;
-            G.ntiles = ceil_div(p->nx, kTileX2D) * ceil_div(p->ny, kBatchTileY);
+            G.ntiles = ceil_div(p->nx, kTileX2D) * ceil_div(p->ny, tile_y);
             if (G.T == 0) continue;
             if (!batched_variant_supported(p->r, G.m, p->pattern)) {
                 set_error("stencil_run_batched: no batched kernel for m=%d", G.m);
@@ -125,12 +160,7 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
             const int off_m = add_block(*cm);
             const int off_1 = add_block(*c1);
             // passes: folded sweeps in groups of b, then the plain remainder
-            const int64_t q = G.T / G.m, rem = G.T % G.m;
-            const int max_halo = std::min(kGhost, std::min(p->nx, p->ny));
-            std::vector<std::pair<int, int>> mb;  // (m, b) per pass
-            for (int64_t d = 0; d < q; d += G.b) mb.push_back({G.m, (int)std::min<int64_t>(G.b, q - d)});
-            for (int64_t d = 0; d < rem; d += max_halo)
-                mb.push_back({1, (int)std::min<int64_t>(max_halo, rem - d)});
+            const std::vector<std::pair<int, int>> mb = grid_passes(p, G.T, G.m, G.b);
             G.gw = 0;
             for (auto &x : mb) G.gw = std::max(G.gw, x.first * x.second);
             const bool out_vec4 = (p->nx % 4 == 0) && ((uintptr_t)G.out % 16 == 0);
@@ -147,7 +177,7 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
                 ps.HX = round_up(ps.H, 4);
                 ps.tiles_x = ceil_div(p->nx, kTileX2D);
                 ps.ntiles = G.ntiles;
-                const int box0 = kTileX2D + 2 * ps.HX, box1 = kBatchTileY + 2 * ps.H;
+                const int box0 = kTileX2D + 2 * ps.HX, box1 = tile_y + 2 * ps.H;
                 auto mk = std::make_tuple((const void *)src.alloc, box0, box1);
                 auto it = map_index.find(mk);
                 if (it == map_index.end()) {
@@ -173,7 +203,7 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
                 ps.dst_gw = last ? 0 : G.gw;
                 ps.dst_vec4 = last ? (out_vec4 ? 1 : 0) : 1;
                 int bf = 0;
-                sweep2d_smem_bytes(kBatchTileY, bb, mm, &bf);
+                sweep2d_smem_bytes(tile_y, bb, mm, &bf);
                 buf_floats = std::max(buf_floats, bf);
                 passes.push_back(ps);
                 G.npass += 1;
@@ -230,11 +260,12 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
         a.coefs = reinterpret_cast<const float *>(dev + o_coef);
         a.done = reinterpret_cast<int *>(dev + o_done);
         a.next = a.done + passes.size();
-        a.tile_y = kBatchTileY;
+        a.tile_y = tile_y;
         a.buf_floats = buf_floats;
+        a.nwork = nwork;
         a.status = p0->d_status;
         a.wait_ns = (unsigned long long)p0->wait_ms * 1000000ull;
-        const size_t smem = batched_smem_bytes(buf_floats);
+        const size_t smem = batched_smem_bytes(buf_floats, nwork);
         if (smem > (size_t)p0->max_smem) {
             set_error("stencil_run_batched: shared memory");
             return STENCIL_ERR_UNSUPPORTED;
