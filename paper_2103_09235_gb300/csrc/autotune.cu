@@ -135,6 +135,8 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
                 for (int b : {16, 32, 64}) cands.push_back({0, m, b, 0});
         } else if (p->ndim == 3) {
             if (sweep3d_supported(p->r, m, p->pattern)) cands.push_back({0, m, 1, 0});
+            if (sweep3d_tb_supported(p->r, m, p->pattern) && 2 * R <= std::min(kGhost, nmin))
+                cands.push_back({0, m, 2, 0});
         } else {
             if (sweep2d_supported(p->r, m, p->pattern))
                 for (int b : {1, 2, 3, 4, 6, 8})

@@ -132,6 +132,14 @@ size_t sweep3d_smem_bytes(int tile_y, int R, int *buf_floats);
 cudaError_t launch_sweep3d(int rb, int m, int pattern, const CUtensorMap &map,
                            const Sweep3DArgs &a, int grid, size_t smem, cudaStream_t s);
 int sweep3d_ctas_per_sm(int rb, int m, int pattern, size_t smem);
+// Two fused 3D sweeps per launch (temporal blocking, b = 2): folded radius <= 2.
+// The staged boxes carry sweep3d_tb_halo_x() columns and 2R rows/planes of
+// halo per side; a.halo_x must be set to sweep3d_tb_halo_x().
+bool sweep3d_tb_supported(int rb, int m, int pattern);
+size_t sweep3d_tb_smem_bytes(int R, int *buf_floats);
+int sweep3d_tb_halo_x();
+cudaError_t launch_sweep3d_tb(int rb, int m, int pattern, const CUtensorMap &map,
+                              const Sweep3DArgs &a, int grid, size_t smem, cudaStream_t s);
 
 // ---- 1D sweep (FP32/FP64, temporally blocked in shared memory) ------------
 struct Sweep1DArgs {

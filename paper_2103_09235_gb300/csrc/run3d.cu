@@ -14,7 +14,8 @@ namespace {
 constexpr int kTX3 = 64, kTY3 = 16;
 }
 
-static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m,
+// One 3D pass of b (1 or 2) fused sweeps of c = c^(m).
+static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m, int b,
                                       const std::vector<double> &c, float *dst, int64_t dst_py,
                                       int64_t dst_pz, int dst_gw, bool dst_vec4, cudaStream_t s)
 {
@@ -26,21 +27,21 @@ static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int 
     a.tiles_x = ceil_div(p->nx, kTX3);
     a.tiles_y = ceil_div(p->ny, kTY3);
     a.ntiles_xy = a.tiles_x * a.tiles_y;
-    // z chunks of 16 planes for radius 1 and 32 for wider stencils (each chunk
-    // re-reads 2R planes of halo): many short CTAs balance the SMs and bound
-    // the tail; measured on GB300 at 512^3 and 256^3
-    int zc = R <= 1 ? 16 : 32;
+    // z chunks of 16 planes for a single radius-1 sweep and 32 otherwise (each
+    // chunk re-reads 2bR planes of halo): many short CTAs balance the SMs and
+    // bound the tail; measured on GB300 at 512^3 and 256^3
+    int zc = (b == 1 && R <= 1) ? 16 : 32;
     while (zc > 8 && (int64_t)a.ntiles_xy * ceil_div(p->nz, zc) < 4 * p->sm_count) zc /= 2;
     a.zchunk = zc;
     a.zchunks = ceil_div(p->nz, zc);
     a.ntiles = a.ntiles_xy * a.zchunks;
     a.tile_y = kTY3;
-    a.halo_x = round_up(R, 4);
+    a.halo_x = b == 2 ? sweep3d_tb_halo_x() : round_up(R, 4);
     a.map_x0 = src.gx;
     a.map_y0 = src.gy;
     a.map_z0 = src.gz;
     int bf = 0;
-    const size_t smem = sweep3d_smem_bytes(kTY3, R, &bf);
+    const size_t smem = b == 2 ? sweep3d_tb_smem_bytes(R, &bf) : sweep3d_smem_bytes(kTY3, R, &bf);
     a.buf_floats = bf;
     a.dst = dst;
     a.dst_py = dst_py;
@@ -50,11 +51,12 @@ static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int 
     a.status = p->d_status;
     a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
     for (size_t k = 0; k < c.size(); ++k) a.c[k] = (float)c[k];
-    // one 3D box per stage: 64+2HX columns, 16+2R rows, 4 planes
-    const int box[3] = {kTX3 + 2 * a.halo_x, kTY3 + 2 * R, 4};
+    // one 3D box per stage: 64+2HX columns, 16+2bR rows, 4 planes
+    const int box[3] = {kTX3 + 2 * a.halo_x, kTY3 + 2 * b * R, 4};
     const CUtensorMap *map = plan_map(p, src, box);
     if (!map) return STENCIL_ERR_CUDA;
-    cudaError_t e = launch_sweep3d(p->r, m, p->pattern, *map, a, a.ntiles, smem, s);
+    cudaError_t e = b == 2 ? launch_sweep3d_tb(p->r, m, p->pattern, *map, a, a.ntiles, smem, s)
+                           : launch_sweep3d(p->r, m, p->pattern, *map, a, a.ntiles, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "3D sweep launch");
     return STENCIL_OK;
 }
@@ -62,12 +64,19 @@ static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int 
 stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
                        cudaStream_t s)
 {
+    int b = p->block_b;
     if (m == 0) {
         if (p->tuned_m == 0 && p->autotune) {
             stencil_status_t st = autotune2d(p, s);
             if (st != STENCIL_OK) return st;
         }
         m = p->tuned_m > 0 ? p->tuned_m : 1;
+        if (b == 0) b = p->tuned_b;
+    }
+    if (b <= 0) b = 1;
+    if (b > 2) {
+        set_error("3D sweep: at most 2 fused sweeps per pass (block_b = %d)", b);
+        return STENCIL_ERR_UNSUPPORTED;
     }
     const int R = m * p->r;
     const int nmin = std::min(p->nx, std::min(p->ny, p->nz));
@@ -79,26 +88,37 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
         set_error("3D sweep: no kernel for r=%d m=%d", p->r, m);
         return STENCIL_ERR_UNSUPPORTED;
     }
+    if (b == 2 && (!sweep3d_tb_supported(p->r, m, p->pattern) || 2 * R > std::min(kGhost, nmin))) {
+        set_error("3D sweep: no fused pair of sweeps for r=%d m=%d on this grid", p->r, m);
+        return STENCIL_ERR_UNSUPPORTED;
+    }
     const std::vector<double> *cm = nullptr, *c1 = nullptr;
     stencil_status_t st = plan_folded(p, m, &cm);
     if (st == STENCIL_OK) st = plan_folded(p, 1, &c1);
     if (st == STENCIL_OK) st = ensure_padded(p);
     if (st != STENCIL_OK) return st;
     ensure_device_facts(p);
+    // passes as (m, fused sweeps): floor(T/m) folded sweeps in groups of b,
+    // then the T mod m plain steps, paired too when a fused plain pair exists
+    std::vector<std::pair<int, int>> passes;
     const int64_t q = T / m, rem = T % m;
-    const int64_t npass = q + rem;
-    const int gw = q ? R : p->r;
+    for (int64_t d = 0; d < q; d += b) passes.push_back({m, (int)std::min<int64_t>(b, q - d)});
+    const int b1 = (b == 2 && sweep3d_tb_supported(p->r, 1, p->pattern)) ? 2 : 1;
+    for (int64_t d = 0; d < rem; d += b1) passes.push_back({1, (int)std::min<int64_t>(b1, rem - d)});
+    // ghost band: the widest halo any pass reads
+    int gw = p->r;
+    for (auto &x : passes) gw = std::max(gw, x.first * x.second * p->r);
     const bool out_vec4 = (p->nx % 4 == 0) && ((uintptr_t)out % 16 == 0);
     auto enqueue = [&](cudaStream_t st_, int *nl) -> stencil_status_t {
         cudaError_t e = launch_import(p->A, in, gw, st_);
         if (e != cudaSuccess) return cuda_fail(e, "import launch");
         *nl += 1;
         const Padded *cur = &p->A, *oth = &p->B;
-        for (int64_t i = 0; i < npass; ++i) {
-            const bool last = i + 1 == npass;
-            const int mm = i < q ? m : 1;
+        for (size_t i = 0; i < passes.size(); ++i) {
+            const bool last = i + 1 == passes.size();
+            const int mm = passes[i].first, bb = passes[i].second;
             stencil_status_t r = launch_pass3d(
-                p, *cur, mm, mm == m ? *cm : *c1, last ? out : oth->origin,
+                p, *cur, mm, bb, mm == m ? *cm : *c1, last ? out : oth->origin,
                 last ? (int64_t)p->nx : oth->py, last ? (int64_t)p->nx * p->ny : oth->pz,
                 last ? 0 : gw, last ? out_vec4 : true, st_);
             if (r != STENCIL_OK) return r;
@@ -107,10 +127,11 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
         }
         return STENCIL_OK;
     };
-    std::vector<int64_t> key = {4, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, p->wait_ms};
+    std::vector<int64_t> key = {4, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, b,
+                                p->wait_ms};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
-    p->last_b = 1;
+    p->last_b = b;
     p->last_engine = 0;
     return st;
 }

@@ -100,18 +100,22 @@ def test_box8192_T512(env, box8192, m, opts):
         assert err <= 1e-5
 
 
-@pytest.mark.parametrize("shape,kind,m,seed", [((512, 512, 512), "star", 2, 4),
-                                               ((256, 256, 256), "box", 2, 5),
-                                               ((256, 256, 256), "box", 1, 5)])
-def test_3d_T200(env, shape, kind, m, seed):
-    """3D 7-point star 512^3 and 27-point box 256^3, T = 200, folded m = 2 (and plain)."""
+@pytest.mark.parametrize("shape,kind,m,b,seed", [((512, 512, 512), "star", 2, 1, 4),
+                                                 ((512, 512, 512), "star", 2, 2, 4),
+                                                 ((512, 512, 512), "star", 1, 2, 4),
+                                                 ((256, 256, 256), "box", 2, 1, 5),
+                                                 ((256, 256, 256), "box", 1, 1, 5),
+                                                 ((256, 256, 256), "box", 1, 2, 5)])
+def test_3d_T200(env, shape, kind, m, b, seed):
+    """3D 7-point star 512^3 and 27-point box 256^3, T = 200: plain, folded m = 2,
+    and two fused sweeps per pass (temporal blocking)."""
     _, _, oracle = env
     x = synth.grid(BASE + seed, shape, np.float32)
     c = synth.dyadic_coeffs(BASE + seed, 3, 1, kind)
-    y = run(env, shape, c, x, 200, m)
+    y = run(env, shape, c, x, 200, m, block_b=b)
     ref = oracle.spectral_run(x.astype(np.float64), c, 200)
     err = oracle.rel_l2(y, ref)
-    print("3d %s %s m=%d rel-L2 %.3e" % (shape, kind, m, err))
+    print("3d %s %s m=%d b=%d rel-L2 %.3e" % (shape, kind, m, b, err))
     assert err <= 1e-5
 
 

@@ -300,6 +300,44 @@ def test_sweep3d_parity(env, shape, kind, r, T, m):
     assert info["m"] == m
 
 
+CASES_3D_FUSED = [
+    # shape (z, y, x), kind, r, T, m: two fused sweeps per pass (block_b = 2)
+    ((100, 40, 70), "star", 1, 7, 1),    # three pairs and one single sweep
+    ((100, 40, 70), "box", 1, 6, 1),
+    ((100, 40, 70), "star", 1, 9, 2),    # two folded pairs, then the plain step
+    ((66, 33, 130), "box", 1, 10, 2),    # two pairs and one single folded sweep
+    ((40, 36, 64), "star", 2, 5, 1),
+    ((12, 9, 11), "star", 1, 6, 1),      # ghost bands overlapping in every axis
+    ((7, 6, 9), "box", 1, 5, 1),
+    ((150, 20, 24), "star", 1, 11, 2),   # many z chunks per tile column
+]
+
+
+@pytest.mark.parametrize("shape,kind,r,T,m", CASES_3D_FUSED)
+def test_sweep3d_fused_pairs(env, shape, kind, r, T, m):
+    """3D temporal blocking: two sweeps per HBM round trip match the oracle."""
+    _, _, oracle = env
+    c = synth.dyadic_coeffs(3400 + r, 3, r, kind)
+    x = synth.grid(3500 + T, shape, np.float32)
+    y, info = gpu_run(env, shape, c, x, T, m, block_b=2)
+    check(y, oracle.run(x.astype(np.float64), c, T))
+    assert info["m"] == m and info["b"] == 2
+
+
+def test_sweep3d_fused_pairs_rejects_wide(env):
+    """A fused pair needs folded radius <= 2 and a ghost band of 2R."""
+    torch, binding, _ = env
+    c = synth.dyadic_coeffs(3600, 3, 1, "star")
+    plan = binding.Plan((40, 40, 40), c).set_option("block_b", 2)
+    x = torch.zeros((40, 40, 40), device="cuda")
+    with pytest.raises(binding.StencilError) as ei:
+        plan.run(x, x, 12, fold_m=3)
+    assert ei.value.status == 2
+    with pytest.raises(binding.StencilError):
+        binding.Plan((40, 40, 40), c).set_option("block_b", 3).run(x, x, 12, fold_m=1)
+    plan.close()
+
+
 @pytest.mark.parametrize("shape,kind", [((300, 520), "star"), ((260, 300), "box"), ((6000,), "box"),
                                         ((40, 36, 70), "star")])
 def test_autotune_choice_is_correct_and_cached(env, shape, kind, tmp_path, monkeypatch):
