@@ -4,17 +4,18 @@
 //
 // A CTA owns a 64 x 16 (x, y) output column and a chunk of z planes, as in
 // the single-sweep kernel, and input planes arrive through the same
-// three-stage ring of 4-plane TMA boxes fed by a producer warp.  The boxes
-// carry 2R rows and 8 columns of halo per side.  For every input plane:
+// ring of 4-plane TMA boxes fed by a producer warp (two stages here).  The
+// boxes carry 2R rows and 8 columns of halo per side.  For every chunk of four
+// input planes:
 //   1. the first sweep, over the tile plus a rim of R cells (18 strips of 4
-//      columns by 16+2R rows, one per consumer thread), adds the plane into a
-//      register window along z; once the window's oldest intermediate plane
-//      is complete, its block goes to a shared-memory plane buffer (two of
-//      them, alternating);
+//      columns by 16+2R rows, one per consumer thread), adds each plane into
+//      a register window along z; every intermediate plane the window
+//      completes goes to a ring of eight shared-memory plane buffers;
 //   2. after one barrier over the consumer warps, the second sweep (16 x 16
-//      strips) reads that intermediate plane's neighbours from the buffer
-//      into its own window along z and stores every output plane it
-//      completes.
+//      strips) reads those intermediate planes' neighbours from the ring into
+//      its own window along z and stores every output plane it completes.
+// One barrier per four planes: the ring holds two chunks, so the next chunk's
+// first sweep writes only slots the second sweep finished before the barrier.
 // The rim's intermediate values come from the ghost-padded input (the band is
 // 2R wide), so they are the periodic values; only the tile is stored, and the
 // CTA then refreshes the ghost band of its output block as the single-sweep
@@ -31,6 +32,8 @@ constexpr int HXT = 8;                     // input halo columns per side (>= 2R
 constexpr int S1X = TX3 / 4 + 2;           // first-sweep strips: the tile plus 4 columns per side
 constexpr int SPT = TX3 + 2 * HXT;         // staged row pitch (floats)
 constexpr int SPP = TX3 + 8;               // intermediate-plane row pitch: x0-4 .. x0+68
+constexpr int NSTT = 2;                    // TMA stages (4 planes each)
+constexpr int NPS = 2 * ZC;                // intermediate-plane ring: two chunks' worth
 
 template <int RB, int M, int PAT>
 __global__ void __launch_bounds__(NTT)
@@ -41,13 +44,13 @@ __global__ void __launch_bounds__(NTT)
     constexpr int NSEG = 4 + 2 * RP;
     static_assert(RP <= 4 && S1X * (TY3 + 2 * R) <= NCT, "first sweep needs one thread per strip");
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // full[NST], then empty[NST]
-    uint64_t *empty = bars + NST;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);  // full[NSTT], then empty[NSTT]
+    uint64_t *empty = bars + NSTT;
     float *stages = reinterpret_cast<float *>(smem + 1024);
     constexpr int ROWS_IN = TY3 + 4 * R, ROWS_P = TY3 + 2 * R;
     constexpr int plane_in = SPT * ROWS_IN;
     constexpr int plane_p = (SPP * ROWS_P + 31) / 32 * 32;
-    float *pbuf = stages + NST * a.buf_floats;  // two intermediate planes
+    float *pbuf = stages + NSTT * a.buf_floats;  // ring of NPS intermediate planes
     const uint32_t chunk_bytes = (uint32_t)(plane_in * ZC * 4);
     const int tid = threadIdx.x;
 
@@ -61,7 +64,7 @@ __global__ void __launch_bounds__(NTT)
 
     if (tid == 0) {
         prefetch_tensormap(&map);
-        for (int s = 0; s < NST; ++s) {
+        for (int s = 0; s < NSTT; ++s) {
             mbar_init(&bars[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -69,13 +72,13 @@ __global__ void __launch_bounds__(NTT)
     }
     __syncthreads();
     if (tid >= NCT) {
-        // producer: chunk c (input planes 4c .. 4c+3) into stage c % NST once
-        // the consumers released the chunk NST earlier
+        // producer: chunk c (input planes 4c .. 4c+3) into stage c % NSTT once
+        // the consumers released the chunk NSTT earlier
         if (tid != NCT) return;
         int c = 0;
         for (; c < nchunks; ++c) {
-            const int s = c % NST;
-            if (c >= NST && !mbar_wait_bounded(&empty[s], ((c / NST) - 1) & 1, a.wait_ns)) {
+            const int s = c % NSTT;
+            if (c >= NSTT && !mbar_wait_bounded(&empty[s], ((c / NSTT) - 1) & 1, a.wait_ns)) {
                 record_status(a.status, DEV_TIMEOUT);
                 break;
             }
@@ -83,8 +86,8 @@ __global__ void __launch_bounds__(NTT)
             tma_load_3d(stages + s * a.buf_floats, &map, &bars[s], a.map_x0 + x0 - HXT,
                         a.map_y0 + y0 - 2 * R, a.map_z0 + zin0 + c * ZC);
         }
-        for (int q = max(0, c - NST); q < c; ++q)
-            mbar_wait_bounded(&bars[q % NST], (q / NST) & 1, a.wait_ns);
+        for (int q = max(0, c - NSTT); q < c; ++q)
+            mbar_wait_bounded(&bars[q % NSTT], (q / NSTT) & 1, a.wait_ns);
         return;
     }
 
@@ -148,36 +151,45 @@ __global__ void __launch_bounds__(NTT)
 
     bool failed = false;
     for (int c = 0; c < nchunks; ++c) {
-        const int s = c % NST;
-        const bool landed = mbar_wait_bounded(&bars[s], (c / NST) & 1, a.wait_ns);
+        const int s = c % NSTT;
+        const bool landed = mbar_wait_bounded(&bars[s], (c / NSTT) & 1, a.wait_ns);
         if (consumers_any3<NCT>(!landed)) {
             if (!landed) record_status(a.status, DEV_TIMEOUT);
             failed = true;
             break;
         }
         const float *chunk = stages + s * a.buf_floats;
+        const int pend = min(ZC, nin - c * ZC);  // planes of this chunk
+        // 1. first sweep over the chunk's planes: input plane p into w1; the
+        // intermediate plane p - 2R completes once 2R+1 input planes are in,
+        // and goes to slot (p - 2R) mod 8 of the plane ring
+        if (do1) {
 #pragma unroll 1
-        for (int q = 0; q < ZC; ++q) {
-            const int p = c * ZC + q;
-            if (p >= nin) break;
-            // 1. first sweep: the input plane into w1; an intermediate plane
-            // completes once 2R+1 input planes have been added
-            if (do1) {
+            for (int q = 0; q < pend; ++q) {
+                const int p = c * ZC + q;
                 // staged column of intermediate column 4*s1 is 4*s1 + 4; the
                 // strip's loads start RP columns to its left
                 accumulate(w1, chunk + q * plane_in + 4 * s1 + 4 - RP, SPT, r1 + R);
                 if (p >= 2 * R) {
-                    float *dst = pbuf + ((p - 2 * R) & 1) * plane_p + r1 * SPP + 4 * s1;
+                    float *dst = pbuf + ((p - 2 * R) & (NPS - 1)) * plane_p + r1 * SPP + 4 * s1;
                     *reinterpret_cast<float4 *>(dst) = make_float4(w1[0][0], w1[0][1], w1[0][2], w1[0][3]);
                 }
                 shift(w1);
             }
-            NamedBarrier<NCT>::sync();  // the intermediate plane is in its buffer
-            // 2. second sweep: intermediate plane p - 2R into w2; output plane
-            // z0 - 2R + (p - 2R) completes once 2R+1 of them have been added
-            if (do2 && p >= 2 * R) {
-                const int qi = p - 2 * R;
-                accumulate(w2, pbuf + (qi & 1) * plane_p + 4 * s2 + 4 - RP, SPP, r2 + R);
+        }
+        // the chunk's intermediate planes are in the ring and its stage has
+        // been read by every consumer
+        NamedBarrier<NCT>::sync();
+        if (tid == 0) mbar_arrive(&empty[s]);
+        // 2. second sweep over the same planes: intermediate plane qi into w2;
+        // output plane z0 - 2R + qi completes once 2R+1 of them are in.  The
+        // slots written by the next chunk were last read before this barrier.
+        if (do2) {
+#pragma unroll 1
+            for (int q = 0; q < pend; ++q) {
+                const int qi = c * ZC + q - 2 * R;
+                if (qi < 0) continue;
+                accumulate(w2, pbuf + (qi & (NPS - 1)) * plane_p + 4 * s2 + 4 - RP, SPP, r2 + R);
                 const int zo = z0 - 2 * R + qi;
                 if (zo >= z0 && live) {
                     float *row = a.dst + zo * a.dst_pz + Y * a.dst_py;
@@ -193,9 +205,6 @@ __global__ void __launch_bounds__(NTT)
                 shift(w2);
             }
         }
-        // every consumer passed the barrier of the chunk's last plane, so all
-        // reads of stage s are done
-        if (tid == 0) mbar_arrive(&empty[s]);
     }
     if (consumers_any3<NCT>(failed) || a.dst_gw <= 0) return;
     refresh_ghosts3<NCT>(a, x0, y0, z0, z1, tid);
@@ -249,7 +258,7 @@ size_t sweep3d_tb_smem_bytes(int R, int *buf_floats)
     const int bf = round_up(SPT * (TY3 + 4 * R) * ZC, 32);
     const int pp = round_up(SPP * (TY3 + 2 * R), 32);
     if (buf_floats) *buf_floats = bf;
-    return 1024 + ((size_t)NST * bf + 2 * pp) * 4;
+    return 1024 + ((size_t)NSTT * bf + (size_t)NPS * pp) * 4;
 }
 
 int sweep3d_tb_halo_x() { return HXT; }
