@@ -90,6 +90,9 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
  *                   two do not fit the tile).  A blocked pass refills a stage
  *                   after the tile's first sweep, so 1 still overlaps copies with
  *                   compute; a single-sweep pass with 1 stage does not.
+ *   "cta_threads"   threads per CTA of the 2D CUDA-core sweep: 0 = automatic
+ *                   (chosen by the autotuner, else the kernel's own size), 256 =
+ *                   two half-size CTAs per SM for folded sweeps that run 512.
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
  *   "tc_tma_store"  1 = tensor-core tiles leave through a TMA store when the
  *                   destination allows it (default 1); 0 = direct stores.

@@ -131,23 +131,33 @@ cudaError_t prepare_t()
     return once;
 }
 
+// Threads per CTA of a launch: the instance's own count, or 256 when asked
+// for and the instance runs 512 (the tile body adapts to its block size; two
+// 256-thread CTAs per SM then keep their barriers independent).
+template <int RB, int M, int PAT>
+int threads_t(int want)
+{
+    constexpr int full = threads2d<RB, M, PAT>();
+    return (want == 256 && full == 512) ? 256 : full;
+}
+
 template <int RB, int M, int PAT>
 cudaError_t launch_t(const CUtensorMap &map, const Sweep2DArgs &a, int grid, size_t smem,
-                     cudaStream_t s)
+                     int threads, cudaStream_t s)
 {
     cudaError_t e = prepare_t<RB, M, PAT>();
     if (e != cudaSuccess) return e;
-    k_sweep2d<RB, M, PAT><<<grid, threads2d<RB, M, PAT>(), smem, s>>>(map, a);
+    k_sweep2d<RB, M, PAT><<<grid, threads_t<RB, M, PAT>(threads), smem, s>>>(map, a);
     return cudaGetLastError();
 }
 
 template <int RB, int M, int PAT>
-int occupancy_t(size_t smem)
+int occupancy_t(size_t smem, int threads)
 {
     if (prepare_t<RB, M, PAT>() != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep2d<RB, M, PAT>,
-                                                      threads2d<RB, M, PAT>(), smem) !=
+                                                      threads_t<RB, M, PAT>(threads), smem) !=
         cudaSuccess)
         return 0;
     return n;
@@ -180,20 +190,22 @@ size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats, int nstages
     return 1024 + static_cast<size_t>(nbuf) * bf * 4;
 }
 
-int sweep2d_ctas_per_sm(int rb, int m, int pattern, size_t smem)
+int sweep2d_ctas_per_sm(int rb, int m, int pattern, size_t smem, int threads)
 {
 #define SG_X(RB_, M_, P_) \
-    if (rb == RB_ && m == M_ && pattern == P_) return occupancy_t<RB_, M_, P_>(smem);
+    if (rb == RB_ && m == M_ && pattern == P_) return occupancy_t<RB_, M_, P_>(smem, threads);
     SG_SWEEP2D_LIST(SG_X)
 #undef SG_X
     return 0;
 }
 
 cudaError_t launch_sweep2d(int rb, int m, int pattern, const CUtensorMap &map,
-                           const Sweep2DArgs &a, int grid, size_t smem, cudaStream_t s)
+                           const Sweep2DArgs &a, int grid, size_t smem, int threads,
+                           cudaStream_t s)
 {
 #define SG_X(RB_, M_, P_) \
-    if (rb == RB_ && m == M_ && pattern == P_) return launch_t<RB_, M_, P_>(map, a, grid, smem, s);
+    if (rb == RB_ && m == M_ && pattern == P_)  \
+        return launch_t<RB_, M_, P_>(map, a, grid, smem, threads, s);
     SG_SWEEP2D_LIST(SG_X)
 #undef SG_X
     return cudaErrorInvalidValue;

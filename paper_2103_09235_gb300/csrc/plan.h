@@ -25,6 +25,7 @@ struct stencil_plan_s {
     int block_b = 0;
     int tile_y = 0;
     int stages = 0;  // TMA stages per CTA of the 2D sweep (0 = automatic)
+    int cta_threads = 0;  // threads per CTA of the 2D sweep (0 = automatic, or 256)
     int tc_center = 1;
     int tc_tma_store = 1;
     int autotune = 1;
@@ -48,10 +49,10 @@ struct stencil_plan_s {
     // cached launch facts
     int sm_count = 0, max_smem = 0;
     struct PassCfg {
-        int ty, bf, grid, nstages;
+        int ty, bf, grid, nstages, threads;
         size_t smem;
     };
-    std::map<std::tuple<int, int, int>, PassCfg> pass_cfg;  // (m, b, tile_y option)
+    std::map<std::tuple<int, int, int>, PassCfg> pass_cfg;  // (m, b, tile/stage/thread options)
 
     // executable graphs of whole runs, keyed by everything a run enqueues
     struct GraphEnt {

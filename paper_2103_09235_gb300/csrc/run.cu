@@ -138,7 +138,7 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
 stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
                                       stencil_plan_s::PassCfg *cfg)
 {
-    auto key = std::make_tuple(m, b, p->tile_y * 8 + p->stages);
+    auto key = std::make_tuple(m, b, (p->tile_y * 8 + p->stages) * 1024 + p->cta_threads);
     auto it = p->pass_cfg.find(key);
     if (it != p->pass_cfg.end()) {
         *cfg = it->second;
@@ -169,7 +169,8 @@ stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
         return STENCIL_ERR_UNSUPPORTED;
     }
     const int ntiles = ceil_div(p->nx, kTileX2D) * ceil_div(p->ny, ty);
-    const int occ = std::max(1, sweep2d_ctas_per_sm(p->r, m, p->pattern, smem));
+    const int occ = std::max(1, sweep2d_ctas_per_sm(p->r, m, p->pattern, smem, p->cta_threads));
+    cfg->threads = p->cta_threads;
     cfg->ty = ty;
     cfg->nstages = ns;
     cfg->bf = bf;
@@ -213,7 +214,7 @@ stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int 
     const int box[2] = {kTileX2D + 2 * HX, cfg.ty + 2 * H};
     const CUtensorMap *map = plan_map(p, src, box);
     if (!map) return STENCIL_ERR_CUDA;
-    cudaError_t e = launch_sweep2d(p->r, m, p->pattern, *map, a, cfg.grid, cfg.smem, s);
+    cudaError_t e = launch_sweep2d(p->r, m, p->pattern, *map, a, cfg.grid, cfg.smem, cfg.threads, s);
     if (e != cudaSuccess) return cuda_fail(e, "2D sweep launch");
     return STENCIL_OK;
 }

@@ -261,6 +261,9 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "tile_y")) {
         if (v != 0 && (v < 8 || v > 192)) goto bad;
         p->tile_y = (int)v;
+    } else if (!strcmp(key, "cta_threads")) {
+        if (v != 0 && v != 256) goto bad;
+        p->cta_threads = (int)v;
     } else if (!strcmp(key, "stages")) {
         if (v < 0 || v > 6) goto bad;
         p->stages = (int)v;

@@ -91,13 +91,18 @@ def test_sweep2d_parity(env, shape, kind, r, T, m, b):
     assert info["m"] == m
 
 
-@pytest.mark.parametrize("tile_y", [16, 32, 48, 96])
-def test_sweep2d_tile_shapes(env, tile_y):
+@pytest.mark.parametrize("tile_y,stages,threads", [(16, 0, 0), (32, 0, 0), (48, 0, 0), (96, 0, 0),
+                                                   (128, 0, 0), (160, 1, 0), (64, 1, 0),
+                                                   (64, 2, 256), (96, 1, 256), (32, 3, 0)])
+def test_sweep2d_tile_shapes(env, tile_y, stages, threads):
+    """Tile heights, TMA stage counts (one stage: refilled after a tile's first
+    sweep) and half-size CTAs all give the oracle's result."""
     _, _, oracle = env
     shape = (250, 300)
     c = synth.dyadic_coeffs(7, 2, 1, "star")
     x = synth.grid(8, shape, np.float32)
-    y, _ = gpu_run(env, shape, c, x, 18, 2, block_b=3, tile_y=tile_y)
+    y, _ = gpu_run(env, shape, c, x, 18, 2, block_b=3, tile_y=tile_y, stages=stages,
+                   cta_threads=threads)
     check(y, oracle.run(x.astype(np.float64), c, 18))
 
 
@@ -212,23 +217,26 @@ def test_bad_fold_rejected(env):
     assert plan.run_status(x, x, -1, 1) == 1
 
 
-def test_bounded_wait_reports_timeout(env):
-    """A copy that never arrives ends the kernel's wait with a status, not a hang."""
+@pytest.mark.parametrize("m,b,stages", [(1, 1, 0), (2, 2, 0), (2, 2, 1)])
+def test_bounded_wait_reports_timeout(env, m, b, stages):
+    """A copy that never arrives ends the kernel's wait with a status, not a hang
+    (single sweeps, and blocked sweeps whose stage is refilled early)."""
     torch, binding, oracle = env
     shape = (200, 260)
     c = synth.dyadic_coeffs(21, 2, 1, "star")
     x = synth.grid(22, shape, np.float32)
-    plan = binding.Plan(shape, c)
+    plan = binding.Plan(shape, c).set_option("block_b", b).set_option("stages", stages)
     plan.set_option("wait_limit_ms", 50).set_option("fault_withhold_copy", 1)
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty_like(xd)
-    plan.run(xd, yd, 3, fold_m=1)
+    T = 2 * m * b
+    plan.run(xd, yd, T, fold_m=m)
     assert plan.sync_status() == 5
     assert plan.sync_status() == 0          # cleared
     plan.set_option("fault_withhold_copy", 0)
-    plan.run(xd, yd, 3, fold_m=1)            # the context is still usable
+    plan.run(xd, yd, T, fold_m=m)            # the context is still usable
     plan.sync()
-    check(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, 3))
+    check(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, T))
 
 
 def test_graph_replay_matches_direct_launches(env):
