@@ -248,9 +248,12 @@ def measure_variants(torch, binding, dev, stream, flush, args):
     s3 = synth.BASE_SEED + 3
     single("box8192_T512_plain_fp32", (8192, 8192), "box", s3, 512, 1, block_b=1)
     single("box8192_T512_cuda_core_m2b2", (8192, 8192), "box", s3, 512, 2, block_b=2)
+    single("box8192_T512_cuda_core_autotuned", (8192, 8192), "box", s3, 512, 0)
     single("box8192_T512_tc_bf16x3_m4", (8192, 8192), "box", s3, 512, 4, precision=1)
     single("box8192_T512_tc_bf16x3_m8", (8192, 8192), "box", s3, 512, 8, precision=1)
     single("star512cube_T200_plain", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1, ndim=3)
+    single("star512cube_T200_plain_fused2", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1,
+           ndim=3, block_b=2)
     single("star512cube_T200_m2", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 2, ndim=3)
     single("box256cube_T200_plain", (256, 256, 256), "box", synth.BASE_SEED + 5, 200, 1, ndim=3)
     single("box256cube_T200_m2", (256, 256, 256), "box", synth.BASE_SEED + 5, 200, 2, ndim=3)
@@ -298,6 +301,8 @@ def run_gpu(args):
     def make_plan(m, b, precision=0):
         plan = binding.Plan(SHAPE, c)
         plan.set_option("block_b", b).set_option("precision", precision)
+        if args.tile_y:
+            plan.set_option("tile_y", args.tile_y)
         return plan
 
     xd = torch.from_numpy(x_host).to(dev)
@@ -468,6 +473,8 @@ def main():
     ap.add_argument("--fold-m", type=int, default=0,
                     help="fold depth; 0 = the library's autotuner chooses m, b and the tile")
     ap.add_argument("--block-b", type=int, default=0)
+    ap.add_argument("--tile-y", type=int, default=0,
+                    help="rows per 2D tile (0 = the autotuner's or the library's choice)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="0 = FP32 CUDA cores, 1 = BF16x3 tensor cores, 2 = BF16x1")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
