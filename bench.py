@@ -435,7 +435,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": list(SHAPE), "T": T_STEPS,
-                       "fold_m": used_m, "block_b": used_b, "engine": engine,
+                       "fold_m": used_m, "block_b": used_b, "tile_y": plan.get("last_tile_y"),
+                       "engine": engine,
                        "precision": ["fp32", "bf16x3", "bf16x1"][args.precision],
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},

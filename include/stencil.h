@@ -110,7 +110,8 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, i
 
 /*
  * Reads a plan property.  Keys: "last_m", "last_b", "last_engine" (0 CUDA core,
- * 1 tensor core), "launches" (kernels the plan has launched so far),
+ * 1 tensor core), "last_tile_y" (rows per tile of the last 2D CUDA-core run's
+ * first pass), "launches" (kernels the plan has launched so far),
  * "scratch_bytes" (device bytes the plan owns).
  */
 stencil_status_t stencil_plan_get(stencil_plan_t plan, const char *key, int64_t *value);

@@ -27,7 +27,7 @@ namespace sg {
 
 namespace {
 
-constexpr const char *kLibVersion = "2";
+constexpr const char *kLibVersion = "3";
 
 struct Cand {
     int engine;  // 0 CUDA core, 1 tensor core

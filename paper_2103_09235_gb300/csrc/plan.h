@@ -68,6 +68,7 @@ struct stencil_plan_s {
     // bookkeeping
     long long launches = 0;
     int last_m = 0, last_b = 0, last_engine = 0;
+    int last_ty = 0;  // tile height of the last 2D CUDA-core run's first pass
     // autotuner choice for fold_m = 0: m, b, tile_y, engine (m = 0: not tuned yet)
     int tuned_m = 0, tuned_b = 0, tuned_ty = 0, tuned_engine = 0;
 };

@@ -274,10 +274,12 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
     int gw = 0;
     for (const Pass &ps : passes) gw = std::max(gw, ps.b * ps.m * p->r);
     // resolve every pass configuration before any capture starts
+    int first_ty = 0;
     for (const Pass &ps : passes) {
         stencil_plan_s::PassCfg cfg;
         st = pass2d_config(p, ps.m, ps.b, &cfg);
         if (st != STENCIL_OK) return st;
+        if (!first_ty) first_ty = cfg.ty;
     }
     const bool out_vec4 = (p->nx % 4 == 0) && ((uintptr_t)out % 16 == 0);
 
@@ -304,6 +306,7 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = b;
+    p->last_ty = first_ty;
     p->last_engine = 0;
     return st;
 }

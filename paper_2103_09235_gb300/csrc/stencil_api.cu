@@ -304,6 +304,7 @@ stencil_status_t stencil_plan_get(stencil_plan_t p, const char *key, int64_t *va
     }
     if (!strcmp(key, "last_m")) *value = p->last_m;
     else if (!strcmp(key, "last_b")) *value = p->last_b;
+    else if (!strcmp(key, "last_tile_y")) *value = p->last_ty;
     else if (!strcmp(key, "last_engine")) *value = p->last_engine;
     else if (!strcmp(key, "launches")) *value = p->launches;
     else if (!strcmp(key, "scratch_bytes")) *value = (int64_t)p->scratch_bytes;

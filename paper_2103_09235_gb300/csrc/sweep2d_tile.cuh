@@ -68,9 +68,13 @@ struct Strip {
             for (int b = -R; b <= R; ++b) n += TP::nz(a, b) ? 1 : 0;
         return n;
     }();
-    // rows of the steady loop unrolled together: a full turn of the window
-    // when the row's multiply-adds are few, so the window shift is renamed away
-    static constexpr int UNR = NNZ * 4 <= 200 ? W : 1;
+    // rows of the steady loop unrolled together.  Rolled (1), the window shift
+    // costs register moves; a full turn (W) renames them away but multiplies
+    // the code, and instruction-cache misses then cost more.  Measured on
+    // GB300: the plain 9-point box runs faster unrolled (737 vs 672 GS/s at
+    // 8192^2), every other instance rolled (plain star 778 vs 735, folded
+    // sweeps 1-11 % faster).
+    static constexpr int UNR = (PAT == PAT_BOX && R == 1) ? W : 1;
 
     __device__ __forceinline__ static void load(const float *rowp, float (&seg)[NSEG])
     {
