@@ -225,7 +225,7 @@ cudaError_t launch_grid_mean(const float *origin, int nx, int ny, int64_t py, do
 
 // ---- tensor maps ------------------------------------------------------------
 // Encodes a tiled FP32 tensor map over a padded grid's whole allocation.
-// box has P.ndim entries (x first).  Returns false if the driver refuses it.
+// box has P.ndim entries (x first).  Returns false if the encoder refuses it.
 bool encode_padded_map(CUtensorMap *map, const Padded &P, const int *box);
 // Encodes a 2D FP32 store map over exactly nx x ny elements at base (row
 // stride pitch elements) with 128-byte swizzle; false if unaligned or refused.
