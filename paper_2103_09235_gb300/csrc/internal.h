@@ -105,12 +105,13 @@ struct BatchArgs {
     int tile_y;
     int buf_floats;
     int nwork;                // work buffers: 2 if a pass fuses >= 3 sweeps, 1 for 2, else 0
+    int nstage;               // TMA stages: 1 (refilled after a tile's first sweep) or 2
     int *status;
     unsigned long long wait_ns;
 };
 bool batched_variant_supported(int rb, int m, int pattern);
-// Two TMA stages plus nwork (0..2) work buffers of buf_floats each.
-size_t batched_smem_bytes(int buf_floats, int nwork);
+// nstage TMA stages plus nwork (0..2) work buffers of buf_floats each.
+size_t batched_smem_bytes(int buf_floats, int nwork, int nstage);
 int batched_ctas_per_sm(size_t smem);
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s);
 

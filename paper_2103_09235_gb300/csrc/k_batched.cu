@@ -7,20 +7,24 @@
 // grids' first passes, then all grids' second passes, and so on.
 //
 // A CTA is 15 consumer warps that run the tile body and one producer warp
-// (one active lane) that feeds them through a two-stage ring:
+// (one active lane) that feeds them:
 //   producer: pop an item from the device queue (one atomic counter), wait
 //             (bounded) until every tile of the grid's previous pass is
-//             counted done, write the item's description into the stage's
-//             slot, and request the tile (2D TMA box) and the grid's folded
-//             weights (bulk copy) on the stage's "full" mbarrier;
+//             counted done, write the item's description into one of two
+//             slots and request the grid's folded weights (bulk copy) and,
+//             once the TMA stage is free, the tile (2D TMA box), all on the
+//             slot's "full" mbarrier;
 //   consumers: wait on "full", run the TMA-staged, register-window,
 //             temporally blocked tile body (the same one as the single-grid
-//             sweep, weights from shared memory), then release the stage on
-//             its "empty" mbarrier;
-//   producer: once a stage is released, publish its item (release fence and
+//             sweep, weights from shared memory), release the stage after the
+//             tile's first sweep (the later ones read only work buffers) and
+//             the slot when the tile is done;
+//   producer: once a slot is released, publish its item (release fence and
 //             an atomic add on the pass's done counter).
-// Scheduling therefore never stalls the consumers: while they compute one
-// item, the next one's copies are in flight.  Items only wait for items
+// With one stage refilled after the first sweep, the next tile's copy overlaps
+// the current tile's later sweeps, and the buffers left over allow tiles of up
+// to 128 rows.  Batches of single sweeps keep two stages instead.
+// Scheduling therefore never stalls the consumers.  Items only wait for items
 // earlier in the list, every CTA is resident, and a producer that waits on a
 // dependency keeps publishing the item its consumers are finishing, so the
 // queue cannot deadlock.  Every wait is bounded; on expiry the CTA records a
@@ -84,14 +88,16 @@ __device__ __forceinline__ bool consumers_any(bool v)
 }
 
 // Runs the tile body of the variant (pattern, m); radius-1 base stencils.
+template <class Hook>
 __device__ __forceinline__ void run_variant(const StageMeta &md, const float *stage, float *w0,
-                                            float *w1, int TY, const SmemCoef &cf)
+                                            float *w1, int TY, const SmemCoef &cf,
+                                            const Hook &stage_free)
 {
     const TileOut o{md.dst, md.dst_py, md.nx, md.ny, md.dst_gw, md.dst_vec4};
 #define SG_BATCHED_CASE(P_, M_)                                                                 \
     case P_ * 8 + M_:                                                                           \
         process_tile<1, M_, P_, ConsumerSync>(stage, w0, w1, TY, md.H, md.HX, md.b, cf, o,      \
-                                              md.gx0, md.gy0, md.vx, md.vy);                    \
+                                              md.gx0, md.gy0, md.vx, md.vy, stage_free);        \
         break;
     switch (md.variant) {
         SG_BATCHED_CASE(PAT_STAR, 1)
@@ -105,17 +111,23 @@ __device__ __forceinline__ void run_variant(const StageMeta &md, const float *st
 #undef SG_BATCHED_CASE
 }
 
-// The producer: one thread.  Stage s = k & 1 carries the CTA's k-th item.
-__device__ __forceinline__ void produce(const BatchArgs &a, uint64_t *full, uint64_t *empty,
-                                        StageMeta *meta, float *cslot, float *st0, float *st1)
+// The producer: one thread.  The CTA's k-th item uses description/weight slot
+// p = k & 1 (barriers full[p], done[p]) and TMA stage k % S (barrier
+// sfree[k % S]).  A stage is released after the item's first sweep when the
+// item fuses two or more (the later sweeps read only work buffers), else when
+// the item ends; a slot is released when the item ends.
+__device__ __forceinline__ void produce(const BatchArgs &a, uint64_t *full, uint64_t *done_bar,
+                                        uint64_t *sfree, StageMeta *meta, float *cslot,
+                                        float *stage0)
 {
-    // per stage: the pass of the item it holds, not yet published (-1: none),
-    // and that item's number k (registers, selected by stage)
+    const int S = a.nstage;
+    // per slot: the pass of the item it holds, not yet published (-1: none),
+    // and that item's number k (registers, selected by slot)
     int pp0 = -1, pp1 = -1, pk0 = 0, pk1 = 0;
-    auto pend_pass = [&](int s) { return s ? pp1 : pp0; };
-    auto pend_k = [&](int s) { return s ? pk1 : pk0; };
-    auto hold = [&](int s, int pass, int k) {
-        if (s) {
+    auto pend_pass = [&](int p) { return p ? pp1 : pp0; };
+    auto pend_k = [&](int p) { return p ? pk1 : pk0; };
+    auto hold = [&](int p, int pass, int k) {
+        if (p) {
             pp1 = pass;
             pk1 = k;
         } else {
@@ -123,27 +135,27 @@ __device__ __forceinline__ void produce(const BatchArgs &a, uint64_t *full, uint
             pk0 = k;
         }
     };
-    auto publish = [&](int s) {
-        __threadfence();  // the consumers' stores, acquired through the empty barrier
-        atomicAdd(&a.done[pend_pass(s)], 1);
-        hold(s, -1, pend_k(s));
+    auto publish = [&](int p) {
+        __threadfence();  // the consumers' stores, acquired through the done barrier
+        atomicAdd(&a.done[pend_pass(p)], 1);
+        hold(p, -1, pend_k(p));
     };
     bool ok = true;
     for (int k = 0;; ++k) {
-        const int s = k & 1;
+        const int p = k & 1;
         if (k >= 2) {
-            // refill stage s only after the consumers released item k - 2
-            if (!mbar_wait_bounded(&empty[s], ((k - 2) >> 1) & 1, a.wait_ns)) {
+            // reuse slot p only after the consumers finished item k - 2
+            if (!mbar_wait_bounded(&done_bar[p], ((k - 2) >> 1) & 1, a.wait_ns)) {
                 ok = false;
                 break;
             }
-            if (pend_pass(s) >= 0) publish(s);
+            if (pend_pass(p) >= 0) publish(p);
         }
-        StageMeta &md = meta[s];
+        StageMeta &md = meta[p];
         const int idx = atomicAdd(a.next, 1);
         if (idx >= a.nitems) {
             md.stop = 1;
-            mbar_arrive(&full[s]);
+            mbar_arrive(&full[p]);
             break;
         }
         const BatchItem item = a.items[idx];
@@ -154,8 +166,8 @@ __device__ __forceinline__ void produce(const BatchArgs &a, uint64_t *full, uint
             const uint64_t t0 = globaltimer_ns();
             while (ld_acquire(cnt) < need) {
                 // the item the consumers are finishing may be one this item waits for
-                const int o = s ^ 1;
-                if (pend_pass(o) >= 0 && mbar_test_wait(&empty[o], (pend_k(o) >> 1) & 1)) publish(o);
+                const int o = p ^ 1;
+                if (pend_pass(o) >= 0 && mbar_test_wait(&done_bar[o], (pend_k(o) >> 1) & 1)) publish(o);
                 if (globaltimer_ns() - t0 > a.wait_ns) {
                     ok = false;
                     break;
@@ -163,7 +175,7 @@ __device__ __forceinline__ void produce(const BatchArgs &a, uint64_t *full, uint
             }
             if (!ok) {
                 md.stop = 2;
-                mbar_arrive(&full[s]);
+                mbar_arrive(&full[p]);
                 break;
             }
         }
@@ -186,62 +198,85 @@ __device__ __forceinline__ void produce(const BatchArgs &a, uint64_t *full, uint
         const uint32_t tile_bytes =
             (uint32_t)((kTileX2D + 2 * ps.HX) * (a.tile_y + 2 * ps.H) * 4);
         const uint32_t coef_bytes = (uint32_t)(((ps.ncoef + 3) & ~3) * 4);
+        mbar_arrive_expect_tx(&full[p], tile_bytes + coef_bytes);
+        bulk_load(cslot + p * kCoefSlot, a.coefs + ps.coef, coef_bytes, &full[p]);
+        // the stage must have been released by item k - S.  After a timeout
+        // the copy is still requested (the results are void by then): the
+        // slot's barrier then completes, and the drain below lets every
+        // requested copy land before the CTA exits
+        const int st = k % S;
+        const bool stage_ok =
+            k < S || mbar_wait_bounded(&sfree[st], ((k - S) / S) & 1, a.wait_ns);
         fence_proxy_async_global();  // other CTAs' stores, acquired above, before the copy reads them
-        mbar_arrive_expect_tx(&full[s], tile_bytes + coef_bytes);
-        tma_load_2d(s ? st1 : st0, &a.maps[ps.map], &full[s], ps.map_x0 + tx * kTileX2D - ps.HX,
-                    ps.map_y0 + ty * a.tile_y - ps.H);
-        bulk_load(cslot + s * kCoefSlot, a.coefs + ps.coef, coef_bytes, &full[s]);
-        hold(s, item.pass, k);
+        tma_load_2d(stage0 + st * a.buf_floats, &a.maps[ps.map], &full[p],
+                    ps.map_x0 + tx * kTileX2D - ps.HX, ps.map_y0 + ty * a.tile_y - ps.H);
+        hold(p, item.pass, k);
+        if (!stage_ok) {
+            ok = false;
+            break;
+        }
     }
     if (!ok) record_status(a.status, DEV_TIMEOUT);
     // publish what the consumers still finish; if they stopped, let the
     // requested copies land before the CTA exits
-    for (int s = 0; s < 2; ++s) {
-        if (pend_pass(s) < 0) continue;
-        const uint32_t par = (pend_k(s) >> 1) & 1;
-        if (mbar_wait_bounded(&empty[s], par, a.wait_ns))
-            publish(s);
+    for (int p = 0; p < 2; ++p) {
+        if (pend_pass(p) < 0) continue;
+        const uint32_t par = (pend_k(p) >> 1) & 1;
+        if (mbar_wait_bounded(&done_bar[p], par, a.wait_ns))
+            publish(p);
         else
-            mbar_wait_bounded(&full[s], par, a.wait_ns);
+            mbar_wait_bounded(&full[p], par, a.wait_ns);
     }
 }
 
 __global__ void __launch_bounds__(kThreadsBatched, 1) k_batched(const __grid_constant__ BatchArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // full[2], then empty[2]
-    uint64_t *empty = full + 2;
-    StageMeta *meta = reinterpret_cast<StageMeta *>(smem + 64);  // one slot per stage
-    float *cslot = reinterpret_cast<float *>(smem + 256);      // kCoefSlot weights per stage
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // full[2], done[2], sfree[2]
+    uint64_t *done_bar = full + 2;
+    uint64_t *sfree = full + 4;
+    StageMeta *meta = reinterpret_cast<StageMeta *>(smem + 64);  // one per slot
+    float *cslot = reinterpret_cast<float *>(smem + 256);      // kCoefSlot weights per slot
     float *base = reinterpret_cast<float *>(smem + 1024) + BUF_PAD;
-    auto stage = [&](int i) { return base + i * a.buf_floats; };  // two TMA stages
+    const int S = a.nstage;  // TMA stages at base, base + buf_floats
     // work buffers after the stages (a pass of b fused sweeps touches b - 1 of them)
-    float *w0 = base + 2 * a.buf_floats, *w1 = a.nwork >= 2 ? base + 3 * a.buf_floats : w0;
+    float *w0 = base + S * a.buf_floats;
+    float *w1 = a.nwork >= 2 ? base + (S + 1) * a.buf_floats : w0;
     const int tid = threadIdx.x;
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&done_bar[i], 1);
+            mbar_init(&sfree[i], 1);
         }
         fence_mbar_init();
     }
     __syncthreads();
     if (tid >= kConsumers) {
-        if (tid == kConsumers) produce(a, full, empty, meta, cslot, stage(0), stage(1));
+        if (tid == kConsumers) produce(a, full, done_bar, sfree, meta, cslot, base);
         return;
     }
     for (int k = 0;; ++k) {
-        const int s = k & 1;
-        const bool landed = mbar_wait_bounded(&full[s], (k >> 1) & 1, a.wait_ns);
+        const int p = k & 1;
+        const bool landed = mbar_wait_bounded(&full[p], (k >> 1) & 1, a.wait_ns);
         if (consumers_any(!landed)) {
             if (tid == 0) record_status(a.status, DEV_TIMEOUT);
             break;
         }
-        const StageMeta md = meta[s];
+        const StageMeta md = meta[p];
         if (md.stop) break;
-        run_variant(md, stage(s), w0, w1, a.tile_y, SmemCoef{cslot + s * kCoefSlot});
-        ConsumerSync::sync();  // stage, slot and work buffers are free again
-        if (tid == 0) mbar_arrive(&empty[s]);
+        uint64_t *free_bar = &sfree[k % S];
+        // b >= 2: the stage is free once the first sweep is done
+        auto stage_free = [&]() {
+            if (tid == 0) mbar_arrive(free_bar);
+        };
+        run_variant(md, base + (k % S) * a.buf_floats, w0, w1, a.tile_y,
+                    SmemCoef{cslot + p * kCoefSlot}, stage_free);
+        ConsumerSync::sync();  // the item's buffers and slot are free again
+        if (tid == 0) {
+            if (md.b < 2) mbar_arrive(free_bar);
+            mbar_arrive(&done_bar[p]);
+        }
     }
 }
 
@@ -253,11 +288,11 @@ bool batched_variant_supported(int rb, int m, int pattern)
     return rb == 1 && m >= 1 && ((pattern == PAT_STAR && m <= 4) || (pattern == PAT_BOX && m <= 2));
 }
 
-size_t batched_smem_bytes(int buf_floats, int nwork)
+size_t batched_smem_bytes(int buf_floats, int nwork, int nstage)
 {
-    // barriers, stage slots and weights in the first KB; two stages and the
+    // barriers, item slots and weights in the first KB; the stages and the
     // work buffers after it
-    return 1024 + (size_t)(2 + nwork) * buf_floats * 4 + 2 * BUF_PAD * 4;
+    return 1024 + (size_t)(nstage + nwork) * buf_floats * 4 + 2 * BUF_PAD * 4;
 }
 
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s)

@@ -14,7 +14,7 @@
 namespace sg {
 namespace {
 
-constexpr int kBatchTileYMax = 96;  // tallest tile tried; shortened until shared memory fits
+constexpr int kBatchTileYMax = 128;  // tallest tile tried; shortened until shared memory fits
 
 struct GridPlan {
     stencil_plan_s *p;
@@ -106,8 +106,10 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
         std::vector<CUtensorMap> maps;
         std::vector<float> coefs;
         std::map<std::tuple<const void *, int, int>, int> map_index;
-        // one tile height for the whole batch: the tallest (up to 96 rows)
-        // whose two stages and work buffers fit for the widest halo
+        // one tile height for the whole batch: the tallest (up to 128 rows)
+        // whose stages and work buffers fit for the widest halo.  Passes that
+        // fuse sweeps free their stage after the first one, so one stage
+        // suffices; batches of single sweeps keep two.
         int max_h = 1, nwork = 0;
         for (int g = 0; g < n; ++g) {
             if (T[g] == 0) continue;
@@ -118,10 +120,11 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
                 nwork = std::max(nwork, x.second >= 3 ? 2 : x.second - 1);
             }
         }
+        const int nstage = nwork > 0 ? 1 : 2;
         int tile_y = kBatchTileYMax;
         auto smem_for = [&](int ty, int *bf) {
             sweep2d_smem_bytes(ty, max_h, 1, bf);
-            return batched_smem_bytes(*bf, nwork);
+            return batched_smem_bytes(*bf, nwork, nstage);
         };
         int bf_probe = 0;
         while (tile_y > 16 && (smem_for(tile_y, &bf_probe) > (size_t)p0->max_smem ||
@@ -263,9 +266,10 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
         a.tile_y = tile_y;
         a.buf_floats = buf_floats;
         a.nwork = nwork;
+        a.nstage = nstage;
         a.status = p0->d_status;
         a.wait_ns = (unsigned long long)p0->wait_ms * 1000000ull;
-        const size_t smem = batched_smem_bytes(buf_floats, nwork);
+        const size_t smem = batched_smem_bytes(buf_floats, nwork, nstage);
         if (smem > (size_t)p0->max_smem) {
             set_error("stencil_run_batched: shared memory");
             return STENCIL_ERR_UNSUPPORTED;
