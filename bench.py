@@ -279,6 +279,22 @@ def measure_variants(torch, binding, dev, stream, flush, args):
     return out
 
 
+def max_over_ranks(torch, value: float, pg, device) -> float:
+    """The largest of every rank's value (the whole job ends with its slowest
+    rank); the value itself on one rank."""
+    if pg is None:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws: int, npts: float, T: int, steps: int, ms_total: float) -> float:
+    """GStencil/s of the whole job: every rank advances its own copy of the
+    workload (replicas), so the job updates ws * npts * T points per step."""
+    return ws * npts * T * steps / (ms_total * 1e-3) / 1e9
+
+
 def run_gpu(args):
     import torch
     from paper_2103_09235_gb300 import build, binding
@@ -342,12 +358,8 @@ def run_gpu(args):
     if pg:
         pg.barrier()
     ms_step = statistics.mean(times)
-    ms_total = sum(times)
-    if pg:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = ws * npts * T_STEPS * args.steps / (ms_total * 1e-3) / 1e9
+    ms_total = max_over_ranks(torch, sum(times), pg, dev)
+    value = whole_job_rate(ws, npts, T_STEPS, args.steps, ms_total)
     used_m, used_b = plan.get("last_m"), plan.get("last_b")
     engine = "tensor-core" if plan.get("last_engine") == 1 else "cuda-core"
     if args.ncu:
@@ -408,12 +420,8 @@ def run_gpu(args):
         e1.record(stream)
         e1.synchronize()
         e_times.append(e0.elapsed_time(e1))
-    e2e_total = sum(e_times)
-    if pg:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e = ws * npts * T_STEPS * args.steps / (e2e_total * 1e-3) / 1e9
+    e2e_total = max_over_ranks(torch, sum(e_times), pg, dev)
+    e2e = whole_job_rate(ws, npts, T_STEPS, args.steps, e2e_total)
 
     # --- the other configurations of the workload family, each timed the same
     # way (events around whole runs, L2 flushed between runs); reported beside
