@@ -235,6 +235,8 @@ def measure_variants(torch, binding, dev, stream, flush, args):
         out[name] = {"gstencil_s": float(np.prod(shape)) * T / (ms * 1e-3) / 1e9, "ms": ms,
                      "m": plan.get("last_m"), "b": plan.get("last_b"),
                      "engine": "tensor-core" if plan.get("last_engine") else "cuda-core"}
+        if plan.get("last_engine"):
+            out[name]["tc_kernel"] = "grouped" if plan.get("last_tc_form") == 2 else "per-offset"
         plan.close()
         del x, y
         torch.cuda.empty_cache()
@@ -250,7 +252,10 @@ def measure_variants(torch, binding, dev, stream, flush, args):
     single("box8192_T512_cuda_core_m2b2", (8192, 8192), "box", s3, 512, 2, block_b=2)
     single("box8192_T512_cuda_core_autotuned", (8192, 8192), "box", s3, 512, 0)
     single("box8192_T512_tc_bf16x3_m4", (8192, 8192), "box", s3, 512, 4, precision=1)
+    single("box8192_T512_tc_bf16x3_m6", (8192, 8192), "box", s3, 512, 6, precision=1)
     single("box8192_T512_tc_bf16x3_m8", (8192, 8192), "box", s3, 512, 8, precision=1)
+    single("box8192_T512_tc_bf16x3_m8_per_offset", (8192, 8192), "box", s3, 512, 8, precision=1,
+           tc_form=1)
     single("star512cube_T200_plain", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1, ndim=3)
     single("star512cube_T200_plain_fused2", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1,
            ndim=3, block_b=2)
@@ -317,6 +322,7 @@ def run_gpu(args):
     def make_plan(m, b, precision=0):
         plan = binding.Plan(SHAPE, c)
         plan.set_option("block_b", b).set_option("precision", precision)
+        plan.set_option("tc_form", args.tc_form)
         if args.tile_y:
             plan.set_option("tile_y", args.tile_y)
         return plan
@@ -362,6 +368,7 @@ def run_gpu(args):
     value = whole_job_rate(ws, npts, T_STEPS, args.steps, ms_total)
     used_m, used_b = plan.get("last_m"), plan.get("last_b")
     engine = "tensor-core" if plan.get("last_engine") == 1 else "cuda-core"
+    grouped = engine == "tensor-core" and plan.get("last_tc_form") == 2
     if args.ncu:
         # profiling run: only the timed loop above, nothing else
         if rank == 0:
@@ -399,7 +406,8 @@ def run_gpu(args):
         try:
             with open(tfile) as f:
                 tr = json.load(f)
-            key = "%s_%s_m%d_b%d" % (args.config, engine, used_m, used_b)
+            key = "%s_%s_m%d_b%d" % (args.config, engine + ("-grouped" if grouped else ""),
+                                     used_m, used_b)
             traffic = tr.get(key)
         except Exception:
             traffic = None
@@ -453,7 +461,8 @@ def run_gpu(args):
                          "peak_source": peak_kind if bound == "hbm" else
                          ("MEASURED_PEAKS.json bf16_tflops_sustained" if bound == "tensor" else
                           "152 SMs x 128 FP32 FMA/clk x 2 flop x measured max SM clock"),
-                         "kernel": "k_tc2d" if engine == "tensor-core" else
+                         "kernel": ("k_tc2d_grouped" if grouped else "k_tc2d")
+                                   if engine == "tensor-core" else
                                    ("k_sweep3d" if len(SHAPE) == 3 else "k_sweep2d"),
                          "pass_ms": pass_ms, "alg_bytes_per_launch": alg_bytes,
                          "alg_flops_per_launch": alg_flops,
@@ -484,6 +493,8 @@ def main():
     ap.add_argument("--block-b", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0,
                     help="rows per 2D tile (0 = the autotuner's or the library's choice)")
+    ap.add_argument("--tc-form", type=int, default=0, choices=[0, 1, 2],
+                    help="tensor-core kernel: 0 by folded radius, 1 per row offset, 2 grouped")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="0 = FP32 CUDA cores, 1 = BF16x3 tensor cores, 2 = BF16x1")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -94,7 +94,12 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
  *                   (chosen by the autotuner, else the kernel's own size), 256 =
  *                   two half-size CTAs per SM for folded sweeps that run 512.
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
- *   "tc_tma_store"  1 = tensor-core tiles leave through a TMA store when the
+ *   "tc_form"       tensor-core kernel: 1 = one MMA per row offset of the folded
+ *                   weights (the row shift applied through the operand descriptor);
+ *                   2 = four row offsets per MMA, the remaining shifts done in the
+ *                   epilogue (fewer, wider MMAs; 125-row tiles); 0 = by the folded
+ *                   radius: grouped from R = m*r >= 6 (default).
+ *   "tc_tma_store"  1 = per-offset tensor-core tiles leave through a TMA store when the
  *                   destination allows it (default 1); 0 = direct stores.
  *   "wait_limit_ms" bound of every device-side wait (default 2000).
  *   "autotune"      1 = time candidates when stencil_run gets fold_m = 0 (default 1).
@@ -111,7 +116,8 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, i
 /*
  * Reads a plan property.  Keys: "last_m", "last_b", "last_engine" (0 CUDA core,
  * 1 tensor core), "last_tile_y" (rows per tile of the last 2D CUDA-core run's
- * first pass), "launches" (kernels the plan has launched so far),
+ * first pass), "last_tc_form" (1 per-offset, 2 grouped: the tensor-core kernel
+ * of the last tensor-core run), "launches" (kernels the plan has launched so far),
  * "scratch_bytes" (device bytes the plan owns).
  */
 stencil_status_t stencil_plan_get(stencil_plan_t plan, const char *key, int64_t *value);

@@ -189,6 +189,9 @@ constexpr int kTcK = 48;
 constexpr int kTcKC = kTcK / 8;                 // 16-byte K chunks
 constexpr int kTcMaxR = 8;
 constexpr int kTcPanelElems = 64 * kTcK;        // one row offset: C_hi (32 rows) over C_lo (32 rows)
+constexpr int kTcGroup = 4;                     // grouped form: row offsets per MMA
+constexpr int kTcOutRows = kTcM - (kTcGroup - 1);  // grouped form: output rows per tile
+constexpr int kTcGroupedMinR = 6;               // folded radius from which the grouped form is used
 constexpr int kTcThreads = 384;
 
 struct TC2DArgs {
@@ -199,6 +202,7 @@ struct TC2DArgs {
     int box_w;              // staging box width (floats)
     int rows;               // 128 + 2R staged rows
     int rows_p;             // A-operand rows per K chunk in shared memory (odd)
+    int nstage;             // grouped form: FP32 staging slots (1 or 2)
     int terms;              // 3: hi*hi + hi*lo + lo*hi, 1: hi*hi
     int map_x0, map_y0;     // tensor-map coordinates of the interior origin
     const double *mean_sum; // grid sum; mu = mean_sum[0] * inv_n (null: mu = 0)
@@ -215,6 +219,13 @@ struct TC2DArgs {
 };
 bool tc2d_supported(int R);
 size_t tc2d_smem_bytes(int R, bool tma_store);
+// Grouped form (k_tc2d_grouped.cu): four row offsets per MMA, 125 output rows
+// of 32 columns per tile, direct stores.
+size_t tc2dg_smem_bytes(int R, int nstage);
+size_t tc2dg_panel_elems(int R);
+double tc2dg_build_panels(const double *cm, int R, uint16_t *host_out);
+cudaError_t launch_tc2dg(const CUtensorMap &map, const TC2DArgs &a, int grid, size_t smem,
+                         cudaStream_t s);
 // Builds the (2R+1) BF16 Toeplitz panels of folded weights cm ((2R+1)^2,
 // row-major (dy, dx)) with the hi/lo split and the mass correction; returns
 // the FP64 sum of cm, which the epilogue multiplies by mu.

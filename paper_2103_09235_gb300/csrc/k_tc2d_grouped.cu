@@ -1,0 +1,550 @@
+// Folded 2D box sweep on the tcgen05 tensor cores, grouped form (BF16 hi/lo,
+// FP32 accumulate): four row offsets per MMA.  Used for wide folds (R >= 6),
+// where the per-offset kernel of k_tc2d.cu issues the most MMAs.
+//
+// One sweep applies the folded weights c^(m) (radius R = m*r, Section 3.2):
+//   out[y][x0+n] = sum_{a=0..2R} sum_k X[y+a][x0-R+k] * T_a[k][n],
+// with the tile's input rows starting R above its outputs and T_a the banded
+// Toeplitz matrix holding row a of c^(m) (T_a[k][n] = c[a][k-n] for
+// 0 <= k-n <= 2R).  This is the paper's vertical and horizontal folding
+// (Section 3.3, Eq. vfold and Eq. horifold) written as dense contractions
+// over the tile's 48-column window; the partial sums the paper keeps in
+// vector registers accumulate in tensor memory instead.
+//
+// Row offsets go four at a time into one MMA.  For the group of offsets
+// a = 4g .. 4g+3 the A operand is the tile's rows shifted down by 4g (the
+// no-swizzle K-major layout puts rows 16 bytes apart, so the shift is a move
+// of the descriptor start, not a copy) and B holds T_4g .. T_4g+3 side by side
+// in N.  Accumulating every group into the same tensor-memory columns gives
+//   D[l][j][n] = sum_g sum_k X[l+4g][k] T_{4g+j}[k][n],
+// and the epilogue finishes the remaining shifts: out[y][n] = sum_{j<4}
+// D[y+j][j][n] (warp shuffles, and a hand-over of three rows between warps).
+// An MMA on this part costs about the same whatever its N up to 256, so
+// grouping divides the MMA count by about four at the price of 3 of the 128
+// rows.
+//
+// Tile: 128 input rows (the MMA's M) give 125 output rows of 32 columns.  The
+// FP32 rows arrive by TMA; converter warps subtract the grid mean mu, split
+// v = x - mu into v_hi = bf16(v) and v_lo = bf16(v - v_hi) and write both in
+// the no-swizzle K-major layout.  Per (group, K step) one MMA of N = 256
+// multiplies v_hi by [T_hi | T_lo] and one of N = 128 multiplies v_lo by T_hi;
+// the epilogue adds the two halves and mu * sum(c) and stores the rows
+// directly.  Toeplitz panels stay resident in shared memory.
+//
+// Warp roles (384 threads): warp 0 issues TMA loads, warp 1 owns tensor
+// memory and issues the MMAs (one thread), warps 4-7 convert, warps 8-11
+// drain the accumulator to global memory.  Every wait is bounded; a wait that
+// runs out records a timeout, raises an abort flag that ends the other roles'
+// waits, lets in-flight copies and MMAs land, frees tensor memory and returns.
+// Every operand and accumulator range is checked against its buffer before
+// use; a range out of bounds records a device-check status and is skipped.
+#include <cuda_bf16.h>
+
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace sg {
+namespace {
+
+constexpr int NT = kTcThreads;
+constexpr int GRP = kTcGroup;                 // row offsets per MMA
+constexpr int OUT_ROWS = kTcOutRows;          // output rows per tile: 128 - (GRP - 1)
+constexpr int PANEL_ROWS = 2 * GRP * kTcN;    // [T_hi of the group | T_lo of the group]
+constexpr int PANEL_BYTES = PANEL_ROWS * 32;  // one (group, K step): 2 K chunks x 256 rows x 16 B
+constexpr int LBO_B = PANEL_ROWS * 16;        // K-chunk stride of a panel
+constexpr uint32_t TMEM_COLS = 512;           // two 256-column accumulators
+constexpr uint32_t TMEM_TILE = 256;
+constexpr int XCH_FLOATS = 4 * (GRP - 1) * (GRP - 1) * kTcN;  // rows handed between warps
+
+// ---- tcgen05 wrappers ------------------------------------------------------
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    // start address, leading (K-chunk) and stride (8-row group) byte offsets,
+    // all >> 4; bit 46 = descriptor version 1; swizzle mode 0 (none)
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    // no memory clobber: ordering with the operand writes comes from the
+    // mbarrier waits and fences around the issue loop
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---- bounded waits shared by all roles --------------------------------------
+
+struct Ctl {
+    uint64_t stage_full[2], stage_empty[2], a_full[2], a_empty[2], d_full[2], d_empty[2];
+    uint32_t tmem_base;
+    int abort;
+    int epi_ok[2][4];  // per-iteration votes of the four epilogue warps
+};
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, Ctl *ctl,
+                                              const TC2DArgs &a)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int *)&ctl->abort) return false;
+        if (globaltimer_ns() - t0 > a.wait_ns) {
+            *(volatile int *)&ctl->abort = 1;
+            record_status(a.status, DEV_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// A final bounded wait used while winding down after an abort.
+__device__ __forceinline__ void drain_wait(uint64_t *bar, uint32_t parity, const TC2DArgs &a)
+{
+    mbar_wait_bounded(bar, parity, a.wait_ns);
+}
+
+}  // namespace
+}  // namespace sg
+
+namespace sg {
+namespace {
+
+// Shared-memory layout (bytes from the 1024-aligned base):
+//   [0, 1024)           control block (barriers, tensor-memory address, abort flag)
+//   A operands          buffer s, part h (0 = hi, 1 = lo) at off_a + (2s+h)*a_bytes
+//   FP32 staging        slot t at off_stage + t*stage_bytes (TMA boxes; 1 or 2 slots)
+//   Toeplitz panels     groups x 3 K steps x PANEL_BYTES
+//   hand-over buffer    XCH_FLOATS floats (rows passed between epilogue warps)
+struct TcLayout {
+    uint32_t a_bytes, off_a, stage_bytes, off_stage, off_b, off_x, total;
+};
+
+__host__ __device__ inline int tc_groups(int R) { return (2 * R + 1 + GRP - 1) / GRP; }
+
+__host__ __device__ inline TcLayout tc_layout(int R, int rows, int rows_p, int box_w, int nstage)
+{
+    TcLayout L;
+    L.a_bytes = (uint32_t)(kTcKC * rows_p * 16);
+    L.off_a = 1024;
+    L.off_stage = (L.off_a + 4 * L.a_bytes + 127) / 128 * 128;
+    L.stage_bytes = ((uint32_t)(rows * box_w * 4) + 127) / 128 * 128;
+    L.off_b = L.off_stage + (uint32_t)nstage * L.stage_bytes;
+    L.off_x = L.off_b + (uint32_t)(tc_groups(R) * (kTcK / 16)) * PANEL_BYTES;
+    L.total = L.off_x + XCH_FLOATS * 4;
+    return L;
+}
+
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void store_point_tc(const TC2DArgs &a, int X, int Y, float v)
+{
+    float *dst = a.dst;
+    const int64_t py = a.dst_py;
+    const int nx = a.nx, ny = a.ny, gw = a.dst_gw;
+    const bool xl = X < gw, xh = X >= nx - gw, yl = Y < gw, yh = Y >= ny - gw;
+    if (xl) dst[Y * py + X + nx] = v;
+    if (xh) dst[Y * py + X - nx] = v;
+    if (yl) {
+        dst[(Y + ny) * py + X] = v;
+        if (xl) dst[(Y + ny) * py + X + nx] = v;
+        if (xh) dst[(Y + ny) * py + X - nx] = v;
+    }
+    if (yh) {
+        dst[(Y - ny) * py + X] = v;
+        if (xl) dst[(Y - ny) * py + X + nx] = v;
+        if (xh) dst[(Y - ny) * py + X - nx] = v;
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1)
+    k_tc2d_grouped(const __grid_constant__ CUtensorMap map, const __grid_constant__ TC2DArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    Ctl *ctl = reinterpret_cast<Ctl *>(smem);
+    const TcLayout L = tc_layout(a.R, a.rows, a.rows_p, a.box_w, a.nstage);
+    const int NSG = a.nstage;  // FP32 staging slots
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = smem_u32(smem);
+    const int R = a.R;
+
+    if (tid == 0) {
+        prefetch_tensormap(&map);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&ctl->stage_full[s], 1);
+            mbar_init(&ctl->stage_empty[s], 128);
+            mbar_init(&ctl->a_full[s], 128);
+            mbar_init(&ctl->a_empty[s], 1);
+            mbar_init(&ctl->d_full[s], 1);
+            mbar_init(&ctl->d_empty[s], 128);
+        }
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&ctl->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    {  // resident Toeplitz panels
+        const int n16 = tc_groups(R) * (kTcK / 16) * PANEL_BYTES / 16;
+        const uint4 *gp = reinterpret_cast<const uint4 *>(a.panels);
+        uint4 *sp = reinterpret_cast<uint4 *>(smem + L.off_b);
+        for (int i = tid; i < n16; i += NT) sp[i] = gp[i];
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+    const int first = blockIdx.x, step = gridDim.x;
+
+    if (warp == 0) {
+        // ---- producer: FP32 tile + halo by TMA
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(a.rows * a.box_w * 4);
+            int i = 0, last = -1;
+            for (int tile = first; tile < a.ntiles; tile += step, ++i) {
+                const int s = i % NSG, k = i / NSG;
+                if (!wait_or_abort(&ctl->stage_empty[s], (k & 1) ^ 1, ctl, a)) break;
+                const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+                mbar_arrive_expect_tx(&ctl->stage_full[s], bytes);
+                tma_load_2d(smem + L.off_stage + s * L.stage_bytes, &map, &ctl->stage_full[s],
+                            a.map_x0 + tx * kTcN - a.halo_x, a.map_y0 + ty * OUT_ROWS - R);
+                last = i;
+            }
+            if (ctl->abort && last >= 0)
+                drain_wait(&ctl->stage_full[last % NSG], (last / NSG) & 1, a);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint32_t id256 = idesc_bf16(kTcM, 2 * GRP * kTcN), id128 = idesc_bf16(kTcM, GRP * kTcN);
+            const uint32_t lbo_a = (uint32_t)a.rows_p * 16;
+            const int ngroups = tc_groups(R);
+            // bytes an MMA reads from its start: two K chunks of 128 A rows
+            // (or of N B rows), 16 bytes each
+            const uint32_t a_span = lbo_a + kTcM * 16, b_span = LBO_B + PANEL_ROWS * 16;
+            int i = 0, last = -1;
+            for (int tile = first; tile < a.ntiles; tile += step, ++i) {
+                const int s = i & 1, k = i >> 1;
+                if (!wait_or_abort(&ctl->a_full[s], k & 1, ctl, a)) break;
+                if (!wait_or_abort(&ctl->d_empty[s], (k & 1) ^ 1, ctl, a)) break;
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)s * TMEM_TILE;
+                const uint32_t a_hi = sbase + L.off_a + (2 * s) * L.a_bytes;
+                const uint32_t a_lo = a_hi + L.a_bytes;
+                const uint32_t kstep_bytes = 2 * lbo_a;
+                for (int g = 0; g < ngroups; ++g) {
+#pragma unroll
+                    for (int kk = 0; kk < kTcK / 16; ++kk) {
+                        // group g: A moved down 4g rows (16 bytes each), B its own panel
+                        const uint32_t ao = (uint32_t)(GRP * g) * 16 + kk * kstep_bytes;
+                        const uint32_t b_at = sbase + L.off_b + (uint32_t)((g * (kTcK / 16) + kk) * PANEL_BYTES);
+                        if (ao + a_span > L.a_bytes || b_at + b_span > sbase + L.off_x) {
+                            record_status(a.status, DEV_CHECK);  // would read past its buffer
+                            continue;
+                        }
+                        const uint64_t dh = smem_desc(a_hi + ao, lbo_a, 128);
+                        const uint64_t dl = smem_desc(a_lo + ao, lbo_a, 128);
+                        const uint64_t db = smem_desc(b_at, LBO_B, 128);
+                        const uint32_t acc = (g == 0 && kk == 0) ? 0u : 1u;
+                        if (a.terms == 3) {
+                            mma_bf16(dt, dh, db, id256, acc);  // v_hi [T_hi | T_lo]
+                            mma_bf16(dt, dl, db, id128, 1u);   // v_lo T_hi
+                        } else {
+                            mma_bf16(dt, dh, db, id128, acc);  // v_hi T_hi
+                        }
+                    }
+                }
+                mma_commit(&ctl->a_empty[s]);
+                mma_commit(&ctl->d_full[s]);
+                last = i;
+            }
+            if (ctl->abort && last >= 0) drain_wait(&ctl->d_full[last & 1], (last >> 1) & 1, a);
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ---- converters: FP32 staging -> centred BF16 hi/lo operands
+        const int ct = tid - 128;
+        const float mu = a.mean_sum ? (float)(a.mean_sum[0] * a.inv_n) : 0.f;
+        const int off = a.halo_x - R;
+        const uint32_t lbo_a = (uint32_t)a.rows_p * 16;
+        int i = 0;
+        for (int tile = first; tile < a.ntiles; tile += step, ++i) {
+            const int s = i & 1, k = i >> 1;        // A buffer
+            const int t = i % NSG, kt = i / NSG;    // staging slot
+            bool ok = wait_or_abort(&ctl->stage_full[t], kt & 1, ctl, a);
+            ok = ok && wait_or_abort(&ctl->a_empty[s], (k & 1) ^ 1, ctl, a);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const float *st = reinterpret_cast<const float *>(smem + L.off_stage + t * L.stage_bytes);
+            unsigned char *ahi = smem + L.off_a + (2 * s) * L.a_bytes;
+            unsigned char *alo = ahi + L.a_bytes;
+            for (int it = ct; it < a.rows * kTcKC; it += 128) {
+                const int kc = it % kTcKC, r = it / kTcKC;
+                const float *src = st + r * a.box_w + kc * 8 + off;
+                float v[8];
+                if (off == 0) {  // 16-byte aligned: two vector loads
+                    const float4 p0 = reinterpret_cast<const float4 *>(src)[0];
+                    const float4 p1 = reinterpret_cast<const float4 *>(src)[1];
+                    v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
+                    v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+                } else if ((off & 1) == 0) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 p = reinterpret_cast<const float2 *>(src)[e];
+                        v[2 * e] = p.x;
+                        v[2 * e + 1] = p.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v[e] = src[e];
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] -= mu;
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]);
+                    const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * e + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 =
+                        __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
+                    hw[e] = (uint32_t)__bfloat16_as_ushort(h0) |
+                            ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    lw[e] = (uint32_t)__bfloat16_as_ushort(l0) |
+                            ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+                const uint32_t o = kc * lbo_a + r * 16;
+                *reinterpret_cast<uint4 *>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&ctl->stage_empty[t]);
+            mbar_arrive(&ctl->a_full[s]);
+        }
+    } else if (warp >= 8) {
+        // ---- epilogue: tensor memory -> registers -> global memory
+        const int q = warp - 8;
+        const float mu = a.mean_sum ? (float)(a.mean_sum[0] * a.inv_n) : 0.f;
+        const float musum = mu * a.sum_c;
+        int i = 0;
+        for (int tile = first; tile < a.ntiles; tile += step, ++i) {
+            const int s = i & 1, k = i >> 1;
+            bool ok = wait_or_abort(&ctl->d_full[s], k & 1, ctl, a);
+            ok = __all_sync(0xffffffffu, ok);
+            // the four epilogue warps decide together, so that none of them is
+            // left waiting at a named barrier the others never reach
+            if (lane == 0) ctl->epi_ok[s][q] = ok ? 1 : 0;
+            epi_barrier();
+            const volatile int *votes = ctl->epi_ok[s];
+            if (!(votes[0] && votes[1] && votes[2] && votes[3])) break;
+            tc_fence_after();
+            const uint32_t tcol = (uint32_t)s * TMEM_TILE;  // this tile's first column
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + tcol;
+            float *xch = reinterpret_cast<float *>(smem + L.off_x);
+            const int row = 32 * q + lane;  // output row within the tile
+            float o[32];
+            // offset j of the group: D[row][j] holds X rows row+4g+j; output row
+            // y takes D[y+j][j], i.e. row + j of the accumulator
+            const bool cols_ok = tcol + (uint32_t)(2 * GRP * kTcN) <= TMEM_COLS;
+            if (!cols_ok && lane == 0) record_status(a.status, DEV_CHECK);
+#pragma unroll
+            for (int j = 0; j < GRP; ++j) {
+                float v0[32], v1[32];
+#pragma unroll
+                for (int n = 0; n < 32; ++n) v0[n] = v1[n] = 0.f;
+                if (cols_ok) {
+                    tmem_ld32(taddr + (uint32_t)(j * kTcN), v0);
+                    if (a.terms == 3) tmem_ld32(taddr + (uint32_t)((GRP + j) * kTcN), v1);
+                    tmem_ld_wait();
+                }
+#pragma unroll
+                for (int n = 0; n < 32; ++n) {
+                    const float t = v0[n] + (a.terms == 3 ? v1[n] : 0.f);
+                    if (j == 0) {
+                        o[n] = t + musum;
+                    } else {
+                        // rows handed to the previous warp: this warp's first GRP-1
+                        if (lane < GRP - 1)
+                            xch[((q * (GRP - 1) + lane) * (GRP - 1) + (j - 1)) * kTcN + n] = t;
+                        const float u = __shfl_down_sync(0xffffffffu, t, j);
+                        if (lane + j < 32) o[n] += u;
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&ctl->d_empty[s]);  // every accumulator column has been read
+            epi_barrier();
+            if (q < 3) {
+#pragma unroll
+                for (int j = 1; j < GRP; ++j)
+                    if (lane + j >= 32) {
+                        const float *src =
+                            xch + (((q + 1) * (GRP - 1) + (lane + j - 32)) * (GRP - 1) + (j - 1)) * kTcN;
+#pragma unroll
+                        for (int n = 0; n < 32; ++n) o[n] += src[n];
+                    }
+            }
+            const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+            const int Y = ty * OUT_ROWS + row;
+            const int X0 = tx * kTcN;
+            if (row < OUT_ROWS && Y < a.ny) {
+                float *drow = a.dst + Y * a.dst_py + X0;
+                if (a.dst_vec4 && X0 + 32 <= a.nx) {
+#pragma unroll
+                    for (int n = 0; n < 32; n += 4)
+                        *reinterpret_cast<float4 *>(drow + n) =
+                            make_float4(o[n], o[n + 1], o[n + 2], o[n + 3]);
+                } else {
+#pragma unroll
+                    for (int n = 0; n < 32; ++n)
+                        if (X0 + n < a.nx) drow[n] = o[n];
+                }
+                if (a.dst_gw > 0 && (X0 < a.dst_gw || X0 + 32 > a.nx - a.dst_gw ||
+                                     Y < a.dst_gw || Y >= a.ny - a.dst_gw)) {
+#pragma unroll
+                    for (int n = 0; n < 32; ++n)
+                        if (X0 + n < a.nx) store_point_tc(a, X0 + n, Y, o[n]);
+                }
+            }
+        }
+    }
+
+    __syncwarp();  // every warp reconverges after its role before the block barrier
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+
+static void tc_geometry(int R, int *rows, int *rows_p, int *box_w, int *halo_x)
+{
+    *halo_x = round_up(R, 4);
+    *rows = kTcM + 2 * R;
+    *rows_p = *rows | 1;  // odd: consecutive K chunks fall in different bank groups
+    *box_w = round_up(kTcK + *halo_x - R, 4);
+}
+
+size_t tc2dg_smem_bytes(int R, int nstage)
+{
+    int rows, rows_p, box_w, hx;
+    tc_geometry(R, &rows, &rows_p, &box_w, &hx);
+    return tc_layout(R, rows, rows_p, box_w, nstage).total;
+}
+
+size_t tc2dg_panel_elems(int R) { return (size_t)tc_groups(R) * (kTcK / 16) * PANEL_BYTES / 2; }
+
+double tc2dg_build_panels(const double *cm, int R, uint16_t *out)
+{
+    const int W = 2 * R + 1;
+    std::vector<double> hi(W * W), lo(W * W);
+    double target = 0.0, got = 0.0;
+    for (int i = 0; i < W * W; ++i) {
+        const __nv_bfloat16 h = __double2bfloat16(cm[i]);
+        hi[i] = (double)__bfloat162float(h);
+        lo[i] = (double)__bfloat162float(__double2bfloat16(cm[i] - hi[i]));
+        target += cm[i];
+        got += hi[i] + lo[i];
+    }
+    // mass correction: the centre tap's lo absorbs the rounding of the sum
+    const int c = R * W + R;
+    lo[c] = (double)__bfloat162float(__double2bfloat16(lo[c] + (target - got)));
+    // panel (group g, K step kk): 2 K chunks of 8 window columns; in each, the
+    // 256 stacked rows [T_4g .. T_4g+3 hi | the same lo] 16 bytes apart.
+    // Offsets past 2R (the last group's padding) have zero weights.
+    const int G = tc_groups(R);
+    for (int g = 0; g < G; ++g)
+        for (int kk = 0; kk < kTcK / 16; ++kk) {
+            uint16_t *panel = out + (size_t)(g * (kTcK / 16) + kk) * (PANEL_BYTES / 2);
+            for (int rr = 0; rr < PANEL_ROWS; ++rr) {
+                const int part = rr / (GRP * kTcN), j = (rr / kTcN) % GRP, n = rr % kTcN;
+                const int aa = GRP * g + j;  // row offset (0 .. 2R)
+                const std::vector<double> &src = part == 0 ? hi : lo;
+                for (int kc = 0; kc < 2; ++kc)
+                    for (int e = 0; e < 8; ++e) {
+                        const int k = 16 * kk + 8 * kc + e;  // window column
+                        const int b = k - n;                 // column offset + R
+                        double w = 0.0;
+                        if (aa <= 2 * R && b >= 0 && b <= 2 * R) w = src[aa * W + b];
+                        panel[(size_t)kc * PANEL_ROWS * 8 + (size_t)rr * 8 + e] =
+                            __bfloat16_as_ushort(__double2bfloat16(w));
+                    }
+            }
+        }
+    // The epilogue adds mu * (sum of the exact folded weights): the mean the
+    // exact stencil carries forward.  The split weights then act only on the
+    // centred values x - mu, whose mean stays near zero, so their residual
+    // mass error does not make the grid mean drift sweep after sweep.
+    return target;
+}
+
+cudaError_t launch_tc2dg(const CUtensorMap &map, const TC2DArgs &a,
+                        int grid, size_t smem, cudaStream_t s)
+{
+    static cudaError_t once = [] {
+        int dev = 0, maxs = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return cudaFuncSetAttribute(k_tc2d_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    }();
+    if (once != cudaSuccess) return once;
+    k_tc2d_grouped<<<grid, NT, smem, s>>>(map, a);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

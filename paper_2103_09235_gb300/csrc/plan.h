@@ -28,6 +28,7 @@ struct stencil_plan_s {
     int cta_threads = 0;  // threads per CTA of the 2D sweep (0 = automatic, or 256)
     int tc_center = 1;
     int tc_tma_store = 1;
+    int tc_form = 0;  // tensor cores: 0 by folded radius, 1 one MMA per row offset, 2 grouped
     int autotune = 1;
     long long wait_ms = 2000;
     int fault_withhold_copy = 0;  // test hook, see stencil_plan_set_option
@@ -68,6 +69,7 @@ struct stencil_plan_s {
     // bookkeeping
     long long launches = 0;
     int last_m = 0, last_b = 0, last_engine = 0;
+    int last_tc_form = 0;  // tensor-core kernel of the last tensor-core run (1 or 2)
     int last_ty = 0;  // tile height of the last 2D CUDA-core run's first pass
     // autotuner choice for fold_m = 0: m, b, tile_y, engine (m = 0: not tuned yet)
     int tuned_m = 0, tuned_b = 0, tuned_ty = 0, tuned_engine = 0;

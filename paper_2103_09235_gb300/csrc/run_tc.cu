@@ -12,16 +12,22 @@
 
 namespace sg {
 
-static stencil_status_t tc_panels(stencil_plan_s *p, int m, const uint16_t **out, double *sum)
+// Toeplitz panels of c^(m) for the per-offset or the grouped tensor-core
+// kernel, built once per plan.
+static stencil_status_t tc_panels(stencil_plan_s *p, int m, bool grouped, const uint16_t **out,
+                                  double *sum)
 {
-    auto it = p->panels.find(m);
+    const int key = grouped ? m + 64 : m;
+    auto it = p->panels.find(key);
     if (it == p->panels.end()) {
         const std::vector<double> *cm = nullptr;
         stencil_status_t st = plan_folded(p, m, &cm);
         if (st != STENCIL_OK) return st;
         const int R = m * p->r;
-        std::vector<uint16_t> host((size_t)(2 * R + 1) * kTcPanelElems);
-        const double wsum = tc2d_build_panels(cm->data(), R, host.data());
+        std::vector<uint16_t> host(grouped ? tc2dg_panel_elems(R)
+                                           : (size_t)(2 * R + 1) * kTcPanelElems);
+        const double wsum = grouped ? tc2dg_build_panels(cm->data(), R, host.data())
+                                    : tc2d_build_panels(cm->data(), R, host.data());
         uint16_t *d = nullptr;
         cudaError_t e = cudaMalloc(&d, host.size() * sizeof(uint16_t));
         if (e == cudaSuccess)
@@ -31,11 +37,54 @@ static stencil_status_t tc_panels(stencil_plan_s *p, int m, const uint16_t **out
             return cuda_fail(e, "tensor-core panels");
         }
         p->scratch_bytes += host.size() * sizeof(uint16_t);
-        it = p->panels.emplace(m, d).first;
-        p->panel_sum[m] = wsum;
+        it = p->panels.emplace(key, d).first;
+        p->panel_sum[key] = wsum;
     }
     *out = it->second;
-    *sum = p->panel_sum[m];
+    *sum = p->panel_sum[key];
+    return STENCIL_OK;
+}
+
+// One pass of the grouped tensor-core kernel (k_tc2d_grouped.cu).
+static stencil_status_t launch_tc_grouped_pass(stencil_plan_s *p, const Padded &src, int m,
+                                               const uint16_t *panels, double sum_c, float *dst,
+                                               int64_t dst_py, int dst_gw, bool dst_vec4,
+                                               cudaStream_t s)
+{
+    const int R = m * p->r;
+    TC2DArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.tiles_x = ceil_div(p->nx, kTcN);
+    a.ntiles = a.tiles_x * ceil_div(p->ny, kTcOutRows);
+    a.R = R;
+    a.halo_x = round_up(R, 4);
+    a.rows = kTcM + 2 * R;
+    a.rows_p = a.rows | 1;
+    a.box_w = round_up(kTcK + a.halo_x - R, 4);
+    a.terms = p->precision == STENCIL_PREC_BF16X1 ? 1 : 3;
+    a.map_x0 = src.gx;
+    a.map_y0 = src.gy;
+    a.mean_sum = p->tc_center ? p->d_acc : nullptr;
+    a.inv_n = 1.0 / ((double)p->nx * p->ny);
+    a.sum_c = (float)sum_c;
+    a.panels = panels;
+    a.dst = dst;
+    a.dst_py = dst_py;
+    a.dst_gw = dst_gw;
+    a.dst_vec4 = dst_vec4 ? 1 : 0;
+    a.status = p->d_status;
+    a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
+    const int box[2] = {a.box_w, a.rows};
+    const CUtensorMap *map = plan_map(p, src, box);
+    if (!map) return STENCIL_ERR_CUDA;
+    // two FP32 staging slots when they fit, else one: the converters empty a
+    // slot long before the tile's MMAs finish
+    a.nstage = tc2dg_smem_bytes(R, 2) <= (size_t)p->max_smem ? 2 : 1;
+    const int grid = std::min(a.ntiles, p->sm_count);
+    cudaError_t e = launch_tc2dg(*map, a, grid, tc2dg_smem_bytes(R, a.nstage), s);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core sweep launch");
     return STENCIL_OK;
 }
 
@@ -99,14 +148,19 @@ stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_
         return STENCIL_ERR_UNSUPPORTED;
     }
     ensure_device_facts(p);
-    if (tc2d_smem_bytes(R, false) > (size_t)p->max_smem) {
+    // the grouped form issues about a quarter of the MMAs but pays a fixed
+    // epilogue per tile: it wins for wide folds (measured on GB300: 1318 vs
+    // 1002 GS/s at R = 8, 783 vs 853 at R = 4, 394 vs 643 at R = 2)
+    const bool grouped = p->tc_form == 2 || (p->tc_form == 0 && R >= kTcGroupedMinR);
+    if (grouped ? tc2dg_smem_bytes(R, 1) > (size_t)p->max_smem
+                : tc2d_smem_bytes(R, false) > (size_t)p->max_smem) {
         set_error("tensor-core sweep: shared memory");
         return STENCIL_ERR_UNSUPPORTED;
     }
     const uint16_t *panels = nullptr;
     double sum_c = 0.0;
     const std::vector<double> *c1 = nullptr;
-    stencil_status_t st = tc_panels(p, m, &panels, &sum_c);
+    stencil_status_t st = tc_panels(p, m, grouped, &panels, &sum_c);
     if (st == STENCIL_OK) st = plan_folded(p, 1, &c1);
     if (st == STENCIL_OK) st = ensure_padded(p);
     if (st != STENCIL_OK) return st;
@@ -139,9 +193,13 @@ stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_
         int64_t done = 0;
         for (int64_t i = 0; i < q; ++i, ++done) {
             const bool last = done + 1 == npass;
-            stencil_status_t r = launch_tc_pass(p, *cur, m, panels, sum_c, last ? out : oth->origin,
-                                                last ? (int64_t)p->nx : oth->py, last ? 0 : gw,
-                                                last ? out_vec4 : true, st_);
+            float *dst = last ? out : oth->origin;
+            const int64_t dpy = last ? (int64_t)p->nx : oth->py;
+            stencil_status_t r =
+                grouped ? launch_tc_grouped_pass(p, *cur, m, panels, sum_c, dst, dpy, last ? 0 : gw,
+                                                 last ? out_vec4 : true, st_)
+                        : launch_tc_pass(p, *cur, m, panels, sum_c, dst, dpy, last ? 0 : gw,
+                                         last ? out_vec4 : true, st_);
             if (r != STENCIL_OK) return r;
             *nl += 1;
             std::swap(cur, oth);
@@ -159,11 +217,12 @@ stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_
         return STENCIL_OK;
     };
     std::vector<int64_t> key = {3, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m,
-                                p->precision, p->tc_center, p->wait_ms};
+                                p->precision, p->tc_center, p->wait_ms, grouped ? 1 : 0};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = 1;
     p->last_engine = 1;
+    p->last_tc_form = grouped ? 2 : 1;
     return st;
 }
 

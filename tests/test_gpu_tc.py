@@ -27,15 +27,19 @@ def env(oracle_mod):
     return torch, binding, oracle_mod
 
 
-def run_tc(env, shape, c, x, T, m, precision=1, center=1):
+def run_tc(env, shape, c, x, T, m, precision=1, center=1, form=0):
     torch, binding, _ = env
     plan = binding.Plan(shape, c)
     plan.set_option("precision", precision).set_option("tc_center", center)
+    plan.set_option("tc_form", form)
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty_like(xd)
     plan.run(xd, yd, T, fold_m=m)
     plan.sync()
     assert plan.get("last_engine") == 1
+    R = m * (c.shape[0] // 2)
+    want = form if form else (2 if R >= 6 else 1)
+    assert plan.get("last_tc_form") == want
     y = yd.cpu().numpy()
     plan.close()
     return y
@@ -53,17 +57,20 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("shape,r,T,m", CASES)
-def test_tc_bf16x3_parity(env, shape, r, T, m):
+def test_tc_bf16x3_parity(env, shape, r, T, m, form):
+    """Both tensor-core kernels: one MMA per row offset (1) and four offsets per MMA (2)."""
     _, _, oracle = env
     c = synth.dyadic_coeffs(500 + r, 2, r, "box")
     x = synth.grid(600 + T, shape, np.float32)
     ref = oracle.run(x.astype(np.float64), c, T)
-    y3 = run_tc(env, shape, c, x, T, m, precision=1)
+    y3 = run_tc(env, shape, c, x, T, m, precision=1, form=form)
     err3 = oracle.rel_l2(y3, ref)
-    y1 = run_tc(env, shape, c, x, T, m, precision=2)
+    y1 = run_tc(env, shape, c, x, T, m, precision=2, form=form)
     err1 = oracle.rel_l2(y1, ref)
-    print("TC %s r=%d T=%d m=%d: BF16x3 rel-L2 %.3e, BF16x1 rel-L2 %.3e" % (shape, r, T, m, err3, err1))
+    print("TC form %d %s r=%d T=%d m=%d: BF16x3 rel-L2 %.3e, BF16x1 rel-L2 %.3e"
+          % (form, shape, r, T, m, err3, err1))
     assert err3 <= TOL
     assert err1 > err3
 
