@@ -106,8 +106,9 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
  *   "graph"         1 = capture each distinct run (pointers, T, m, options) once into
  *                   a CUDA graph and replay it (default 1); 0 = launch kernel by kernel.
  *                   A run on a stream that is itself being captured is never graphed.
- *   "fault_withhold_copy"  test hook: 1 = the 2D CUDA-core sweep never issues its
- *                   first tile copy, so its bounded wait runs out and stencil_sync
+ *   "fault_withhold_copy"  test hook: 1 = the 2D CUDA-core sweep and the single-sweep
+ *                   3D kernel never issue a CTA's first copy, so their bounded waits
+ *                   run out and stencil_sync
  *                   reports STENCIL_ERR_TIMEOUT (no GPU fault; the context stays usable).
  * Errors: INVALID_ARG for an unknown key or an out-of-range value.
  */

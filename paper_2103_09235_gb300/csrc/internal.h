@@ -120,6 +120,7 @@ struct Sweep3DArgs {
     int nx, ny, nz;
     int tiles_x, tiles_y, ntiles_xy, zchunks, ntiles;
     int tile_y, zchunk;
+    int fault_withhold_copy;    // test hook: k_sweep3d never issues a CTA's first chunk
     int halo_x;                 // R rounded up to a multiple of 4
     int map_x0, map_y0, map_z0;
     int buf_floats;             // floats per shared-memory plane slot
@@ -222,6 +223,9 @@ size_t tc2d_smem_bytes(int R, bool tma_store);
 // Grouped form (k_tc2d_grouped.cu): four row offsets per MMA, 125 output rows
 // of 32 columns per tile, direct stores.
 size_t tc2dg_smem_bytes(int R, int nstage);
+// Tile geometry of the grouped kernel: staged rows, A-operand row pitch (rows),
+// FP32 staging row pitch (floats; also the TMA box width) and halo columns.
+void tc2dg_geometry(int R, int *rows, int *rows_p, int *box_w, int *halo_x);
 size_t tc2dg_panel_elems(int R);
 double tc2dg_build_panels(const double *cm, int R, uint16_t *host_out);
 cudaError_t launch_tc2dg(const CUtensorMap &map, const TC2DArgs &a, int grid, size_t smem,

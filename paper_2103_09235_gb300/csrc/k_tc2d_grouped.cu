@@ -270,9 +270,20 @@ __global__ void __launch_bounds__(NT, 1)
             const uint32_t id256 = idesc_bf16(kTcM, 2 * GRP * kTcN), id128 = idesc_bf16(kTcM, GRP * kTcN);
             const uint32_t lbo_a = (uint32_t)a.rows_p * 16;
             const int ngroups = tc_groups(R);
+            const uint32_t kstep_bytes = 2 * lbo_a;
             // bytes an MMA reads from its start: two K chunks of 128 A rows
-            // (or of N B rows), 16 bytes each
+            // (or of N B rows), 16 bytes each.  The furthest (group, K step)
+            // is checked once: every other one starts below it.
             const uint32_t a_span = lbo_a + kTcM * 16, b_span = LBO_B + PANEL_ROWS * 16;
+            const uint32_t ao_max = (uint32_t)(GRP * (ngroups - 1)) * 16 + (kTcK / 16 - 1) * kstep_bytes;
+            const uint32_t b_max = L.off_b + (uint32_t)(ngroups * (kTcK / 16) - 1) * PANEL_BYTES;
+            const bool ranges_ok = ao_max + a_span <= L.a_bytes && b_max + b_span <= L.off_x;
+            if (!ranges_ok) record_status(a.status, DEV_CHECK);  // would read past its buffer
+            // descriptors are built once; an operand's start moves by adding its
+            // byte offset / 16 to the start-address field (shared-memory
+            // addresses / 16 stay below 2^14, so the field never carries)
+            const uint64_t dA0 = smem_desc(sbase + L.off_a, lbo_a, 128);
+            const uint64_t dB0 = smem_desc(sbase + L.off_b, LBO_B, 128);
             int i = 0, last = -1;
             for (int tile = first; tile < a.ntiles; tile += step, ++i) {
                 const int s = i & 1, k = i >> 1;
@@ -280,28 +291,23 @@ __global__ void __launch_bounds__(NT, 1)
                 if (!wait_or_abort(&ctl->d_empty[s], (k & 1) ^ 1, ctl, a)) break;
                 tc_fence_after();
                 const uint32_t dt = tmem + (uint32_t)s * TMEM_TILE;
-                const uint32_t a_hi = sbase + L.off_a + (2 * s) * L.a_bytes;
-                const uint32_t a_lo = a_hi + L.a_bytes;
-                const uint32_t kstep_bytes = 2 * lbo_a;
-                for (int g = 0; g < ngroups; ++g) {
+                const uint64_t dh0 = dA0 + (((2 * s) * L.a_bytes) >> 4);
+                const uint64_t dl0 = dh0 + (L.a_bytes >> 4);
+                if (ranges_ok) {
+                    for (int g = 0; g < ngroups; ++g) {
 #pragma unroll
-                    for (int kk = 0; kk < kTcK / 16; ++kk) {
-                        // group g: A moved down 4g rows (16 bytes each), B its own panel
-                        const uint32_t ao = (uint32_t)(GRP * g) * 16 + kk * kstep_bytes;
-                        const uint32_t b_at = sbase + L.off_b + (uint32_t)((g * (kTcK / 16) + kk) * PANEL_BYTES);
-                        if (ao + a_span > L.a_bytes || b_at + b_span > sbase + L.off_x) {
-                            record_status(a.status, DEV_CHECK);  // would read past its buffer
-                            continue;
-                        }
-                        const uint64_t dh = smem_desc(a_hi + ao, lbo_a, 128);
-                        const uint64_t dl = smem_desc(a_lo + ao, lbo_a, 128);
-                        const uint64_t db = smem_desc(b_at, LBO_B, 128);
-                        const uint32_t acc = (g == 0 && kk == 0) ? 0u : 1u;
-                        if (a.terms == 3) {
-                            mma_bf16(dt, dh, db, id256, acc);  // v_hi [T_hi | T_lo]
-                            mma_bf16(dt, dl, db, id128, 1u);   // v_lo T_hi
-                        } else {
-                            mma_bf16(dt, dh, db, id128, acc);  // v_hi T_hi
+                        for (int kk = 0; kk < kTcK / 16; ++kk) {
+                            // group g: A moved down 4g rows (16 bytes each), B its own panel
+                            const uint32_t ao16 = ((uint32_t)(GRP * g) * 16 + kk * kstep_bytes) >> 4;
+                            const uint64_t db =
+                                dB0 + ((uint32_t)((g * (kTcK / 16) + kk) * PANEL_BYTES) >> 4);
+                            const uint32_t acc = (g == 0 && kk == 0) ? 0u : 1u;
+                            if (a.terms == 3) {
+                                mma_bf16(dt, dh0 + ao16, db, id256, acc);  // v_hi [T_hi | T_lo]
+                                mma_bf16(dt, dl0 + ao16, db, id128, 1u);   // v_lo T_hi
+                            } else {
+                                mma_bf16(dt, dh0 + ao16, db, id128, acc);  // v_hi T_hi
+                            }
                         }
                     }
                 }
@@ -327,44 +333,75 @@ __global__ void __launch_bounds__(NT, 1)
             const float *st = reinterpret_cast<const float *>(smem + L.off_stage + t * L.stage_bytes);
             unsigned char *ahi = smem + L.off_a + (2 * s) * L.a_bytes;
             unsigned char *alo = ahi + L.a_bytes;
-            for (int it = ct; it < a.rows * kTcKC; it += 128) {
-                const int kc = it % kTcKC, r = it / kTcKC;
-                const float *src = st + r * a.box_w + kc * 8 + off;
-                float v[8];
-                if (off == 0) {  // 16-byte aligned: two vector loads
-                    const float4 p0 = reinterpret_cast<const float4 *>(src)[0];
-                    const float4 p1 = reinterpret_cast<const float4 *>(src)[1];
-                    v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
-                    v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
-                } else if ((off & 1) == 0) {
+            // consecutive threads take consecutive rows of one K chunk: their
+            // 16-byte operand stores are contiguous, and the staging pitch
+            // (4 mod 8 floats) puts their FP32 loads in distinct banks.  Two
+            // items per pass keep two sets of loads in flight.
+            // (row, chunk) of item it = kc * rows + r advances by 128 items per
+            // step without a division: rows > 128, so r wraps at most once
+            const int n_items = a.rows * kTcKC;
+            int rr[2], kq[2];
+            rr[0] = ct;
+            kq[0] = 0;
+            for (int it0 = ct; it0 < n_items; it0 += 256) {
+                rr[1] = rr[0] + 128;
+                kq[1] = kq[0];
+                if (rr[1] >= a.rows) {
+                    rr[1] -= a.rows;
+                    ++kq[1];
+                }
+                float v[2][8];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int it = it0 + 128 * u;
+                    if (it >= n_items) continue;
+                    const int r = rr[u], kc = kq[u];
+                    const float *src = st + r * a.box_w + kc * 8 + off;
+                    if (off == 0) {  // 16-byte aligned: two vector loads
+                        const float4 p0 = reinterpret_cast<const float4 *>(src)[0];
+                        const float4 p1 = reinterpret_cast<const float4 *>(src)[1];
+                        v[u][0] = p0.x; v[u][1] = p0.y; v[u][2] = p0.z; v[u][3] = p0.w;
+                        v[u][4] = p1.x; v[u][5] = p1.y; v[u][6] = p1.z; v[u][7] = p1.w;
+                    } else if ((off & 1) == 0) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 p = reinterpret_cast<const float2 *>(src)[e];
+                            v[u][2 * e] = p.x;
+                            v[u][2 * e + 1] = p.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[u][e] = src[e];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int it = it0 + 128 * u;
+                    if (it >= n_items) continue;
+                    const int r = rr[u], kc = kq[u];
+                    uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const float2 p = reinterpret_cast<const float2 *>(src)[e];
-                        v[2 * e] = p.x;
-                        v[2 * e + 1] = p.y;
+                        const float x0 = v[u][2 * e] - mu, x1 = v[u][2 * e + 1] - mu;
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0);
+                        const __nv_bfloat16 h1 = __float2bfloat16_rn(x1);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                        hw[e] = (uint32_t)__bfloat16_as_ushort(h0) |
+                                ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                        lw[e] = (uint32_t)__bfloat16_as_ushort(l0) |
+                                ((uint32_t)__bfloat16_as_ushort(l1) << 16);
                     }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = src[e];
+                    const uint32_t o = kc * lbo_a + r * 16;
+                    *reinterpret_cast<uint4 *>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] -= mu;
-                uint32_t hw[4], lw[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]);
-                    const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * e + 1]);
-                    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
-                    const __nv_bfloat16 l1 =
-                        __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
-                    hw[e] = (uint32_t)__bfloat16_as_ushort(h0) |
-                            ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                    lw[e] = (uint32_t)__bfloat16_as_ushort(l0) |
-                            ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                rr[0] = rr[1] + 128;
+                kq[0] = kq[1];
+                if (rr[0] >= a.rows) {
+                    rr[0] -= a.rows;
+                    ++kq[0];
                 }
-                const uint32_t o = kc * lbo_a + r * 16;
-                *reinterpret_cast<uint4 *>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4 *>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
             fence_proxy_async_smem();
             mbar_arrive(&ctl->stage_empty[t]);
@@ -472,18 +509,22 @@ __global__ void __launch_bounds__(NT, 1)
 }  // namespace
 
 
-static void tc_geometry(int R, int *rows, int *rows_p, int *box_w, int *halo_x)
+void tc2dg_geometry(int R, int *rows, int *rows_p, int *box_w, int *halo_x)
 {
     *halo_x = round_up(R, 4);
     *rows = kTcM + 2 * R;
     *rows_p = *rows | 1;  // odd: consecutive K chunks fall in different bank groups
-    *box_w = round_up(kTcK + *halo_x - R, 4);
+    // staging row pitch: the window's columns, rounded up to 4 mod 8 floats so
+    // that eight consecutive rows start in eight different 16-byte bank groups
+    const int need = kTcK + *halo_x - R;
+    *box_w = round_up(need, 4);
+    if (*box_w % 8 == 0) *box_w += 4;
 }
 
 size_t tc2dg_smem_bytes(int R, int nstage)
 {
     int rows, rows_p, box_w, hx;
-    tc_geometry(R, &rows, &rows_p, &box_w, &hx);
+    tc2dg_geometry(R, &rows, &rows_p, &box_w, &hx);
     return tc_layout(R, rows, rows_p, box_w, nstage).total;
 }
 

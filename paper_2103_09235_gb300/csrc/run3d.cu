@@ -35,6 +35,7 @@ static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int 
     a.zchunk = zc;
     a.zchunks = ceil_div(p->nz, zc);
     a.ntiles = a.ntiles_xy * a.zchunks;
+    a.fault_withhold_copy = p->fault_withhold_copy;
     a.tile_y = kTY3;
     a.halo_x = b == 2 ? sweep3d_tb_halo_x() : round_up(R, 4);
     a.map_x0 = src.gx;
@@ -128,7 +129,7 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
         return STENCIL_OK;
     };
     std::vector<int64_t> key = {4, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, b,
-                                p->wait_ms};
+                                p->wait_ms, p->fault_withhold_copy};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = b;

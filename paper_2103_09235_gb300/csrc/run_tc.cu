@@ -59,10 +59,7 @@ static stencil_status_t launch_tc_grouped_pass(stencil_plan_s *p, const Padded &
     a.tiles_x = ceil_div(p->nx, kTcN);
     a.ntiles = a.tiles_x * ceil_div(p->ny, kTcOutRows);
     a.R = R;
-    a.halo_x = round_up(R, 4);
-    a.rows = kTcM + 2 * R;
-    a.rows_p = a.rows | 1;
-    a.box_w = round_up(kTcK + a.halo_x - R, 4);
+    tc2dg_geometry(R, &a.rows, &a.rows_p, &a.box_w, &a.halo_x);
     a.terms = p->precision == STENCIL_PREC_BF16X1 ? 1 : 3;
     a.map_x0 = src.gx;
     a.map_y0 = src.gy;

@@ -239,6 +239,29 @@ def test_bounded_wait_reports_timeout(env, m, b, stages):
     check(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, T))
 
 
+@pytest.mark.parametrize("kind,m", [("star", 1), ("box", 2)])
+def test_bounded_wait_reports_timeout_3d(env, kind, m):
+    """The single-sweep 3D kernel: a withheld chunk ends the consumer warps'
+    waits and the producer's with a status, for a padded destination (ghost
+    refresh) and the dense last pass alike; the next run is correct."""
+    torch, binding, oracle = env
+    shape = (40, 48, 64)
+    c = synth.dyadic_coeffs(23, 3, 1, kind)
+    x = synth.grid(24, shape, np.float32)
+    plan = binding.Plan(shape, c).set_option("block_b", 1)
+    plan.set_option("wait_limit_ms", 50).set_option("fault_withhold_copy", 1)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    T = 2 * m
+    plan.run(xd, yd, T, fold_m=m)
+    assert plan.sync_status() == 5
+    assert plan.sync_status() == 0
+    plan.set_option("fault_withhold_copy", 0)
+    plan.run(xd, yd, T, fold_m=m)
+    plan.sync()
+    check(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, T))
+
+
 def test_graph_replay_matches_direct_launches(env):
     """A run replayed from its captured graph equals the same run launched kernel by kernel."""
     torch, binding, oracle = env
