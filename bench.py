@@ -223,7 +223,12 @@ def measure_variants(torch, binding, dev, stream, flush, args):
     out = {}
 
     def single(name, shape, kind, seed, T, m, ndim=2, dtype="f32", **opts):
-        c = synth.heat1d_coeffs() if kind == "heat" else synth.dyadic_coeffs(seed, ndim, 1, kind)
+        if kind == "heat":
+            c = synth.heat1d_coeffs()
+        elif kind == "sep":  # a separable 9-point box (one counterpart at every m)
+            c = synth.separable_coeffs(seed, 1, 1)
+        else:
+            c = synth.dyadic_coeffs(seed, ndim, 1, kind)
         npdt = np.float64 if dtype == "f64" else np.float32
         x = torch.from_numpy(synth.grid(seed, shape, npdt)).to(dev)
         y = torch.empty_like(x)
@@ -237,6 +242,8 @@ def measure_variants(torch, binding, dev, stream, flush, args):
                      "engine": "tensor-core" if plan.get("last_engine") else "cuda-core"}
         if plan.get("last_engine"):
             out[name]["tc_kernel"] = "grouped" if plan.get("last_tc_form") == 2 else "per-offset"
+        elif ndim == 2:
+            out[name]["counterparts"] = plan.get("last_cp")
         plan.close()
         del x, y
         torch.cuda.empty_cache()
@@ -256,6 +263,13 @@ def measure_variants(torch, binding, dev, stream, flush, args):
     single("box8192_T512_tc_bf16x3_m8", (8192, 8192), "box", s3, 512, 8, precision=1)
     single("box8192_T512_tc_bf16x3_m8_per_offset", (8192, 8192), "box", s3, 512, 8, precision=1,
            tc_form=1)
+    # a separable box (the paper's Gaussian-blur family): counterpart form
+    # (Section 3.3) against the direct form, same grid and steps
+    s7 = synth.BASE_SEED + 7
+    single("sepbox8192_T512_counterparts_m8", (8192, 8192), "sep", s7, 512, 8, block_b=2)
+    single("sepbox8192_T512_counterparts_m4", (8192, 8192), "sep", s7, 512, 4, block_b=2)
+    single("sepbox8192_T512_direct_m2b2", (8192, 8192), "sep", s7, 512, 2, block_b=2,
+           counterparts=2)
     single("star512cube_T200_plain", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1, ndim=3)
     single("star512cube_T200_plain_fused2", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1,
            ndim=3, block_b=2)

@@ -94,6 +94,15 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
  *                   (chosen by the autotuner, else the kernel's own size), 256 =
  *                   two half-size CTAs per SM for folded sweeps that run 512.
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
+ *   "counterparts"  2D CUDA-core sweeps in counterpart form (Section 3.3 vertical then
+ *                   horizontal folding; Section 3.5 counterpart reuse): when c^(m)
+ *                   factors exactly as a sum of K <= 2 separable terms u_k (x) v_k, a
+ *                   sweep folds the input vertically with each u_k and combines the
+ *                   results horizontally with the v_k, 2K(2R+1) multiply-adds per
+ *                   point.  0 = when that undercuts the nonzeros of c^(m) and the
+ *                   sweep is folded (m >= 2) or wide (R >= 3) (default); 1 = always
+ *                   (UNSUPPORTED when the rank is above 2);
+ *                   2 = never.  Folded radii 1, 2, 3, 4, 6, 8.
  *   "tc_form"       tensor-core kernel: 1 = one MMA per row offset of the folded
  *                   weights (the row shift applied through the operand descriptor);
  *                   2 = four row offsets per MMA, the remaining shifts done in the
@@ -118,7 +127,9 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, i
  * Reads a plan property.  Keys: "last_m", "last_b", "last_engine" (0 CUDA core,
  * 1 tensor core), "last_tile_y" (rows per tile of the last 2D CUDA-core run's
  * first pass), "last_tc_form" (1 per-offset, 2 grouped: the tensor-core kernel
- * of the last tensor-core run), "launches" (kernels the plan has launched so far),
+ * of the last tensor-core run), "last_cp" (separable terms K of the last 2D
+ * CUDA-core run's folded passes in counterpart form, 0 = direct form),
+ * "launches" (kernels the plan has launched so far),
  * "scratch_bytes" (device bytes the plan owns).
  */
 stencil_status_t stencil_plan_get(stencil_plan_t plan, const char *key, int64_t *value);
@@ -194,6 +205,21 @@ stencil_status_t stencil_rel_l2(const void *y, stencil_dtype_t ydtype, const dou
  */
 stencil_status_t stencil_fold_cost(int ndim, int radius, const double *coeffs, int m,
                                    int64_t *out);
+
+/*
+ * Host-only counterpart factorisation (Section 3.3, Eq. vfold and Eq. horifold;
+ * Section 3.5) of W x W folded 2D weights `folded` (row-major, row offset
+ * slowest): the smallest K with folded[a][b] = sum_{k<K} u_k[a] v_k[b], found
+ * by Gaussian elimination with complete pivoting in FP64 (entries below 1e-12
+ * of the largest count as zero).  Writes K to *k_out and K rows of W values to
+ * u_out (the counterparts' vertical weights) and v_out (their horizontal
+ * weights); both must hold max_k * W doubles.  When the rank exceeds max_k,
+ * *k_out = max_k + 1 and the first max_k terms are written.  Needs no GPU.
+ * Errors: INVALID_ARG for W outside 1..17, max_k outside 1..W, or a
+ * null pointer.
+ */
+stencil_status_t stencil_fold_counterparts(int W, const double *folded, int max_k, int *k_out,
+                                           double *u_out, double *v_out);
 
 /*
  * T plain steps of a 1D periodic stencil without allocating any memory.

@@ -31,7 +31,7 @@ EXPORTS = [
     "stencil_plan", "stencil_plan_set_option", "stencil_plan_get", "stencil_run",
     "stencil_run_batched", "stencil_sync", "stencil_folded_coeffs", "stencil_rel_l2",
     "stencil_fold_cost", "stencil_plan_destroy", "stencil_status_string", "stencil_last_error",
-    "stencil_run_1d_noalloc",
+    "stencil_run_1d_noalloc", "stencil_fold_counterparts",
 ]
 
 
@@ -72,6 +72,11 @@ def lib():
         L.stencil_run_1d_noalloc.argtypes = [_vp, _vp, _i64, _c.c_int, ctypes.POINTER(_c.c_double),
                                              _i64, _c.c_int, _vp]
         L.stencil_run_1d_noalloc.restype = _c.c_int
+        L.stencil_fold_counterparts.argtypes = [_c.c_int, ctypes.POINTER(_c.c_double), _c.c_int,
+                                                ctypes.POINTER(_c.c_int),
+                                                ctypes.POINTER(_c.c_double),
+                                                ctypes.POINTER(_c.c_double)]
+        L.stencil_fold_counterparts.restype = _c.c_int
         L.stencil_plan_destroy.argtypes = [_vp]
         L.stencil_plan_destroy.restype = None
         L.stencil_status_string.argtypes = [_c.c_int]
@@ -212,6 +217,25 @@ def fold_cost(coeffs, m: int):
     _check(lib().stencil_fold_cost(c.ndim, r, c.ctypes.data_as(ctypes.POINTER(_c.c_double)), int(m), out),
            "stencil_fold_cost")
     return int(out[0]), int(out[1])
+
+
+def fold_counterparts(folded, max_k: int = 2):
+    """Counterpart factorisation of W x W folded weights; host only.
+
+    Returns (K, u, v) with folded = sum_k outer(u[k], v[k]) for K <= max_k;
+    K = max_k + 1 when the rank is higher (u, v then hold max_k terms).
+    """
+    c = np.ascontiguousarray(np.asarray(folded, dtype=np.float64))
+    W = c.shape[0]
+    k = _c.c_int(0)
+    u = np.zeros((max_k, W))
+    v = np.zeros((max_k, W))
+    P = ctypes.POINTER(_c.c_double)
+    _check(lib().stencil_fold_counterparts(W, c.ctypes.data_as(P), int(max_k), ctypes.byref(k),
+                                           u.ctypes.data_as(P), v.ctypes.data_as(P)),
+           "stencil_fold_counterparts")
+    K = int(k.value)
+    return K, u[:min(K, max_k)], v[:min(K, max_k)]
 
 
 def run_1d_noalloc(x, y, coeffs, T: int, stream=None):

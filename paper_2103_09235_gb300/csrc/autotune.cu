@@ -27,7 +27,7 @@ namespace sg {
 
 namespace {
 
-constexpr const char *kLibVersion = "3";
+constexpr const char *kLibVersion = "4";
 
 struct Cand {
     int engine;  // 0 CUDA core, 1 tensor core
@@ -138,7 +138,11 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
             if (sweep3d_tb_supported(p->r, m, p->pattern) && 2 * R <= std::min(kGhost, nmin))
                 cands.push_back({0, m, 2, 0});
         } else {
-            if (sweep2d_supported(p->r, m, p->pattern))
+            // a direct kernel, or the counterpart form of c^(m) (which also
+            // reaches the folds with no direct kernel, m = 6 and 8)
+            const sg::CpFactor *cp = nullptr;
+            const bool cp_ok = R <= kMaxR2D && plan_counterparts(p, m, &cp) == STENCIL_OK && cp->k > 0;
+            if (sweep2d_supported(p->r, m, p->pattern) || cp_ok)
                 for (int b : {1, 2, 3, 4, 6, 8})
                     if (b * R <= std::min(kGhost, nmin) && (m > 1 || b <= 8))
                         for (int ty : {32, 64, 96, 128, 160})

@@ -27,7 +27,9 @@ constexpr int kMaxR1D = 16;
 // Tap patterns a kernel is specialised for.  A star of base radius rb folded
 // m times keeps tap (a, b[, c]) iff sum ceil(|offset_i| / rb) <= m; a box
 // keeps every tap.
-enum Pattern : int { PAT_STAR = 0, PAT_BOX = 1 };
+// Tap patterns of the 2D/3D kernels.  PAT_CP1 and PAT_CP2 are 2D sweeps in
+// counterpart form (c^(m) = sum of 1 or 2 separable terms).
+enum Pattern : int { PAT_STAR = 0, PAT_BOX = 1, PAT_CP1 = 2, PAT_CP2 = 3 };
 
 // FP32 grid in device memory surrounded by kGhost ghost cells per side.
 // Interior point (x, y, z) lives at origin[z*pz + y*py + x].
@@ -66,7 +68,9 @@ struct Sweep2DArgs {
 };
 
 bool sweep2d_supported(int rb, int m, int pattern);
-size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats, int nstages = 2);
+// cp_bufs: counterpart buffers of a counterpart-pattern pass (its K), else 0.
+size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats, int nstages = 2,
+                          int cp_bufs = 0);
 // threads: 0 = the instance's own block size; 256 = two half-size CTAs for
 // instances that run 512.
 int sweep2d_ctas_per_sm(int rb, int m, int pattern, size_t smem, int threads = 0);

@@ -31,8 +31,14 @@ using namespace tile2d;
 // sweeps of at most 41 taps fit 512 threads (<= 128 registers each) in the
 // one CTA per SM their shared memory allows, doubling the warps that hide
 // FMA and shared-load latency; wider stencils keep 256 threads.
+// Counterpart sweeps (two 1D folds per sweep) keep at most 2R+1 x 4
+// accumulators and run 512 threads.
 template <int RB, int M, int PAT>
-constexpr int threads2d() { return RB * M == 1 ? 256 : (Strip<RB, M, PAT>::NNZ <= 41 ? 512 : 256); }
+constexpr int threads2d()
+{
+    if constexpr (PAT >= PAT_CP1) return 512;
+    else return RB * M == 1 ? 256 : (Strip<RB, M, PAT>::NNZ <= 41 ? 512 : 256);
+}
 template <int RB, int M>
 constexpr int min_blocks() { return RB * M == 1 ? 3 : 1; }
 
@@ -109,9 +115,12 @@ __global__ void __launch_bounds__(threads2d<RB, M, PAT>(), min_blocks<RB, M>())
         auto stage_free = [&]() {
             if (tid == 0 && refill < a.ntiles) issue(refill, st);
         };
+        // counterpart buffers (counterpart patterns only) follow the work buffers
+        const int nwork = a.b >= 3 ? 2 : (a.b == 2 ? 1 : 0);
         process_tile<RB, M, PAT>(buf(st), buf(NS), buf(NS + 1), TY, H, HX, a.b, ParamCoef{a.c},
                                  o, tx * TX - HX, ty * TY - H, min(TX, a.nx - tx * TX),
-                                 min(TY, a.ny - ty * TY), stage_free);
+                                 min(TY, a.ny - ty * TY), stage_free, buf(NS + nwork),
+                                 a.buf_floats);
         __syncthreads();
     }
 }
@@ -164,10 +173,14 @@ int occupancy_t(size_t smem, int threads)
 }
 
 // The instantiated (rb, m, pattern) combinations.
+// (counterpart instances are (1, R, PAT_CPk): folded radius R, k separable terms)
 #define SG_SWEEP2D_LIST(X)                                                                     \
     X(1, 1, PAT_STAR) X(1, 2, PAT_STAR) X(1, 3, PAT_STAR) X(1, 4, PAT_STAR) X(2, 1, PAT_STAR) \
     X(2, 2, PAT_STAR) X(1, 1, PAT_BOX) X(1, 2, PAT_BOX) X(1, 3, PAT_BOX) X(1, 4, PAT_BOX)     \
-    X(2, 1, PAT_BOX) X(2, 2, PAT_BOX) X(3, 1, PAT_BOX) X(4, 1, PAT_BOX)
+    X(2, 1, PAT_BOX) X(2, 2, PAT_BOX) X(3, 1, PAT_BOX) X(4, 1, PAT_BOX)                       \
+    X(1, 1, PAT_CP1) X(1, 2, PAT_CP1) X(1, 3, PAT_CP1) X(1, 4, PAT_CP1) X(1, 6, PAT_CP1)      \
+    X(1, 8, PAT_CP1) X(1, 1, PAT_CP2) X(1, 2, PAT_CP2) X(1, 3, PAT_CP2) X(1, 4, PAT_CP2)      \
+    X(1, 6, PAT_CP2) X(1, 8, PAT_CP2)
 
 }  // namespace
 
@@ -180,12 +193,12 @@ bool sweep2d_supported(int rb, int m, int pattern)
     return false;
 }
 
-size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats, int nstages)
+size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats, int nstages, int cp_bufs)
 {
     const int H = b * R, HX = round_up(H, 4);
     const int SP = TX + 2 * HX, ROWS = tile_y + 2 * H;
     const int bf = round_up(SP * ROWS + 2 * BUF_PAD, 32);
-    const int nbuf = nstages + (b >= 3 ? 2 : (b == 2 ? 1 : 0));
+    const int nbuf = nstages + (b >= 3 ? 2 : (b == 2 ? 1 : 0)) + cp_bufs;
     if (buf_floats) *buf_floats = bf;
     return 1024 + static_cast<size_t>(nbuf) * bf * 4;
 }

@@ -10,6 +10,15 @@
 #include "../../include/stencil.h"
 #include "internal.h"
 
+namespace sg {
+// Counterpart form of c^(m): k separable terms sum_k u_k (x) v_k (u over row
+// offsets, v over column offsets, 2R+1 each); k = 0: the direct form.
+struct CpFactor {
+    int k = 0;
+    std::vector<double> u, v;
+};
+}  // namespace sg
+
 struct stencil_plan_s {
     int device = 0;
     int ndim = 0;
@@ -29,12 +38,15 @@ struct stencil_plan_s {
     int tc_center = 1;
     int tc_tma_store = 1;
     int tc_form = 0;  // tensor cores: 0 by folded radius, 1 one MMA per row offset, 2 grouped
+    int counterparts = 0;  // 2D counterpart form: 0 when cheaper, 1 always (rank <= 2), 2 never
     int autotune = 1;
     long long wait_ms = 2000;
     int fault_withhold_copy = 0;  // test hook, see stencil_plan_set_option
 
     // FP64 folded weights computed on the GPU, by m
     std::map<int, std::vector<double>> folded;
+    // their counterpart form (2D), by m
+    std::map<int, sg::CpFactor> cp;
 
     // device state
     int *d_status = nullptr;
@@ -53,7 +65,8 @@ struct stencil_plan_s {
         int ty, bf, grid, nstages, threads;
         size_t smem;
     };
-    std::map<std::tuple<int, int, int>, PassCfg> pass_cfg;  // (m, b, tile/stage/thread options)
+    // (m, b, tile/stage/thread options and counterpart terms)
+    std::map<std::tuple<int, int, int>, PassCfg> pass_cfg;
 
     // executable graphs of whole runs, keyed by everything a run enqueues
     struct GraphEnt {
@@ -71,6 +84,7 @@ struct stencil_plan_s {
     int last_m = 0, last_b = 0, last_engine = 0;
     int last_tc_form = 0;  // tensor-core kernel of the last tensor-core run (1 or 2)
     int last_ty = 0;  // tile height of the last 2D CUDA-core run's first pass
+    int last_cp = 0;  // counterpart terms of the last 2D CUDA-core run's folded passes (0 = direct)
     // autotuner choice for fold_m = 0: m, b, tile_y, engine (m = 0: not tuned yet)
     int tuned_m = 0, tuned_b = 0, tuned_ty = 0, tuned_engine = 0;
 };
@@ -96,10 +110,17 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
 stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s);
 
 void clear_graphs(stencil_plan_s *p);
-stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b, stencil_plan_s::PassCfg *cfg);
+// cpk: counterpart terms of the pass (0 = direct form); cp: their factors.
+stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b, stencil_plan_s::PassCfg *cfg,
+                               int cpk = 0);
 stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int b,
                                const std::vector<double> &c, float *dst, int64_t dst_py,
-                               int dst_gw, bool dst_vec4, cudaStream_t s);
+                               int dst_gw, bool dst_vec4, cudaStream_t s,
+                               const CpFactor *cp = nullptr);
+// Counterpart factorisation of W x W folded weights (complete pivoting):
+// returns the rank K (max_k + 1 when above max_k) and fills K rows of u, v.
+int cp_factor(const double *c, int W, int max_k, double *u, double *v);
+stencil_status_t plan_counterparts(stencil_plan_s *p, int m, const CpFactor **out);
 void ensure_device_facts(stencil_plan_s *p);
 
 // Runs enqueue(stream, &kernels) on stream s.  With graphs enabled and s not

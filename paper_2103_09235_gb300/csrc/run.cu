@@ -136,9 +136,10 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
 
 // Tile shape, shared memory and grid of a 2D CUDA-core pass (cached per plan).
 stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
-                                      stencil_plan_s::PassCfg *cfg)
+                                      stencil_plan_s::PassCfg *cfg, int cpk)
 {
-    auto key = std::make_tuple(m, b, (p->tile_y * 8 + p->stages) * 1024 + p->cta_threads);
+    auto key = std::make_tuple(m, b,
+                               ((p->tile_y * 8 + p->stages) * 1024 + p->cta_threads) * 4 + cpk);
     auto it = p->pass_cfg.find(key);
     if (it != p->pass_cfg.end()) {
         *cfg = it->second;
@@ -152,24 +153,26 @@ stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
     int ty = p->tile_y > 0 ? p->tile_y : (b == 1 ? 32 : 64);
     int ns = p->stages > 0 ? p->stages : (b == 1 ? 4 : 2);
     int bf = 0;
-    size_t smem = sweep2d_smem_bytes(ty, b, R, &bf, ns);
+    size_t smem = sweep2d_smem_bytes(ty, b, R, &bf, ns, cpk);
     // a blocked pass refills its stage right after a tile's first sweep, so
     // one stage still overlaps the copy with the other sweeps: drop the
     // second stage before shrinking the tile
     if (p->stages <= 0 && b >= 2 && smem > (size_t)p->max_smem) {
         ns = 1;
-        smem = sweep2d_smem_bytes(ty, b, R, &bf, ns);
+        smem = sweep2d_smem_bytes(ty, b, R, &bf, ns, cpk);
     }
     while ((smem > (size_t)p->max_smem || ty + 2 * H > 256) && ty > 16) {
         ty -= 8;
-        smem = sweep2d_smem_bytes(ty, b, R, &bf, ns);
+        smem = sweep2d_smem_bytes(ty, b, R, &bf, ns, cpk);
     }
     if (smem > (size_t)p->max_smem) {
         set_error("2D sweep: halo %d needs too much shared memory", H);
         return STENCIL_ERR_UNSUPPORTED;
     }
     const int ntiles = ceil_div(p->nx, kTileX2D) * ceil_div(p->ny, ty);
-    const int occ = std::max(1, sweep2d_ctas_per_sm(p->r, m, p->pattern, smem, p->cta_threads));
+    // counterpart instances are (1, R, PAT_CPk)
+    const int occ = std::max(1, cpk ? sweep2d_ctas_per_sm(1, R, PAT_CP1 + cpk - 1, smem, p->cta_threads)
+                                    : sweep2d_ctas_per_sm(p->r, m, p->pattern, smem, p->cta_threads));
     cfg->threads = p->cta_threads;
     cfg->ty = ty;
     cfg->nstages = ns;
@@ -183,10 +186,12 @@ stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
 // One CUDA-core 2D pass from padded grid `src` to `dst` (padded origin or dense).
 stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int b,
                                       const std::vector<double> &c, float *dst, int64_t dst_py,
-                                      int dst_gw, bool dst_vec4, cudaStream_t s)
+                                      int dst_gw, bool dst_vec4, cudaStream_t s,
+                                      const CpFactor *cp)
 {
+    const int cpk = cp ? cp->k : 0;
     stencil_plan_s::PassCfg cfg;
-    stencil_status_t st = pass2d_config(p, m, b, &cfg);
+    stencil_status_t st = pass2d_config(p, m, b, &cfg, cpk);
     if (st != STENCIL_OK) return st;
     const int R = m * p->r;
     const int H = b * R, HX = round_up(H, 4);
@@ -210,11 +215,23 @@ stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int 
     a.status = p->d_status;
     a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
     a.fault_withhold_copy = p->fault_withhold_copy;
-    for (size_t k = 0; k < c.size(); ++k) a.c[k] = (float)c[k];
+    if (cpk) {
+        // u_0 .. u_{K-1}, then v_0 .. v_{K-1}
+        const int W = 2 * R + 1;
+        for (int k = 0; k < cpk * W; ++k) {
+            a.c[k] = (float)cp->u[k];
+            a.c[cpk * W + k] = (float)cp->v[k];
+        }
+    } else {
+        for (size_t k = 0; k < c.size(); ++k) a.c[k] = (float)c[k];
+    }
     const int box[2] = {kTileX2D + 2 * HX, cfg.ty + 2 * H};
     const CUtensorMap *map = plan_map(p, src, box);
     if (!map) return STENCIL_ERR_CUDA;
-    cudaError_t e = launch_sweep2d(p->r, m, p->pattern, *map, a, cfg.grid, cfg.smem, cfg.threads, s);
+    cudaError_t e = cpk ? launch_sweep2d(1, R, PAT_CP1 + cpk - 1, *map, a, cfg.grid, cfg.smem,
+                                         cfg.threads, s)
+                        : launch_sweep2d(p->r, m, p->pattern, *map, a, cfg.grid, cfg.smem,
+                                         cfg.threads, s);
     if (e != cudaSuccess) return cuda_fail(e, "2D sweep launch");
     return STENCIL_OK;
 }
@@ -257,7 +274,13 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
         set_error("2D sweep: folded width %d exceeds the grid or the ghost band", 2 * R + 1);
         return STENCIL_ERR_INVALID_ARG;
     }
-    if (!sweep2d_supported(p->r, m, p->pattern) || !sweep2d_supported(p->r, 1, p->pattern)) {
+    // the counterpart form of the folded (and, when forced, the plain) passes
+    const CpFactor *cpm = nullptr, *cp1 = nullptr;
+    stencil_status_t st = plan_counterparts(p, m, &cpm);
+    if (st == STENCIL_OK) st = plan_counterparts(p, 1, &cp1);
+    if (st != STENCIL_OK) return st;
+    if ((!cpm->k && !sweep2d_supported(p->r, m, p->pattern)) ||
+        (!cp1->k && !sweep2d_supported(p->r, 1, p->pattern))) {
         set_error("2D sweep: no CUDA-core kernel for r=%d m=%d", p->r, m);
         return STENCIL_ERR_UNSUPPORTED;
     }
@@ -266,18 +289,19 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
     while (b > 1 && b * R > max_halo) --b;
 
     const std::vector<double> *cm = nullptr, *c1 = nullptr;
-    stencil_status_t st = plan_folded(p, m, &cm);
+    st = plan_folded(p, m, &cm);
     if (st == STENCIL_OK) st = plan_folded(p, 1, &c1);
     if (st == STENCIL_OK) st = ensure_padded(p);
     if (st != STENCIL_OK) return st;
     const std::vector<Pass> passes = make_passes(T, m, b, p->r, max_halo);
+    auto cp_of = [&](const Pass &ps) { return ps.m == m ? cpm : cp1; };
     int gw = 0;
     for (const Pass &ps : passes) gw = std::max(gw, ps.b * ps.m * p->r);
     // resolve every pass configuration before any capture starts
     int first_ty = 0;
     for (const Pass &ps : passes) {
         stencil_plan_s::PassCfg cfg;
-        st = pass2d_config(p, ps.m, ps.b, &cfg);
+        st = pass2d_config(p, ps.m, ps.b, &cfg, cp_of(ps)->k);
         if (st != STENCIL_OK) return st;
         if (!first_ty) first_ty = cfg.ty;
     }
@@ -294,7 +318,8 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
             stencil_status_t r = launch_pass2d(p, *cur, ps.m, ps.b, ps.m == m ? *cm : *c1,
                                                last ? out : oth->origin,
                                                last ? (int64_t)p->nx : oth->py, last ? 0 : gw,
-                                               last ? out_vec4 : true, st_);
+                                               last ? out_vec4 : true, st_,
+                                               cp_of(ps)->k ? cp_of(ps) : nullptr);
             if (r != STENCIL_OK) return r;
             *nl += 1;
             std::swap(cur, oth);
@@ -302,11 +327,12 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
         return STENCIL_OK;
     };
     std::vector<int64_t> key = {2, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, b,
-                                p->tile_y, p->wait_ms, p->fault_withhold_copy};
+                                p->tile_y, p->wait_ms, p->fault_withhold_copy, cpm->k, cp1->k};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = b;
     p->last_ty = first_ty;
+    p->last_cp = cpm->k;
     p->last_engine = 0;
     return st;
 }

@@ -276,6 +276,11 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "fault_withhold_copy")) {
         if (v != 0 && v != 1) goto bad;
         p->fault_withhold_copy = (int)v;
+    } else if (!strcmp(key, "counterparts")) {
+        if (v < 0 || v > 2) goto bad;
+        p->counterparts = (int)v;
+        p->cp.clear();  // the choice per m follows the option
+        p->tuned_m = 0;
     } else if (!strcmp(key, "tc_form")) {
         if (v < 0 || v > 2) goto bad;
         p->tc_form = (int)v;
@@ -310,6 +315,7 @@ stencil_status_t stencil_plan_get(stencil_plan_t p, const char *key, int64_t *va
     else if (!strcmp(key, "last_tile_y")) *value = p->last_ty;
     else if (!strcmp(key, "last_engine")) *value = p->last_engine;
     else if (!strcmp(key, "last_tc_form")) *value = p->last_tc_form;
+    else if (!strcmp(key, "last_cp")) *value = p->last_cp;
     else if (!strcmp(key, "launches")) *value = p->launches;
     else if (!strcmp(key, "scratch_bytes")) *value = (int64_t)p->scratch_bytes;
     else {

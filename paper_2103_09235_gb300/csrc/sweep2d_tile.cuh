@@ -307,6 +307,164 @@ __device__ __forceinline__ void refresh_ghosts(const TileOut &o, int x0, int y0,
     }
 }
 
+// ---- counterpart form (Section 3.3, Eq. vfold and Eq. horifold; Section 3.5)
+// When the folded weights factor as c^(m) = sum_{k<K} u_k (x) v_k (u_k over
+// row offsets, v_k over column offsets), a sweep is a vertical fold of the
+// input with each u_k -- the counterparts V_k -- followed by a horizontal
+// fold that combines the counterparts with the v_k:
+//   V_k[y][x] = sum_a u_k[a] S[y+a][x],   out[y][x] = sum_k sum_b v_k[b] V_k[y][x+b],
+// 2K(2R+1) multiply-adds per point instead of one per nonzero of c^(m).
+// The weights sit in the parameter block as u_0 .. u_{K-1}, then v_0 .. v_{K-1}.
+
+// Vertical fold of rows [r0, r1) and 4-column strips [k0, k1) of S into the
+// counterpart buffers V + k*vstride (same coordinates as S): a register
+// window of 2R+1 output rows per strip, one counterpart at a time, with the
+// same trimmed ramps as sweep_region.
+template <int R, int K, class Sync, class Coef>
+__device__ __forceinline__ void vfold_region(const float *__restrict__ S, float *__restrict__ V,
+                                             int vstride, int SP, int r0, int r1, int k0, int k1,
+                                             const Coef &cf)
+{
+    constexpr int W = 2 * R + 1;
+    const int nsx = k1 - k0, nr = r1 - r0;
+    if (nsx <= 0 || nr <= 0) return;
+    const int nthr = Sync::nthr();
+    int G = nthr / nsx;
+    G = max(1, min(G, nr / (2 * R)));
+    const int items = nsx * G;
+    for (int it = threadIdx.x; it < items; it += nthr) {
+        const int k = k0 + it % nsx, g = it / nsx;
+        const int ya = r0 + (g * nr) / G, yb = r0 + ((g + 1) * nr) / G;
+        const float *col = S + 4 * k;
+#pragma unroll 1
+        for (int q = 0; q < K; ++q) {
+            float acc[W][4];
+#pragma unroll
+            for (int i = 0; i < W; ++i)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
+            float *orow = V + q * vstride + ya * SP + 4 * k;
+            // input row j feeds slot i (output row j - R + i) with weight u_q[R - i]
+            auto feed = [&](int j, int ilo, int ihi) {
+                const float4 x = *reinterpret_cast<const float4 *>(col + j * SP);
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    if (i < ilo || i > ihi) continue;
+                    const float w = cf(q * W + (W - 1 - i));
+                    acc[i][0] = fmaf(w, x.x, acc[i][0]);
+                    acc[i][1] = fmaf(w, x.y, acc[i][1]);
+                    acc[i][2] = fmaf(w, x.z, acc[i][2]);
+                    acc[i][3] = fmaf(w, x.w, acc[i][3]);
+                }
+            };
+            auto emit_shift = [&](bool emit) {
+                if (emit) {
+                    *reinterpret_cast<float4 *>(orow) =
+                        make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                    orow += SP;
+                }
+#pragma unroll
+                for (int i = 0; i < W - 1; ++i)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
+            };
+            int j = ya - R;
+            if (yb - ya >= 2 * R) {
+#pragma unroll
+                for (int u = 0; u < 2 * R; ++u, ++j) {
+                    feed(j, 2 * R - u, W - 1);
+                    emit_shift(false);
+                }
+                const int jm = yb - R;
+#pragma unroll 1
+                for (; j < jm; ++j) {
+                    feed(j, 0, W - 1);
+                    emit_shift(true);
+                }
+#pragma unroll
+                for (int v = 2 * R - 1; v >= 0; --v, ++j) {
+                    feed(j, 0, v);
+                    emit_shift(true);
+                }
+            } else {
+#pragma unroll 1
+                for (; j < yb + R; ++j) {
+                    feed(j, 0, W - 1);
+                    emit_shift(j - R >= ya);
+                }
+            }
+        }
+    }
+}
+
+// Horizontal fold of the counterparts into rows [r0, r1) and strips [k0, k1)
+// of D (or, FINAL, of the global destination), one output row at a time.
+template <int R, int K, bool FINAL, class Sync, class Coef>
+__device__ __forceinline__ void hfold_region(const float *__restrict__ V, int vstride,
+                                             float *__restrict__ D, int SP, int r0, int r1, int k0,
+                                             int k1, const Coef &cf, const TileOut &a, int gx0,
+                                             int gy0)
+{
+    constexpr int W = 2 * R + 1;
+    constexpr int RP = (R + 3) / 4 * 4, NSEG = 4 + 2 * RP;
+    const int nsx = k1 - k0, nr = r1 - r0;
+    if (nsx <= 0 || nr <= 0) return;
+    const int nthr = Sync::nthr();
+    int G = nthr / nsx;
+    G = max(1, min(G, nr));
+    const int items = nsx * G;
+    for (int it = threadIdx.x; it < items; it += nthr) {
+        const int k = k0 + it % nsx, g = it / nsx;
+        const int ya = r0 + (g * nr) / G, yb = r0 + ((g + 1) * nr) / G;
+        const int cx = 4 * k;
+        float *orow;
+        bool fast = false;
+        if constexpr (FINAL) {
+            const int X = gx0 + cx;
+            fast = a.dst_vec4 && X + 3 < a.nx;
+            orow = a.dst + (int64_t)(gy0 + ya) * a.dst_py + X;
+        } else {
+            orow = D + ya * SP + cx;
+        }
+#pragma unroll 1
+        for (int y = ya; y < yb; ++y) {
+            float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                float seg[NSEG];
+                const float4 *rp = reinterpret_cast<const float4 *>(V + q * vstride + y * SP + cx - RP);
+#pragma unroll
+                for (int t = 0; t < NSEG / 4; ++t) {
+                    const float4 x = rp[t];
+                    seg[4 * t] = x.x;
+                    seg[4 * t + 1] = x.y;
+                    seg[4 * t + 2] = x.z;
+                    seg[4 * t + 3] = x.w;
+                }
+#pragma unroll
+                for (int bb = -R; bb <= R; ++bb) {
+                    const float w = cf(K * W + q * W + bb + R);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) o[v] = fmaf(w, seg[v + bb + RP], o[v]);
+                }
+            }
+            if constexpr (FINAL) {
+                if (fast)
+                    *reinterpret_cast<float4 *>(orow) = make_float4(o[0], o[1], o[2], o[3]);
+                else
+                    store_masked4(a.dst, a.dst_py, a.nx, a.dst_vec4, gx0 + cx, gy0 + y, o[0], o[1],
+                                  o[2], o[3]);
+                orow += a.dst_py;
+            } else {
+                *reinterpret_cast<float4 *>(orow) = make_float4(o[0], o[1], o[2], o[3]);
+                orow += SP;
+            }
+        }
+    }
+}
+
 // A callback that does nothing (see process_tile's stage_free).
 struct NoHook {
     __device__ void operator()() const {}
@@ -319,28 +477,59 @@ struct NoHook {
 // every sweep's region is clipped to what those outputs need.  When b >= 2
 // only the first sweep reads the stage: stage_free() runs right after the
 // barrier that ends it, so the caller can refill the stage during the others.
+//
+// Counterpart patterns (PAT_CP1, PAT_CP2: K = 1, 2) take the counterpart
+// buffers at vbuf (K buffers, vstride floats apart); each sweep is a vertical
+// fold into them and a horizontal fold out of them.
 template <int RB, int M, int PAT, class Sync = CtaSync, class Coef, class Hook = NoHook>
 __device__ __forceinline__ void process_tile(const float *stage, float *work0, float *work1,
                                              int TY, int H, int HX, int b, const Coef &cf,
                                              const TileOut &o, int gx0, int gy0, int vx, int vy,
-                                             const Hook &stage_free = Hook())
+                                             const Hook &stage_free = Hook(),
+                                             float *vbuf = nullptr, int vstride = 0)
 {
     constexpr int R = RB * M;
     const int SP = TX + 2 * HX;
     (void)TY;
     const float *src = stage;
-    for (int s = 0; s < b - 1; ++s) {
-        const int sh = (s + 1) * R;  // rim still needed: H - sh per side
-        const int c0 = HX - H + sh, c1 = HX + vx + H - sh;
-        float *dst = (s & 1) ? work1 : work0;
-        sweep_region<RB, M, PAT, false, Sync>(src, dst, SP, sh, 2 * H + vy - sh, c0 / 4,
-                                              (c1 + 3) / 4, cf, o, gx0, gy0);
-        Sync::sync();
-        if (s == 0) stage_free();
-        src = dst;
+    if constexpr (PAT >= PAT_CP1) {
+        constexpr int K = PAT - PAT_CP1 + 1;
+        for (int s = 0; s < b; ++s) {
+            // the region of sweep s: its rim shrinks by R per sweep down to the tile
+            const int sh = (s + 1) * R;
+            const int r0 = sh, r1 = 2 * H + vy - sh;
+            const int c0 = HX - H + sh, c1 = HX + vx + H - sh;
+            vfold_region<R, K, Sync>(src, vbuf, vstride, SP, r0, r1, (c0 - R) / 4,
+                                     (c1 + R + 3) / 4, cf);
+            Sync::sync();
+            if (s == 0 && b >= 2) stage_free();  // the other sweeps read only the counterparts
+            if (s == b - 1) {
+                hfold_region<R, K, true, Sync>(vbuf, vstride, nullptr, SP, r0, r1, c0 / 4,
+                                               (c1 + 3) / 4, cf, o, gx0, gy0);
+            } else {
+                float *dst = (s & 1) ? work1 : work0;
+                hfold_region<R, K, false, Sync>(vbuf, vstride, dst, SP, r0, r1, c0 / 4,
+                                                (c1 + 3) / 4, cf, o, gx0, gy0);
+                Sync::sync();
+                src = dst;
+            }
+        }
+    } else {
+        (void)vbuf;
+        (void)vstride;
+        for (int s = 0; s < b - 1; ++s) {
+            const int sh = (s + 1) * R;  // rim still needed: H - sh per side
+            const int c0 = HX - H + sh, c1 = HX + vx + H - sh;
+            float *dst = (s & 1) ? work1 : work0;
+            sweep_region<RB, M, PAT, false, Sync>(src, dst, SP, sh, 2 * H + vy - sh, c0 / 4,
+                                                  (c1 + 3) / 4, cf, o, gx0, gy0);
+            Sync::sync();
+            if (s == 0) stage_free();
+            src = dst;
+        }
+        sweep_region<RB, M, PAT, true, Sync>(src, nullptr, SP, H, H + vy, HX / 4,
+                                             (HX + vx + 3) / 4, cf, o, gx0, gy0);
     }
-    sweep_region<RB, M, PAT, true, Sync>(src, nullptr, SP, H, H + vy, HX / 4, (HX + vx + 3) / 4,
-                                         cf, o, gx0, gy0);
     refresh_ghosts<Sync>(o, gx0 + HX, gy0 + H, vx, vy);
 }
 

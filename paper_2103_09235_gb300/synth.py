@@ -96,6 +96,40 @@ def dyadic_coeffs(seed: int, ndim: int, radius: int, kind: str) -> np.ndarray:
     return c
 
 
+def _dyadic_1d(seed: int, radius: int, bits: int) -> np.ndarray:
+    """Positive 1D weights k_i / 2**bits summing to exactly 1 (leftover to the centre)."""
+    u = uniform(seed, 2 * radius + 1)
+    raw = 1 + np.floor(u * (1 << 10)).astype(np.int64)
+    denom = 1 << bits
+    k = (raw * denom) // int(raw.sum())
+    k[radius] += denom - int(k.sum())
+    return k.astype(np.float64) / denom
+
+
+def separable_coeffs(seed: int, radius: int, rank: int = 1) -> np.ndarray:
+    """2D box weights that are a sum of `rank` (1 or 2) separable terms.
+
+    Rank 1: outer(u, v) with u, v dyadic 1D weights over 2**12, so every tap is
+    an integer over 2**24 and exact in FP32.  Rank 2: the mean of two such
+    products with 1D weights over 2**11 (taps over 2**23).  Both sum to 1.
+    """
+    if rank == 1:
+        return np.outer(_dyadic_1d(seed, radius, 12), _dyadic_1d(seed + 1, radius, 12))
+    if rank == 2:
+        a = np.outer(_dyadic_1d(seed, radius, 11), _dyadic_1d(seed + 1, radius, 11))
+        b = np.outer(_dyadic_1d(seed + 2, radius, 11), _dyadic_1d(seed + 3, radius, 11))
+        return (a + b) / 2
+    raise ValueError("rank must be 1 or 2")
+
+
+def heat2d_coeffs() -> np.ndarray:
+    """The symmetric 2D 5-point heat stencil: 1/2 at the centre, 1/8 on each axis neighbour."""
+    c = np.zeros((3, 3))
+    c[1, 1] = 0.5
+    c[0, 1] = c[2, 1] = c[1, 0] = c[1, 2] = 0.125
+    return c
+
+
 def heat1d_coeffs() -> np.ndarray:
     """The 1D 3-point heat stencil (0.25, 0.5, 0.25)."""
     return np.array([0.25, 0.5, 0.25], dtype=np.float64)
