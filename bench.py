@@ -239,6 +239,7 @@ def measure_variants(torch, binding, dev, stream, flush, args):
         plan.sync(stream)
         out[name] = {"gstencil_s": float(np.prod(shape)) * T / (ms * 1e-3) / 1e9, "ms": ms,
                      "m": plan.get("last_m"), "b": plan.get("last_b"),
+                     "tile_y": plan.get("last_tile_y") if ndim == 2 else None,
                      "engine": "tensor-core" if plan.get("last_engine") else "cuda-core"}
         if plan.get("last_engine"):
             out[name]["tc_kernel"] = "grouped" if plan.get("last_tc_form") == 2 else "per-offset"
@@ -266,10 +267,10 @@ def measure_variants(torch, binding, dev, stream, flush, args):
     # a separable box (the paper's Gaussian-blur family): counterpart form
     # (Section 3.3) against the direct form, same grid and steps
     s7 = synth.BASE_SEED + 7
-    single("sepbox8192_T512_counterparts_m8", (8192, 8192), "sep", s7, 512, 8, block_b=2)
-    single("sepbox8192_T512_counterparts_m4", (8192, 8192), "sep", s7, 512, 4, block_b=2)
-    single("sepbox8192_T512_direct_m2b2", (8192, 8192), "sep", s7, 512, 2, block_b=2,
-           counterparts=2)
+    single("sepbox8192_T512_autotuned", (8192, 8192), "sep", s7, 512, 0)
+    single("sepbox8192_T512_counterparts_m8b2_ty88", (8192, 8192), "sep", s7, 512, 8, block_b=2,
+           tile_y=88)
+    single("sepbox8192_T512_direct_autotuned", (8192, 8192), "sep", s7, 512, 0, counterparts=2)
     single("star512cube_T200_plain", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1, ndim=3)
     single("star512cube_T200_plain_fused2", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1,
            ndim=3, block_b=2)
