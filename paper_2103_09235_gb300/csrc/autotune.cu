@@ -51,10 +51,11 @@ std::string cache_key(const stencil_plan_s *p)
     cudaGetDeviceProperties(&prop, p->device);
     char buf[512];
     const uint64_t h = fnv1a(p->coeffs.data(), p->coeffs.size() * sizeof(double));
-    snprintf(buf, sizeof(buf), "%d|%lld,%lld,%lld|%d|%d|%016llx|%d|%d|%s|%s", p->ndim,
+    // every option that changes which kernels a candidate can run is part of the key
+    snprintf(buf, sizeof(buf), "%d|%lld,%lld,%lld|%d|%d|%016llx|%d|%d|cp%d|%s|%s", p->ndim,
              (long long)p->shape[0], (long long)p->shape[1], (long long)p->shape[2], p->r,
-             p->pattern, (unsigned long long)h, (int)p->dtype, p->precision, prop.name,
-             kLibVersion);
+             p->pattern, (unsigned long long)h, (int)p->dtype, p->precision, p->counterparts,
+             prop.name, kLibVersion);
     return buf;
 }
 

@@ -76,8 +76,9 @@ __global__ void __launch_bounds__(threads2d<RB, M, PAT>(), min_blocks<RB, M>())
     // while one is computed and a stage is refilled once its tile is done.
     // b >= 2: the stage is free after the tile's first sweep, so it is
     // refilled with the tile NS ahead right then (NS tiles in flight, and a
-    // single stage already overlaps the copy with sweeps 2..b).
-    const bool early = a.b >= 2;
+    // single stage already overlaps the copy with sweeps 2..b).  The
+    // counterpart form frees it after its first vertical fold, for any b.
+    const bool early = a.b >= 2 || PAT >= PAT_CP1;
     // (fault_withhold_copy is a test hook: the first copy is never issued, so
     // the bounded wait below must run out and report a timeout)
     if (tid == 0)

@@ -150,8 +150,10 @@ stencil_status_t pass2d_config(stencil_plan_s *p, int m, int b,
     const int H = b * R;
     // plain single sweeps are memory-bound: small tiles, four in flight per
     // CTA; temporally blocked passes keep taller tiles and double buffering
-    int ty = p->tile_y > 0 ? p->tile_y : (b == 1 ? 32 : 64);
-    int ns = p->stages > 0 ? p->stages : (b == 1 ? 4 : 2);
+    // counterpart passes refill their stage after the first vertical fold:
+    // one stage and the tallest tile that fits
+    int ty = p->tile_y > 0 ? p->tile_y : (cpk ? 160 : (b == 1 ? 32 : 64));
+    int ns = p->stages > 0 ? p->stages : (cpk ? 1 : (b == 1 ? 4 : 2));
     int bf = 0;
     size_t smem = sweep2d_smem_bytes(ty, b, R, &bf, ns, cpk);
     // a blocked pass refills its stage right after a tile's first sweep, so

@@ -316,16 +316,20 @@ __device__ __forceinline__ void refresh_ghosts(const TileOut &o, int x0, int y0,
 // 2K(2R+1) multiply-adds per point instead of one per nonzero of c^(m).
 // The weights sit in the parameter block as u_0 .. u_{K-1}, then v_0 .. v_{K-1}.
 
-// Vertical fold of rows [r0, r1) and 4-column strips [k0, k1) of S into the
-// counterpart buffers V + k*vstride (same coordinates as S): a register
-// window of 2R+1 output rows per strip, one counterpart at a time, with the
-// same trimmed ramps as sweep_region.
+// Vertical fold of rows [r0, r1) and columns [x0, x1) (multiples of 4) of S
+// into the counterpart buffers V + k*vstride (same coordinates as S): a
+// register window of 2R+1 output rows per strip of CW columns, one
+// counterpart at a time, with the same trimmed ramps as sweep_region.  A
+// window needs runs of at least 2R rows, so wide folds (R >= 6) take
+// 2-column strips to keep every thread busy on the same region.
 template <int R, int K, class Sync, class Coef>
 __device__ __forceinline__ void vfold_region(const float *__restrict__ S, float *__restrict__ V,
-                                             int vstride, int SP, int r0, int r1, int k0, int k1,
+                                             int vstride, int SP, int r0, int r1, int x0, int x1,
                                              const Coef &cf)
 {
     constexpr int W = 2 * R + 1;
+    constexpr int CW = R >= 6 ? 2 : 4;
+    const int k0 = x0 / CW, k1 = x1 / CW;
     const int nsx = k1 - k0, nr = r1 - r0;
     if (nsx <= 0 || nr <= 0) return;
     const int nthr = Sync::nthr();
@@ -335,40 +339,52 @@ __device__ __forceinline__ void vfold_region(const float *__restrict__ S, float 
     for (int it = threadIdx.x; it < items; it += nthr) {
         const int k = k0 + it % nsx, g = it / nsx;
         const int ya = r0 + (g * nr) / G, yb = r0 + ((g + 1) * nr) / G;
-        const float *col = S + 4 * k;
+        const float *col = S + CW * k;
 #pragma unroll 1
         for (int q = 0; q < K; ++q) {
-            float acc[W][4];
+            float acc[W][CW];
 #pragma unroll
             for (int i = 0; i < W; ++i)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[i][v] = 0.f;
-            float *orow = V + q * vstride + ya * SP + 4 * k;
+                for (int v = 0; v < CW; ++v) acc[i][v] = 0.f;
+            float *orow = V + q * vstride + ya * SP + CW * k;
             // input row j feeds slot i (output row j - R + i) with weight u_q[R - i]
             auto feed = [&](int j, int ilo, int ihi) {
-                const float4 x = *reinterpret_cast<const float4 *>(col + j * SP);
+                float x[CW];
+                if constexpr (CW == 4) {
+                    const float4 t = *reinterpret_cast<const float4 *>(col + j * SP);
+                    x[0] = t.x;
+                    x[1] = t.y;
+                    x[2] = t.z;
+                    x[3] = t.w;
+                } else {
+                    const float2 t = *reinterpret_cast<const float2 *>(col + j * SP);
+                    x[0] = t.x;
+                    x[1] = t.y;
+                }
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     if (i < ilo || i > ihi) continue;
                     const float w = cf(q * W + (W - 1 - i));
-                    acc[i][0] = fmaf(w, x.x, acc[i][0]);
-                    acc[i][1] = fmaf(w, x.y, acc[i][1]);
-                    acc[i][2] = fmaf(w, x.z, acc[i][2]);
-                    acc[i][3] = fmaf(w, x.w, acc[i][3]);
+#pragma unroll
+                    for (int v = 0; v < CW; ++v) acc[i][v] = fmaf(w, x[v], acc[i][v]);
                 }
             };
             auto emit_shift = [&](bool emit) {
                 if (emit) {
-                    *reinterpret_cast<float4 *>(orow) =
-                        make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                    if constexpr (CW == 4)
+                        *reinterpret_cast<float4 *>(orow) =
+                            make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+                    else
+                        *reinterpret_cast<float2 *>(orow) = make_float2(acc[0][0], acc[0][1]);
                     orow += SP;
                 }
 #pragma unroll
                 for (int i = 0; i < W - 1; ++i)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
+                    for (int v = 0; v < CW; ++v) acc[i][v] = acc[i + 1][v];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
+                for (int v = 0; v < CW; ++v) acc[W - 1][v] = 0.f;
             };
             int j = ya - R;
             if (yb - ya >= 2 * R) {
@@ -480,7 +496,8 @@ struct NoHook {
 //
 // Counterpart patterns (PAT_CP1, PAT_CP2: K = 1, 2) take the counterpart
 // buffers at vbuf (K buffers, vstride floats apart); each sweep is a vertical
-// fold into them and a horizontal fold out of them.
+// fold into them and a horizontal fold out of them, so for any b the stage is
+// free once the first vertical fold has read it.
 template <int RB, int M, int PAT, class Sync = CtaSync, class Coef, class Hook = NoHook>
 __device__ __forceinline__ void process_tile(const float *stage, float *work0, float *work1,
                                              int TY, int H, int HX, int b, const Coef &cf,
@@ -499,10 +516,10 @@ __device__ __forceinline__ void process_tile(const float *stage, float *work0, f
             const int sh = (s + 1) * R;
             const int r0 = sh, r1 = 2 * H + vy - sh;
             const int c0 = HX - H + sh, c1 = HX + vx + H - sh;
-            vfold_region<R, K, Sync>(src, vbuf, vstride, SP, r0, r1, (c0 - R) / 4,
-                                     (c1 + R + 3) / 4, cf);
+            vfold_region<R, K, Sync>(src, vbuf, vstride, SP, r0, r1, (c0 - R) / 4 * 4,
+                                     (c1 + R + 3) / 4 * 4, cf);
             Sync::sync();
-            if (s == 0 && b >= 2) stage_free();  // the other sweeps read only the counterparts
+            if (s == 0) stage_free();  // everything after this reads only the counterparts
             if (s == b - 1) {
                 hfold_region<R, K, true, Sync>(vbuf, vstride, nullptr, SP, r0, r1, c0 / 4,
                                                (c1 + 3) / 4, cf, o, gx0, gy0);

@@ -124,3 +124,21 @@ def test_never_option_matches(env):
     assert (k_cp, k_d) == (1, 0)
     ref = oracle.run(x.astype(np.float64), c, 16)
     assert oracle.rel_l2(y_cp, ref) <= TOL and oracle.rel_l2(y_d, ref) <= TOL
+
+
+def test_autotune_respects_the_option(env, tmp_path, monkeypatch):
+    """The tuning cache keys on the counterparts option: a choice tuned with the
+    counterpart form (a fold with no direct kernel) is not replayed for a plan
+    that forbids it."""
+    torch, binding, oracle = env
+    monkeypatch.setenv("STENCIL_TUNE_CACHE", str(tmp_path / "tune.jsonl"))
+    shape = (256, 512)
+    c = coeffs("sep", 1, 990)
+    x = synth.grid(991, shape, np.float32)
+    T = 24
+    ref = oracle.run(x.astype(np.float64), c, T)
+    for mode in (0, 2, 0, 2):
+        y, k = run(env, shape, c, x, T, 0, 0, mode)
+        assert oracle.rel_l2(y, ref) <= TOL
+        if mode == 2:
+            assert k == 0
