@@ -262,6 +262,9 @@ def measure_variants(torch, binding, dev, stream, flush, args):
     s1 = synth.BASE_SEED + 1
     single("heat1d_2pow20_T100_fp32", (1 << 20,), "heat", s1, 100, 1, ndim=1)
     single("heat1d_2pow20_T100_fp64", (1 << 20,), "heat", s1, 100, 1, ndim=1, dtype="f64")
+    single("heat1d_2pow20_T100_fp32_autotuned", (1 << 20,), "heat", s1, 100, 0, ndim=1)
+    single("heat1d_2pow20_T100_fp64_autotuned", (1 << 20,), "heat", s1, 100, 0, ndim=1,
+           dtype="f64")
     s2 = synth.BASE_SEED + 2
     single("star4096_T1000_plain_fp32", (4096, 4096), "star", s2, 1000, 1, block_b=1)
     single("star4096_T1000_tc_bf16x3_m4", (4096, 4096), "star", s2, 1000, 4, precision=1)

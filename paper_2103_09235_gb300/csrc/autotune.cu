@@ -27,7 +27,7 @@ namespace sg {
 
 namespace {
 
-constexpr const char *kLibVersion = "4";
+constexpr const char *kLibVersion = "5";
 
 struct Cand {
     int engine;  // 0 CUDA core, 1 tensor core
@@ -122,7 +122,7 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     // candidate list
     const int nmin = p->ndim == 1 ? p->nx : std::min(p->nx, p->ndim == 3 ? std::min(p->ny, p->nz) : p->ny);
     std::vector<Cand> cands;
-    for (int m = 1; m <= 8; ++m) {
+    for (int m = 1; m <= (p->ndim == 1 ? 16 : 8); ++m) {
         const int R = m * p->r;
         if (2 * R + 1 > nmin || R > kGhost) break;
         if (m > 1) {
@@ -132,7 +132,10 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
                 continue;  // P = |C(E)| / |C(E_lambda)| < 1: folding is not profitable
         }
         if (p->ndim == 1) {
-            if (m <= 4 && sweep1d_supported(R, p->dtype == STENCIL_F64))
+            // every fold the 1D kernel has (radius up to 16): a fold costs
+            // (2m+1)/m multiply-adds per step but saves m-1 shared-memory
+            // round trips, and FP64 in particular is bound by the former
+            if (sweep1d_supported(R, p->dtype == STENCIL_F64))
                 for (int b : {16, 32, 64}) cands.push_back({0, m, b, 0});
         } else if (p->ndim == 3) {
             if (sweep3d_supported(p->r, m, p->pattern)) cands.push_back({0, m, 1, 0});

@@ -110,6 +110,9 @@ CASES_1D = [
     (1000, 1, 1, "f32"), (4097, 37, 1, "f32"), (65539, 100, 1, "f32"), (65539, 100, 2, "f32"),
     (65539, 99, 3, "f32"), (4097, 37, 1, "f64"), (65539, 100, 1, "f64"), (65539, 101, 4, "f64"),
     (9, 50, 1, "f64"), (300, 64, 1, "f32"),
+    # deep 1D folds (radius 8 and 16) with a plain remainder
+    (65539, 101, 8, "f32"), (65539, 100, 16, "f32"), (65539, 83, 8, "f64"),
+    (65539, 100, 16, "f64"), (1000, 37, 16, "f32"),
 ]
 
 
