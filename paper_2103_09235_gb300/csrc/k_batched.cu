@@ -60,6 +60,24 @@ struct SmemCoef {
     __device__ __forceinline__ float operator()(int k) const { return c[k]; }
 };
 
+// A tile's weights copied from its slot into registers once: read through the
+// slot pointer, every tap of every row would be a shared-memory load (the
+// compiler cannot prove the slot apart from the work buffers the sweep
+// stores to).  Only the taps the pattern uses are ever read, so the copies of
+// the others are dropped.  Patterns of up to 25 taps take this form; the
+// 41-tap star (m = 4) keeps its weights in shared memory, where its registers
+// would otherwise spill.
+template <int N>
+struct RegCoef {
+    float w[N];
+    __device__ __forceinline__ explicit RegCoef(const float *c)
+    {
+#pragma unroll
+        for (int k = 0; k < N; ++k) w[k] = c[k];
+    }
+    __device__ __forceinline__ float operator()(int k) const { return w[k]; }
+};
+
 __device__ __forceinline__ int ld_acquire(const int *p)
 {
     int v;
@@ -95,10 +113,17 @@ __device__ __forceinline__ void run_variant(const StageMeta &md, const float *st
 {
     const TileOut o{md.dst, md.dst_py, md.nx, md.ny, md.dst_gw, md.dst_vec4};
 #define SG_BATCHED_CASE(P_, M_)                                                                 \
-    case P_ * 8 + M_:                                                                           \
-        process_tile<1, M_, P_, ConsumerSync>(stage, w0, w1, TY, md.H, md.HX, md.b, cf, o,      \
-                                              md.gx0, md.gy0, md.vx, md.vy, stage_free);        \
-        break;
+    case P_ * 8 + M_: {                                                                         \
+        if constexpr (Strip<1, M_, P_>::NNZ <= 25) {                                            \
+            const RegCoef<(2 * M_ + 1) * (2 * M_ + 1)> rc(cf.c);                                \
+            process_tile<1, M_, P_, ConsumerSync>(stage, w0, w1, TY, md.H, md.HX, md.b, rc, o,  \
+                                                  md.gx0, md.gy0, md.vx, md.vy, stage_free);    \
+        } else {                                                                                \
+            process_tile<1, M_, P_, ConsumerSync>(stage, w0, w1, TY, md.H, md.HX, md.b, cf, o,  \
+                                                  md.gx0, md.gy0, md.vx, md.vy, stage_free);    \
+        }                                                                                       \
+        break;                                                                                  \
+    }
     switch (md.variant) {
         SG_BATCHED_CASE(PAT_STAR, 1)
         SG_BATCHED_CASE(PAT_STAR, 2)
