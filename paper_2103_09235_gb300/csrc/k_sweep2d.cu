@@ -58,6 +58,10 @@ __global__ void __launch_bounds__(threads2d<RB, M, PAT>(), min_blocks<RB, M>())
     const uint32_t box_bytes = static_cast<uint32_t>(SP) * ROWS * 4u;
     const int tid = threadIdx.x;
 
+    // the item split of each sweep of a full tile, worked out once per CTA
+    // (bytes 512.. of the control block; the barriers use the first 48)
+    SweepGeom *geom = reinterpret_cast<SweepGeom *>(smem + 512);
+    if (tid < a.b) full_tile_geom<RB * M>(geom, tid, a.b, a.tile_y, a.halo, a.halo_x, blockDim.x);
     if (tid == 0) {
         prefetch_tensormap(&map);
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(threads2d<RB, M, PAT>(), min_blocks<RB, M>())
         process_tile<RB, M, PAT>(buf(st), buf(NS), buf(NS + 1), TY, H, HX, a.b, ParamCoef{a.c},
                                  o, tx * TX - HX, ty * TY - H, min(TX, a.nx - tx * TX),
                                  min(TY, a.ny - ty * TY), stage_free, buf(NS + nwork),
-                                 a.buf_floats);
+                                 a.buf_floats, geom);
         __syncthreads();
     }
 }

@@ -135,9 +135,26 @@ static __device__ __noinline__ void store_masked4(float *dst, int64_t py, int nx
     if (X + 3 < nx) row[X + 3] = v3;
 }
 
+// The thread-to-item split of one sweep of a full tile, the same for every
+// full tile of a launch, so each CTA works it out once: nsx strips by G row
+// groups over nr rows, with q / nsx = umulhi(q, mn) and q / G = umulhi(q, mg)
+// (mn = ceil(2^32 / nsx), mg = ceil(2^32 / G); exact for q below 2^17 with
+// divisors below 2^9, since q * (m * d - 2^32) < 2^32 then).
+struct SweepGeom {
+    int nsx_G;    // nsx | G << 16
+    uint32_t mn, mg;
+    int nr;
+};
+
+__host__ __device__ inline uint32_t div_magic(uint32_t d)
+{
+    return (uint32_t)((0x100000000ull + d - 1) / d);
+}
+
 // One sweep over output rows [r0, r1) and 4-column strips [k0, k1) of a
 // shared-memory buffer S (row pitch SP).  FINAL writes to global memory;
-// otherwise the outputs go to the same coordinates of buffer D.
+// otherwise the outputs go to the same coordinates of buffer D.  gm, when
+// given, is the precomputed split of this sweep (full tiles).
 //
 // A strip of rows [ya, yb) reads input rows ya-R .. yb+R-1.  The first 2R
 // rows only feed window slots whose output row is >= ya and the last 2R only
@@ -145,7 +162,8 @@ static __device__ __noinline__ void store_masked4(float *dst, int64_t py, int nx
 template <int RB, int M, int PAT, bool FINAL, class Sync, class Coef>
 __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float *__restrict__ D,
                                              int SP, int r0, int r1, int k0, int k1,
-                                             const Coef &cf, const TileOut &a, int gx0, int gy0)
+                                             const Coef &cf, const TileOut &a, int gx0, int gy0,
+                                             const SweepGeom *gm = nullptr)
 {
     using ST = Strip<RB, M, PAT>;
     constexpr int R = ST::R, W = ST::W, RP = ST::RP, NSEG = ST::NSEG;
@@ -154,15 +172,32 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
     if (nsx <= 0 || nr <= 0) return;
     // row groups: as many as the threads allow, each at least 2R rows tall
     const int nthr = Sync::nthr();  // 256 or 512, chosen per kernel instance
-    int G = nthr / nsx;
-    G = max(1, min(G, nr / (2 * R)));
+    int G;
+    uint32_t mn = 0, mg = 0;
+    if (gm && gm->nsx_G == 0) gm = nullptr;  // a split without a usable reciprocal
+    if (gm) {
+        G = gm->nsx_G >> 16;
+        mn = gm->mn;
+        mg = gm->mg;
+    } else {
+        G = nthr / nsx;
+        G = max(1, min(G, nr / (2 * R)));
+    }
     const int items = nsx * G;
 
     for (int it = threadIdx.x; it < items; it += nthr) {
-        const int k = k0 + it % nsx;
-        const int g = it / nsx;
-        const int ya = r0 + (g * nr) / G;
-        const int yb = r0 + ((g + 1) * nr) / G;
+        int k, g, ya, yb;
+        if (gm) {
+            g = (int)__umulhi((uint32_t)it, mn);
+            k = k0 + it - g * nsx;
+            ya = r0 + (int)__umulhi((uint32_t)(g * nr), mg);
+            yb = r0 + (int)__umulhi((uint32_t)((g + 1) * nr), mg);
+        } else {
+            k = k0 + it % nsx;
+            g = it / nsx;
+            ya = r0 + (g * nr) / G;
+            yb = r0 + ((g + 1) * nr) / G;
+        }
         const int cx = 4 * k;
         const float *col = S + cx - RP;
 
@@ -481,6 +516,34 @@ __device__ __forceinline__ void hfold_region(const float *__restrict__ V, int vs
     }
 }
 
+// The item split of every sweep of a full tile (TX x TY outputs, halo H rows
+// and HX columns, b sweeps of radius R) for blocks of nthr threads; sweep s
+// goes to g[s].  Run by one thread per sweep (s = threadIdx.x < b).
+template <int R>
+__device__ __forceinline__ void full_tile_geom(SweepGeom *g, int s, int b, int TY, int H, int HX,
+                                               int nthr)
+{
+    int nr, k0, k1;
+    if (s < b - 1) {
+        const int sh = (s + 1) * R;
+        nr = 2 * H + TY - 2 * sh;
+        k0 = (HX - H + sh) / 4;
+        k1 = (HX + TX + H - sh + 3) / 4;
+    } else {
+        nr = TY;
+        k0 = HX / 4;
+        k1 = (HX + TX + 3) / 4;
+    }
+    const int nsx = k1 - k0;
+    int G = nthr / nsx;
+    G = max(1, min(G, nr / (2 * R)));
+    // a divisor of 1 has no 32-bit reciprocal: such sweeps keep the divisions
+    g[s].nsx_G = (nsx >= 2 && G >= 2) ? (nsx | (G << 16)) : 0;
+    g[s].mn = div_magic((uint32_t)nsx);
+    g[s].mg = div_magic((uint32_t)G);
+    g[s].nr = nr;
+}
+
 // A callback that does nothing (see process_tile's stage_free).
 struct NoHook {
     __device__ void operator()() const {}
@@ -503,7 +566,8 @@ __device__ __forceinline__ void process_tile(const float *stage, float *work0, f
                                              int TY, int H, int HX, int b, const Coef &cf,
                                              const TileOut &o, int gx0, int gy0, int vx, int vy,
                                              const Hook &stage_free = Hook(),
-                                             float *vbuf = nullptr, int vstride = 0)
+                                             float *vbuf = nullptr, int vstride = 0,
+                                             const SweepGeom *geom = nullptr)
 {
     constexpr int R = RB * M;
     const int SP = TX + 2 * HX;
@@ -534,18 +598,22 @@ __device__ __forceinline__ void process_tile(const float *stage, float *work0, f
     } else {
         (void)vbuf;
         (void)vstride;
+        // the precomputed item splits hold for full tiles only
+        const SweepGeom *gm = (vx == TX && vy == TY) ? geom : nullptr;
         for (int s = 0; s < b - 1; ++s) {
             const int sh = (s + 1) * R;  // rim still needed: H - sh per side
             const int c0 = HX - H + sh, c1 = HX + vx + H - sh;
             float *dst = (s & 1) ? work1 : work0;
             sweep_region<RB, M, PAT, false, Sync>(src, dst, SP, sh, 2 * H + vy - sh, c0 / 4,
-                                                  (c1 + 3) / 4, cf, o, gx0, gy0);
+                                                  (c1 + 3) / 4, cf, o, gx0, gy0,
+                                                  gm ? gm + s : nullptr);
             Sync::sync();
             if (s == 0) stage_free();
             src = dst;
         }
         sweep_region<RB, M, PAT, true, Sync>(src, nullptr, SP, H, H + vy, HX / 4,
-                                             (HX + vx + 3) / 4, cf, o, gx0, gy0);
+                                             (HX + vx + 3) / 4, cf, o, gx0, gy0,
+                                             gm ? gm + (b - 1) : nullptr);
     }
     refresh_ghosts<Sync>(o, gx0 + HX, gy0 + H, vx, vy);
 }
