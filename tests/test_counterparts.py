@@ -126,3 +126,22 @@ def test_bad_arguments(blib):
 def test_zero_weights(blib):
     K, u, v = blib.fold_counterparts(np.zeros((5, 5)), 2)
     assert K == 0
+
+
+@pytest.mark.parametrize("r", [1, 2, 4])
+@pytest.mark.parametrize("rank", [1, 2])
+def test_separable_generator(r, rank):
+    """The separable test weights are exact in FP32, positive, sum to exactly 1
+    and have the stated rank (numpy's SVD rank, independent of the library)."""
+    c = synth.separable_coeffs(960 + r, r, rank)
+    assert c.shape == (2 * r + 1, 2 * r + 1)
+    assert np.all(c > 0)
+    assert np.array_equal(c.astype(np.float32).astype(np.float64), c)
+    assert c.sum() == 1.0
+    assert np.linalg.matrix_rank(c) == rank
+
+
+def test_heat2d_weights():
+    c = synth.heat2d_coeffs()
+    assert c.sum() == 1.0 and np.count_nonzero(c) == 5
+    assert np.linalg.matrix_rank(c) == 2

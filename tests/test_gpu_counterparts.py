@@ -142,3 +142,14 @@ def test_autotune_respects_the_option(env, tmp_path, monkeypatch):
         assert oracle.rel_l2(y, ref) <= TOL
         if mode == 2:
             assert k == 0
+
+
+def test_option_range(env):
+    torch, binding, _ = env
+    plan = binding.Plan((64, 64), coeffs("sep", 1, 995))
+    for bad in (-1, 3):
+        with pytest.raises(binding.StencilError):
+            plan.set_option("counterparts", bad)
+    for ok in (0, 1, 2):
+        plan.set_option("counterparts", ok)
+    plan.close()
