@@ -84,12 +84,16 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
  *                   m*r <= 8) on the tensor cores; plain steps stay on CUDA cores.
  *   "block_b"       temporal-blocking depth: folded sweeps per memory round trip
  *                   (0 = automatic).
- *   "tile_y"        rows per CTA tile of the 2D CUDA-core sweep (0 = automatic).
+ *   "tile_y"        rows per CTA tile of the 2D CUDA-core sweep (0 = automatic: 32
+ *                   for single sweeps, 64 for blocked ones, 160 in counterpart form,
+ *                   lowered until the tile fits in shared memory).
  *   "stages"        TMA stages per CTA of the 2D CUDA-core sweep, 1..6 (0 =
  *                   automatic: 4 for single sweeps; 2 for blocked ones, or 1 when
- *                   two do not fit the tile).  A blocked pass refills a stage
- *                   after the tile's first sweep, so 1 still overlaps copies with
- *                   compute; a single-sweep pass with 1 stage does not.
+ *                   two do not fit the tile; 1 in counterpart form).  A blocked
+ *                   pass refills a stage after the tile's first sweep, and a
+ *                   counterpart-form pass after its first vertical fold, so 1
+ *                   still overlaps copies with compute; a direct single-sweep
+ *                   pass with 1 stage does not.
  *   "cta_threads"   threads per CTA of the 2D CUDA-core sweep: 0 = automatic
  *                   (chosen by the autotuner, else the kernel's own size), 256 =
  *                   two half-size CTAs per SM for folded sweeps that run 512.
