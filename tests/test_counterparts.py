@@ -145,3 +145,22 @@ def test_heat2d_weights():
     c = synth.heat2d_coeffs()
     assert c.sum() == 1.0 and np.count_nonzero(c) == 5
     assert np.linalg.matrix_rank(c) == 2
+
+
+def test_scalar_and_sparse_weights(blib, oracle_mod):
+    """A single weight is one term; a folded star keeps its zero corners
+    (the factors rebuild them exactly); asking for W terms of a full-rank
+    matrix returns its rank."""
+    K, u, v = blib.fold_counterparts(np.array([[0.75]]), 1)
+    assert K == 1 and u[0][0] * v[0][0] == 0.75
+    cm = oracle_mod.fold_coeffs(synth.dyadic_coeffs(971, 2, 1, "star"), 2)
+    W = cm.shape[0]
+    K, u, v = blib.fold_counterparts(cm, W)
+    R = rebuilt(u, v)
+    assert np.max(np.abs(R - cm)) < 1e-15
+    assert np.all(np.abs(R[cm == 0]) < 1e-15)
+    rng = np.random.default_rng(972)
+    full = rng.random((9, 9))
+    K, u, v = blib.fold_counterparts(full, 9)
+    assert K == np.linalg.matrix_rank(full) == 9
+    assert np.max(np.abs(rebuilt(u, v) - full)) < 1e-13
