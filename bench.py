@@ -1,9 +1,21 @@
 """Benchmark of the folded-stencil hot path on one GB300 (or N replicas).
 
-Workload: 2D 5-point star, 4096 x 4096 FP32 grid, seeded dyadic coefficients
-summing to 1, values uniform in [0, 1), periodic, T = 1000 steps, advanced by
-temporal computation folding with temporal blocking.  One "step" of this
-bench is one full stencil_run of T = 1000 time steps on that grid.
+Headline workload: 2D 5-point star, 4096 x 4096 FP32 grid, seeded dyadic
+coefficients summing to 1, values uniform in [0, 1), periodic, T = 1000
+steps, advanced by temporal computation folding with temporal blocking.  One
+"step" of this bench is one full stencil_run of T = 1000 time steps on that
+grid.  The other workloads (1D heat, the 8192^2 box on CUDA and tensor cores,
+a separable box in counterpart form, the 3D star and box, the 256-grid batch)
+are reported in ``variants`` with the same fields as the headline: GStencil/s,
+the roofline of their dominant kernel, the SM clocks seen while they ran, and
+the relative L2 error of the timed output against the FP64 oracle.
+
+Roofline of a pass (one kernel launch): t_roof = max(bytes / HBM bandwidth,
+algorithmic flops / pipe peak), where bytes = one read and one write of the
+grid, and flops = the folded stencil's own multiply-adds (2 nnz(c^(m)) - 1 per
+point and sweep; in counterpart form the two folds' 2K(2R+1) multiply-adds).
+``bound`` names the larger term, ``achieved`` is that term's quantity over the
+measured pass time, ``frac`` = t_roof / pass time.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload instead.
@@ -12,6 +24,7 @@ oracle on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import bisect
 import json
 import os
 import statistics
@@ -48,69 +61,88 @@ CONFIGS = {
     "sepbox8192": dict(shape=(8192, 8192), T=512, kind="sep", seed=synth.BASE_SEED + 7,
                        workload="2D 9-point separable box 8192x8192 FP32, periodic, T=512, "
                                 "outer product of seeded dyadic 1D weights"),
+    "heat1d": dict(shape=(1 << 20,), T=100, kind="heat", seed=synth.BASE_SEED + 1,
+                   workload="1D 3-point heat stencil (1/4, 1/2, 1/4), 2^20 points FP32, "
+                            "periodic, T=100"),
 }
-
-
-def config_coeffs(seed: int, ndim: int, kind: str) -> np.ndarray:
-    """The weights of a configuration: seeded dyadic star/box, or a separable box."""
-    if kind == "sep":
-        return synth.separable_coeffs(seed, 1, 1)
-    return synth.dyadic_coeffs(seed, ndim, 1, kind)
-SHAPE = CONFIGS["star4096"]["shape"]
-T_STEPS = CONFIGS["star4096"]["T"]
-KIND = CONFIGS["star4096"]["kind"]
-SEED = CONFIGS["star4096"]["seed"]
-WORKLOAD = CONFIGS["star4096"]["workload"]
-
-
-def select_config(name: str):
-    global SHAPE, T_STEPS, KIND, SEED, WORKLOAD
-    c = CONFIGS[name]
-    SHAPE, T_STEPS, KIND, SEED, WORKLOAD = c["shape"], c["T"], c["kind"], c["seed"], c["workload"]
 L2_FLUSH_BYTES = 512 << 20
 
 
-def load_peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    try:
-        with open(path) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    except Exception:
-        return 6800.0, "fallback"
+def config_coeffs(seed: int, ndim: int, kind: str) -> np.ndarray:
+    """The weights of a workload: 1D heat, seeded dyadic star/box, or a separable box."""
+    if kind == "heat":
+        return synth.heat1d_coeffs()
+    if kind == "sep":
+        return synth.separable_coeffs(seed, 1, 1)
+    return synth.dyadic_coeffs(seed, ndim, 1, kind)
 
 
-def load_tensor_peak():
-    """Dense BF16 TFLOP/s measured with cuBLAS over seconds (MEASURED_PEAKS.json)."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops_sustained"])
-    except Exception:
-        return 1700.0
+def workload_config(name: str) -> dict:
+    """The `config` object of a workload: what it is, not how it was run."""
+    c = CONFIGS[name]
+    return {"workload": c["workload"], "grid": list(c["shape"]), "T": c["T"]}
 
 
-def fp32_peak_tflops():
-    """CUDA-core FP32 peak: 152 SMs x 128 FMA/clk x 2 flop x the measured max SM clock."""
-    mhz = 2070.0
+# ---- peaks --------------------------------------------------------------------
+
+def _peaks_file():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+            return json.load(f)
     except Exception:
-        pass
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+        return None
 
+
+def hbm_peak():
+    d = _peaks_file()
+    if d and "hbm_gbs" in d:
+        return float(d["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def tensor_peak():
+    """Dense BF16 TFLOP/s, sustained (the kernels run inside long steps)."""
+    d = _peaks_file()
+    if d and "bf16_tflops_sustained" in d:
+        return float(d["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained"
+    return 1700.0, "fallback 1.7 PFLOP/s sustained"
+
+
+def sm_max_mhz():
+    d = _peaks_file()
+    try:
+        return float(d.get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 2070.0
+
+
+def fp32_peak(sms: int):
+    """CUDA-core FP32: SMs x 128 FMA/clk x 2 flop x the maximum SM clock."""
+    return sms * 128 * 2 * sm_max_mhz() * 1e6 / 1e12, \
+        "%d SMs x 128 FP32 FMA/clk x 2 flop x %.0f MHz" % (sms, sm_max_mhz())
+
+
+def fp64_peak():
+    """GB300's nominal dense FP64 rate (no measured figure exists on this machine)."""
+    return 1.25, "nominal GB300 FP64 1.25 TFLOP/s"
+
+
+# ---- clocks -----------------------------------------------------------------------
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+    """Samples nvidia-smi SM clocks and throttle reasons while running; each
+    sample is stamped with the host time it was read, so that the samples of
+    any time window can be summarised."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.samples = []  # (host time, sm MHz, max MHz, reasons)
         self.thread = None
 
     def start(self):
@@ -127,11 +159,19 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            parts = [p.strip() for p in line.strip().split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm, smax = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            reasons = {nm for nm, v in zip(self.NAMES, parts[5:9]) if v.lower() == "active"}
+            self.samples.append((time.time(), sm, smax, reasons))
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -139,23 +179,22 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+
+    def summary(self, t0=None, t1=None):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        s = self.samples
+        if t0 is not None:
+            sel = [x for x in s if t0 <= x[0] <= t1]
+            if not sel and s:  # a window shorter than the sampling period: nearest sample
+                times = [x[0] for x in s]
+                i = min(bisect.bisect_left(times, 0.5 * (t0 + t1)), len(s) - 1)
+                sel = [s[i]]
+            s = sel
+        return {"sm_mhz": statistics.median([x[1] for x in s]) if s else None,
+                "sm_max_mhz": max(x[2] for x in s) if s else None,
+                "reasons": sorted(set().union(*[x[3] for x in s])) if s else [],
+                "samples": len(s)}
 
 
 def dist_env():
@@ -165,51 +204,86 @@ def dist_env():
     return ws, rank, local
 
 
-def oracle_sample(T_sample: int, shape=None):
-    """Times the FP64 oracle on a bounded sample: the full grid, T_sample steps."""
-    import oracle
-    shape = SHAPE if shape is None else shape
-    c = config_coeffs(SEED, len(shape), KIND)
-    x = synth.grid(SEED, shape, np.float32).astype(np.float64)
-    t0 = time.perf_counter()
-    oracle.run(x, c, T_sample)
-    dt = time.perf_counter() - t0
-    return float(np.prod(shape)) * T_sample / dt / 1e9, dt, oracle.max_threads()
+# ---- the CPU-baseline leg: the only part of this file that runs the oracle ----
 
+class OracleLeg:
+    """The CPU-baseline leg.
 
-def calibrate_oracle_steps(target_s: float) -> int:
-    _, dt, _ = oracle_sample(2)
-    return int(max(2, min(2000, round(target_s / max(dt / 2, 1e-6)))))
+    It times the FP64 C oracle on the host cores (the ``cpu_baseline`` field
+    and the reference arm), and it provides the oracle's results against which
+    the accuracy of every timed GPU output is reported: the plain time loop
+    for the 1D workloads, the per-Fourier-mode closed form (spectral_run)
+    elsewhere.  Nothing else in this file imports the oracle.
+    """
+
+    def __init__(self):
+        import oracle
+        self.oracle = oracle
+        self.cache = {}
+
+    def sample(self, name: str, T_sample: int):
+        """Times the oracle on the full grid of a workload for T_sample steps."""
+        w = CONFIGS[name]
+        c = config_coeffs(w["seed"], len(w["shape"]), w["kind"])
+        x = synth.grid(w["seed"], w["shape"], np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        self.oracle.run(x, c, T_sample)
+        dt = time.perf_counter() - t0
+        return float(np.prod(w["shape"])) * T_sample / dt / 1e9, dt, self.oracle.max_threads()
+
+    def calibrate(self, name: str, target_s: float) -> int:
+        _, dt, _ = self.sample(name, 2)
+        return int(max(2, min(2000, round(target_s / max(dt / 2, 1e-6)))))
+
+    def expected(self, x: np.ndarray, c: np.ndarray, T: int) -> np.ndarray:
+        """The FP64 result of T plain steps of c applied to x."""
+        x64 = np.asarray(x, np.float64)
+        if x.ndim == 1:
+            return self.oracle.run(x64, c, T)
+        return self.oracle.spectral_run(x64, c, T)
+
+    def reference(self, key, x, c, T):
+        if key not in self.cache:
+            self.cache = {key: self.expected(x, c, T)}  # one workload held at a time
+        return self.cache[key]
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands, timed on the host cores."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    T_sample = calibrate_oracle_steps(max(1.0, 60.0 / max(1, args.steps + args.warmup)))
+    leg = OracleLeg()
+    w = CONFIGS[args.config]
+    # each timed step is a bounded sample of the workload: the whole grid for
+    # T_sample of its T steps, sized so that warm-up and timed steps take
+    # about a minute together
+    T_sample = leg.calibrate(args.config, max(1.0, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_sample(T_sample)
+        leg.sample(args.config, T_sample)
     vals, secs = [], []
     cores = 1
     for _ in range(args.steps):
-        v, dt, cores = oracle_sample(T_sample)
+        v, dt, cores = leg.sample(args.config, T_sample)
         vals.append(v)
         secs.append(dt)
-    value = statistics.median(vals)
-    ms = 1e3 * float(np.prod(SHAPE)) * T_STEPS / (value * 1e9)
-    sample = "full %s grid, %d of the %d steps per timed step (FP64 C oracle, OpenMP)" % (
-        "x".join(map(str, SHAPE)), T_sample, T_STEPS)
+    npts = float(np.prod(w["shape"]))
+    value = npts * T_sample * args.steps / sum(secs) / 1e9
+    sample = ("full %s grid, %d of the workload's %d steps per timed step "
+              "(FP64 C oracle, OpenMP)" % ("x".join(map(str, w["shape"])), T_sample, w["T"]))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": list(SHAPE), "T": T_STEPS},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.config),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
+
+# ---- timing and rooflines -------------------------------------------------------
 
 def _time_runs(torch, stream, flush, fn, reps=3, warm=1):
     for _ in range(warm):
@@ -228,87 +302,231 @@ def _time_runs(torch, stream, flush, fn, reps=3, warm=1):
     return statistics.median(ts)
 
 
-def measure_variants(torch, binding, dev, stream, flush, args):
-    """GStencil/s of the plain baseline and the other configurations."""
-    out = {}
+def full_passes(T: int, m: int, b: int) -> int:
+    """Passes of b folded sweeps that a run of T steps makes in full."""
+    return (T // m) // b
 
-    def single(name, shape, kind, seed, T, m, ndim=2, dtype="f32", **opts):
-        if kind == "heat":
-            c = synth.heat1d_coeffs()
-        elif kind == "sep":  # a separable 9-point box (one counterpart at every m)
-            c = synth.separable_coeffs(seed, 1, 1)
-        else:
-            c = synth.dyadic_coeffs(seed, ndim, 1, kind)
+
+def pass_roofline(npts, m, b, R, nnz, cp_k, esz, pass_ms, engine, sms):
+    """Roofline of one pass of b fused sweeps of the m-folded stencil."""
+    hbm, hbm_src = hbm_peak()
+    alg_bytes = 2.0 * esz * npts
+    if cp_k:
+        # counterpart form: K vertical and K horizontal folds of 2R+1 taps
+        alg_flops = npts * b * 2.0 * (2 * cp_k * (2 * R + 1))
+    else:
+        alg_flops = npts * b * (2.0 * nnz - 1)
+    if engine == "tensor-core":
+        pk, pk_src, pipe = (*tensor_peak(), "tensor")
+    elif esz == 8:
+        pk, pk_src, pipe = (*fp64_peak(), "alu")
+    else:
+        pk, pk_src, pipe = (*fp32_peak(sms), "alu")
+    t_bytes = alg_bytes / (hbm * 1e9)
+    t_flops = alg_flops / (pk * 1e12)
+    s = pass_ms * 1e-3
+    if t_bytes >= t_flops:
+        out = {"bound": "hbm", "achieved": alg_bytes / s / 1e9, "peak": hbm, "unit": "GB/s",
+               "peak_source": hbm_src}
+    else:
+        out = {"bound": pipe, "achieved": alg_flops / s / 1e12, "peak": pk, "unit": "TFLOP/s",
+               "peak_source": pk_src}
+    out["frac"] = max(t_bytes, t_flops) / s
+    out.update({"pass_ms": pass_ms, "alg_bytes_per_launch": alg_bytes,
+                "alg_flops_per_launch": alg_flops,
+                "hbm_view": {"achieved_gbs": alg_bytes / s / 1e9, "peak_gbs": hbm,
+                             "frac": t_bytes / s},
+                "flops_view": {"achieved_tflops": alg_flops / s / 1e12, "peak_tflops": pk,
+                               "frac": t_flops / s}})
+    return out
+
+
+def kernel_name(engine, grouped, ndim, b, cp_k):
+    if engine == "tensor-core":
+        return "k_tc2d_grouped" if grouped else "k_tc2d"
+    if ndim == 1:
+        return "k_sweep1d"
+    if ndim == 3:
+        return "k_sweep3d_tb" if b == 2 else "k_sweep3d"
+    return "k_sweep2d"
+
+
+def plan_facts(plan, ndim):
+    engine = "tensor-core" if plan.get("last_engine") == 1 else "cuda-core"
+    f = {"m": plan.get("last_m"), "b": plan.get("last_b"), "engine": engine}
+    if ndim == 2 and engine == "cuda-core":
+        f["tile_y"] = plan.get("last_tile_y")
+        f["counterparts"] = plan.get("last_cp")
+    if engine == "tensor-core":
+        f["tc_kernel"] = "grouped" if plan.get("last_tc_form") == 2 else "per-offset"
+    return f
+
+
+def measure_run(torch, binding, stream, flush, plan, x, y, T, m, npts, esz, sms, reps=3):
+    """Times whole runs of T steps and derives the duration of one pass.
+
+    The pass time is the difference of two event-timed runs on the same
+    stream: the full T, which makes n full passes, and T' with one full pass
+    and the same partial pass and plain remainder, so that
+    t(T) - t(T') = (n - 1) passes.  Both runs use the same fold request, so
+    an autotuned run keeps its tuned configuration.
+    """
+    ms_full = _time_runs(torch, stream, flush, lambda: plan.run(x, y, T, fold_m=m, stream=stream),
+                         reps=reps)
+    plan.sync(stream)
+    f = plan_facts(plan, x.dim())
+    mu, bu = max(1, f["m"]), max(1, f["b"])
+    n = full_passes(T, mu, bu)
+    pass_ms = ms_full
+    if n >= 2:
+        T2 = T - (n - 1) * mu * bu
+        ms2 = _time_runs(torch, stream, flush,
+                         lambda: plan.run(x, y, T2, fold_m=m, stream=stream), reps=reps)
+        pass_ms = max(1e-6, (ms_full - ms2) / (n - 1))
+    elif n == 1:
+        pass_ms = ms_full
+    # leave y holding the full run's output for the accuracy check
+    plan.run(x, y, T, fold_m=m, stream=stream)
+    plan.sync(stream)
+    R = mu * plan.radius
+    nnz = int(np.count_nonzero(plan.folded_coeffs(mu)))
+    cp_k = f.get("counterparts", 0)
+    roof = pass_roofline(npts, mu, bu, R, nnz, cp_k, esz, pass_ms, f["engine"], sms)
+    roof["kernel"] = kernel_name(f["engine"], f.get("tc_kernel") == "grouped", x.dim(), bu, cp_k)
+    return ms_full, f, roof
+
+
+def accuracy(torch, binding, stream, y, ref_host, dev):
+    ref_d = torch.from_numpy(np.ascontiguousarray(ref_host)).to(dev)
+    e, ez = binding.rel_l2(y, ref_d, stream=stream)
+    del ref_d
+    return {"rel_l2": e, "rel_l2_zero_mean": ez}
+
+
+# Variants: (name, workload, fold_m, options).  fold_m = 0 lets the library's
+# autotuner choose; the options pin what the name says.
+VARIANTS = [
+    ("star4096_T1000_plain_fp32", "star4096", 1, {"block_b": 1}, "f32"),
+    ("star4096_T1000_tc_bf16x3_m4", "star4096", 4, {"precision": 1}, "f32"),
+    ("heat1d_2pow20_T100_fp32", "heat1d", 1, {}, "f32"),
+    ("heat1d_2pow20_T100_fp64", "heat1d", 1, {}, "f64"),
+    ("heat1d_2pow20_T100_fp32_autotuned", "heat1d", 0, {}, "f32"),
+    ("heat1d_2pow20_T100_fp64_autotuned", "heat1d", 0, {}, "f64"),
+    ("box8192_T512_plain_fp32", "box8192", 1, {"block_b": 1}, "f32"),
+    ("box8192_T512_cuda_core_m2b2", "box8192", 2, {"block_b": 2}, "f32"),
+    ("box8192_T512_cuda_core_autotuned", "box8192", 0, {}, "f32"),
+    ("box8192_T512_tc_bf16x3_m4", "box8192", 4, {"precision": 1}, "f32"),
+    ("box8192_T512_tc_bf16x1_m4", "box8192", 4, {"precision": 2}, "f32"),
+    ("box8192_T512_tc_bf16x3_m6", "box8192", 6, {"precision": 1}, "f32"),
+    ("box8192_T512_tc_bf16x3_m8", "box8192", 8, {"precision": 1}, "f32"),
+    ("box8192_T512_tc_bf16x1_m8", "box8192", 8, {"precision": 2}, "f32"),
+    ("box8192_T512_tc_bf16x3_m8_per_offset", "box8192", 8, {"precision": 1, "tc_form": 1}, "f32"),
+    ("sepbox8192_T512_autotuned", "sepbox8192", 0, {}, "f32"),
+    ("sepbox8192_T512_counterparts_m8b1", "sepbox8192", 8, {"block_b": 1}, "f32"),
+    ("sepbox8192_T512_direct_autotuned", "sepbox8192", 0, {"counterparts": 2}, "f32"),
+    ("star512cube_T200_plain", "star512cube", 1, {"block_b": 1}, "f32"),
+    ("star512cube_T200_plain_fused2", "star512cube", 1, {"block_b": 2}, "f32"),
+    ("star512cube_T200_m2", "star512cube", 2, {"block_b": 1}, "f32"),
+    ("box256cube_T200_plain", "box256cube", 1, {"block_b": 1}, "f32"),
+    ("box256cube_T200_m2", "box256cube", 2, {"block_b": 1}, "f32"),
+]
+
+
+def measure_variants(torch, binding, dev, stream, flush, sampler, leg, sms, only=None):
+    """Every other configuration, each timed, rooflined, clocked and checked."""
+    out = {}
+    for name, wname, m, opts, dtype in VARIANTS:
+        if only and name not in only:
+            continue
+        w = CONFIGS[wname]
+        shape, T = w["shape"], w["T"]
+        c = config_coeffs(w["seed"], len(shape), w["kind"])
         npdt = np.float64 if dtype == "f64" else np.float32
-        x = torch.from_numpy(synth.grid(seed, shape, npdt)).to(dev)
+        x_host = synth.grid(w["seed"], shape, npdt)
+        x = torch.from_numpy(x_host).to(dev)
         y = torch.empty_like(x)
         plan = binding.Plan(shape, c, dtype=dtype)
         for k, v in opts.items():
             plan.set_option(k, v)
-        ms = _time_runs(torch, stream, flush, lambda: plan.run(x, y, T, fold_m=m, stream=stream))
-        plan.sync(stream)
-        out[name] = {"gstencil_s": float(np.prod(shape)) * T / (ms * 1e-3) / 1e9, "ms": ms,
-                     "m": plan.get("last_m"), "b": plan.get("last_b"),
-                     "tile_y": plan.get("last_tile_y") if ndim == 2 else None,
-                     "engine": "tensor-core" if plan.get("last_engine") else "cuda-core"}
-        if plan.get("last_engine"):
-            out[name]["tc_kernel"] = "grouped" if plan.get("last_tc_form") == 2 else "per-offset"
-        elif ndim == 2:
-            out[name]["counterparts"] = plan.get("last_cp")
+        t0 = time.time()
+        ms, facts, roof = measure_run(torch, binding, stream, flush, plan, x, y, T, m,
+                                      float(np.prod(shape)), 8 if dtype == "f64" else 4, sms)
+        t1 = time.time()
+        rec = {"gstencil_s": float(np.prod(shape)) * T / (ms * 1e-3) / 1e9, "ms": ms}
+        rec.update(facts)
+        rec["roofline"] = roof
+        rec["clocks"] = sampler.summary(t0, t1)
+        if leg is not None:
+            ref = leg.reference((wname, dtype), x_host, c, T)
+            rec.update(accuracy(torch, binding, stream, y, ref, dev))
+        out[name] = rec
         plan.close()
         del x, y
         torch.cuda.empty_cache()
+    if not only or "batched256_T10to500" in only:
+        out["batched256_T10to500"] = measure_batched(torch, binding, dev, stream, flush, sampler,
+                                                     leg, sms)
+    return out
 
-    s1 = synth.BASE_SEED + 1
-    single("heat1d_2pow20_T100_fp32", (1 << 20,), "heat", s1, 100, 1, ndim=1)
-    single("heat1d_2pow20_T100_fp64", (1 << 20,), "heat", s1, 100, 1, ndim=1, dtype="f64")
-    single("heat1d_2pow20_T100_fp32_autotuned", (1 << 20,), "heat", s1, 100, 0, ndim=1)
-    single("heat1d_2pow20_T100_fp64_autotuned", (1 << 20,), "heat", s1, 100, 0, ndim=1,
-           dtype="f64")
-    s2 = synth.BASE_SEED + 2
-    single("star4096_T1000_plain_fp32", (4096, 4096), "star", s2, 1000, 1, block_b=1)
-    single("star4096_T1000_tc_bf16x3_m4", (4096, 4096), "star", s2, 1000, 4, precision=1)
-    s3 = synth.BASE_SEED + 3
-    single("box8192_T512_plain_fp32", (8192, 8192), "box", s3, 512, 1, block_b=1)
-    single("box8192_T512_cuda_core_m2b2", (8192, 8192), "box", s3, 512, 2, block_b=2)
-    single("box8192_T512_cuda_core_autotuned", (8192, 8192), "box", s3, 512, 0)
-    single("box8192_T512_tc_bf16x3_m4", (8192, 8192), "box", s3, 512, 4, precision=1)
-    single("box8192_T512_tc_bf16x3_m6", (8192, 8192), "box", s3, 512, 6, precision=1)
-    single("box8192_T512_tc_bf16x3_m8", (8192, 8192), "box", s3, 512, 8, precision=1)
-    single("box8192_T512_tc_bf16x3_m8_per_offset", (8192, 8192), "box", s3, 512, 8, precision=1,
-           tc_form=1)
-    # a separable box (the paper's Gaussian-blur family): counterpart form
-    # (Section 3.3) against the direct form, same grid and steps
-    s7 = synth.BASE_SEED + 7
-    single("sepbox8192_T512_autotuned", (8192, 8192), "sep", s7, 512, 0)
-    single("sepbox8192_T512_counterparts_m8b1", (8192, 8192), "sep", s7, 512, 8, block_b=1)
-    single("sepbox8192_T512_direct_autotuned", (8192, 8192), "sep", s7, 512, 0, counterparts=2)
-    single("star512cube_T200_plain", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1, ndim=3)
-    single("star512cube_T200_plain_fused2", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 1,
-           ndim=3, block_b=2)
-    single("star512cube_T200_m2", (512, 512, 512), "star", synth.BASE_SEED + 4, 200, 2, ndim=3)
-    single("box256cube_T200_plain", (256, 256, 256), "box", synth.BASE_SEED + 5, 200, 1, ndim=3)
-    single("box256cube_T200_m2", (256, 256, 256), "box", synth.BASE_SEED + 5, 200, 2, ndim=3)
-    # 256 independent grids in one persistent launch
+
+def measure_batched(torch, binding, dev, stream, flush, sampler, leg, sms):
+    """256 independent grids in one persistent launch."""
     grids = synth.batched_workload(synth.BASE_SEED + 6)
-    plans, xs, ys, Ts = [], [], [], []
+    plans, xs, ys, Ts, host = [], [], [], [], []
     for g in grids:
         c = synth.dyadic_coeffs(g["coeff_seed"], 2, 1, g["kind"])
         plans.append(binding.Plan(g["shape"], c))
-        xs.append(torch.from_numpy(synth.grid(g["value_seed"], g["shape"], np.float32)).to(dev))
+        xh = synth.grid(g["value_seed"], g["shape"], np.float32)
+        host.append((xh, c))
+        xs.append(torch.from_numpy(xh).to(dev))
         ys.append(torch.empty_like(xs[-1]))
         Ts.append(g["T"])
+    t0 = time.time()
     ms = _time_runs(torch, stream, flush,
                     lambda: binding.run_batched(plans, xs, ys, Ts, stream=stream))
+    t1 = time.time()
     plans[0].sync(stream)
     upd = sum(float(np.prod(g["shape"])) * g["T"] for g in grids)
-    out["batched256_T10to500"] = {"gstencil_s": upd / (ms * 1e-3) / 1e9, "ms": ms,
-                                  "grids": len(grids), "updates": upd}
+    # roofline of the one launch: the algorithmic bytes and flops of every
+    # grid's passes, summed; the launch is bound by the larger total
+    hbm, hbm_src = hbm_peak()
+    pk, pk_src = fp32_peak(sms)
+    tot_bytes = tot_flops = 0.0
+    ms_used = {}
+    for p, g, T in zip(plans, grids, Ts):
+        m, b = max(1, p.get("last_m")), max(1, p.get("last_b"))
+        ms_used[(m, b)] = ms_used.get((m, b), 0) + 1
+        npts = float(np.prod(g["shape"]))
+        q, rem = divmod(T, m)
+        nnz_m = int(np.count_nonzero(p.folded_coeffs(m)))
+        nnz_1 = int(np.count_nonzero(p.folded_coeffs(1)))
+        npass = -(-q // b) + (1 if rem else 0)
+        tot_bytes += npass * 8.0 * npts
+        tot_flops += npts * (q * (2.0 * nnz_m - 1) + rem * (2.0 * nnz_1 - 1))
+    s = ms * 1e-3
+    tb, tf = tot_bytes / (hbm * 1e9), tot_flops / (pk * 1e12)
+    roof = ({"bound": "hbm", "achieved": tot_bytes / s / 1e9, "peak": hbm, "unit": "GB/s",
+             "peak_source": hbm_src} if tb >= tf else
+            {"bound": "alu", "achieved": tot_flops / s / 1e12, "peak": pk, "unit": "TFLOP/s",
+             "peak_source": pk_src})
+    roof.update({"frac": max(tb, tf) / s, "kernel": "k_batched", "launch_ms": ms,
+                 "alg_bytes_per_launch": tot_bytes, "alg_flops_per_launch": tot_flops})
+    rec = {"gstencil_s": upd / s / 1e9, "ms": ms, "grids": len(grids), "updates": upd,
+           "m_b_counts": {"m%d_b%d" % k: v for k, v in sorted(ms_used.items())},
+           "roofline": roof, "clocks": sampler.summary(t0, t1)}
+    if leg is not None:
+        worst = worst_zm = 0.0
+        for (xh, c), y, T in zip(host, ys, Ts):
+            acc = accuracy(torch, binding, stream, y, leg.expected(xh, c, T), dev)
+            worst = max(worst, acc["rel_l2"])
+            worst_zm = max(worst_zm, acc["rel_l2_zero_mean"])
+        rec["rel_l2_max_over_grids"] = worst
+        rec["rel_l2_zero_mean_max_over_grids"] = worst_zm
     for p in plans:
         p.close()
     del xs, ys
     torch.cuda.empty_cache()
-    return out
+    return rec
 
 
 def max_over_ranks(torch, value: float, pg, device) -> float:
@@ -340,27 +558,31 @@ def run_gpu(args):
         dist.init_process_group("nccl")
         pg = dist
     build.build()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
-    c = config_coeffs(SEED, len(SHAPE), KIND)
-    x_host = synth.grid(SEED, SHAPE, np.float32)
+    w = CONFIGS[args.config]
+    SHAPE, T_STEPS = w["shape"], w["T"]
+    dtype = "f32"
+    c = config_coeffs(w["seed"], len(SHAPE), w["kind"])
+    x_host = synth.grid(w["seed"], SHAPE, np.float32)
     npts = float(np.prod(SHAPE))
     stream = torch.cuda.current_stream(dev)
 
-    def make_plan(m, b, precision=0):
-        plan = binding.Plan(SHAPE, c)
-        plan.set_option("block_b", b).set_option("precision", precision)
+    plan = binding.Plan(SHAPE, c, dtype)
+    plan.set_option("block_b", args.block_b).set_option("precision", args.precision)
+    if len(SHAPE) == 2:
         plan.set_option("tc_form", args.tc_form)
-        if args.tile_y:
-            plan.set_option("tile_y", args.tile_y)
-        return plan
+    if args.tile_y:
+        plan.set_option("tile_y", args.tile_y)
+    m_req = args.fold_m
 
     xd = torch.from_numpy(x_host).to(dev)
     yd = torch.empty_like(xd)
     flush = torch.empty((64 if args.ncu else L2_FLUSH_BYTES) // 4, dtype=torch.float32, device=dev)
 
-    def timed_steps(plan, m, T, k, w):
-        for _ in range(w):
-            plan.run(xd, yd, T, fold_m=m, stream=stream)
+    def timed_steps(T, k, wu):
+        for _ in range(wu):
+            plan.run(xd, yd, T, fold_m=m_req, stream=stream)
         plan.sync(stream)
         times = []
         launches0 = plan.get("launches")
@@ -369,86 +591,73 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            plan.run(xd, yd, T, fold_m=m, stream=stream)
+            plan.run(xd, yd, T, fold_m=m_req, stream=stream)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         plan.sync(stream)
         return times, plan.get("launches") - launches0
 
-    m_best, b_best = args.fold_m, args.block_b
-    plan = make_plan(m_best, b_best, args.precision)
+    sampler = ClockSampler(local)
+    sampler.start()
 
     # --- main timed region: whole job, inputs resident on the device
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    times, launches = timed_steps(plan, m_best, T_STEPS, args.steps, args.warmup)
+    t_a = time.time()
+    times, launches = timed_steps(T_STEPS, args.steps, args.warmup)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
+    t_b = time.time()
     if pg:
         pg.barrier()
     ms_step = statistics.mean(times)
     ms_total = max_over_ranks(torch, sum(times), pg, dev)
     value = whole_job_rate(ws, npts, T_STEPS, args.steps, ms_total)
-    used_m, used_b = plan.get("last_m"), plan.get("last_b")
-    engine = "tensor-core" if plan.get("last_engine") == 1 else "cuda-core"
-    grouped = engine == "tensor-core" and plan.get("last_tc_form") == 2
+    facts = plan_facts(plan, len(SHAPE))
     if args.ncu:
         # profiling run: only the timed loop above, nothing else
+        sampler.stop()
         if rank == 0:
-            print(json.dumps({"ncu_run": True, "value": value, "fold_m": used_m, "block_b": used_b}))
+            print(json.dumps({"ncu_run": True, "value": value, "fold_m": facts["m"],
+                              "block_b": facts["b"]}))
         plan.close()
         return
+    clocks = sampler.summary(t_a, t_b)
+    y_timed = yd.clone()  # the output of the timed runs, checked below
 
-    # --- dominant kernel: average duration of one folded pass, by difference of
-    # two CUDA-event-timed runs (T = one pass vs the full T) on the same stream
-    T_one = used_m * used_b
-    t_one, _ = timed_steps(plan, m_best, T_one, 5, 2)
-    n_pass = T_STEPS // (used_m * used_b)
-    rem_steps = T_STEPS - n_pass * used_m * used_b
-    pass_ms = (statistics.median(times) - statistics.median(t_one)) / max(1, n_pass - 1)
-    if rem_steps:
-        pass_ms = statistics.median(times) / max(1, n_pass)
-    peak, peak_kind = load_peaks()
-    alg_bytes = 2 * 4 * npts  # one read and one write of the grid per pass
-    achieved = alg_bytes / (pass_ms * 1e-3) / 1e9
-    # algorithmic flops of one pass: b sweeps of the folded stencil, each
-    # 2*nnz(c^(m)) - 1 flops per point (its own multiply-adds, not the
-    # redundant rim, the Toeplitz zeros or the BF16 split)
-    nnz = int(np.count_nonzero(plan.folded_coeffs(used_m)))
-    alg_flops = npts * used_b * (2 * nnz - 1)
-    used_cp = plan.get("last_cp") if (engine == "cuda-core" and len(SHAPE) == 2) else 0
-    if used_cp:
-        # counterpart form: K vertical and K horizontal folds of 2mr+1 taps,
-        # the algorithm's own multiply-adds in that form
-        alg_flops = npts * used_b * 2 * (2 * used_cp * (2 * used_m + 1))
-    tflops = alg_flops / (pass_ms * 1e-3) / 1e12
-    if engine == "tensor-core":
-        bound, r_ach, r_peak, r_unit = "tensor", tflops, load_tensor_peak(), "TFLOP/s"
-    elif used_m == 1 and used_b == 1:
-        bound, r_ach, r_peak, r_unit = "hbm", achieved, peak, "GB/s"
-    else:
-        bound, r_ach, r_peak, r_unit = "alu", tflops, fp32_peak_tflops(), "TFLOP/s"
-    traffic = None
+    # --- dominant kernel: one pass, by difference of two event-timed runs
+    mu, bu = max(1, facts["m"]), max(1, facts["b"])
+    n = full_passes(T_STEPS, mu, bu)
+    pass_ms = statistics.median(times) / max(1, n)
+    if n >= 2:
+        T2 = T_STEPS - (n - 1) * mu * bu
+        t_two, _ = timed_steps(T2, 5, 2)
+        pass_ms = max(1e-6, (statistics.median(times) - statistics.median(t_two)) / (n - 1))
+    cp_k = facts.get("counterparts", 0)
+    nnz = int(np.count_nonzero(plan.folded_coeffs(mu)))
+    roof = pass_roofline(npts, mu, bu, mu * plan.radius, nnz, cp_k, 4, pass_ms,
+                         facts["engine"], sms)
+    roof["kernel"] = kernel_name(facts["engine"], facts.get("tc_kernel") == "grouped",
+                                 len(SHAPE), bu, cp_k)
+    roof["traffic"] = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         try:
             with open(tfile) as f:
                 tr = json.load(f)
-            key = "%s_%s_m%d_b%d" % (args.config, engine + ("-grouped" if grouped else ""),
-                                     used_m, used_b)
-            traffic = tr.get(key)
+            key = "%s_%s_m%d_b%d" % (args.config, facts["engine"] +
+                                     ("-grouped" if facts.get("tc_kernel") == "grouped" else ""),
+                                     mu, bu)
+            roof["traffic"] = tr.get(key)
         except Exception:
-            traffic = None
+            pass
 
     # --- end to end through the C ABI with host buffers (copies inside the timed region)
     xh = torch.from_numpy(x_host).pin_memory().numpy()
     yh = torch.empty(SHAPE, dtype=torch.float32).pin_memory().numpy()
     for _ in range(max(1, args.warmup)):
-        plan.run(xh, yh, T_STEPS, fold_m=m_best, stream=stream)
+        plan.run(xh, yh, T_STEPS, fold_m=m_req, stream=stream)
     e_times = []
     for _ in range(args.steps):
         flush.zero_()
@@ -456,55 +665,57 @@ def run_gpu(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        plan.run(xh, yh, T_STEPS, fold_m=m_best, stream=stream)  # returns after the D2H copy
+        plan.run(xh, yh, T_STEPS, fold_m=m_req, stream=stream)  # returns after the D2H copy
         e1.record(stream)
         e1.synchronize()
         e_times.append(e0.elapsed_time(e1))
     e2e_total = max_over_ranks(torch, sum(e_times), pg, dev)
     e2e = whole_job_rate(ws, npts, T_STEPS, args.steps, e2e_total)
 
-    # --- the other configurations of the workload family, each timed the same
-    # way (events around whole runs, L2 flushed between runs); reported beside
-    # the headline, not folded into it
-    variants = {}
-    if not args.no_variants:
-        variants = measure_variants(torch, binding, dev, stream, flush, args)
+    # --- the CPU-baseline leg (rank 0): the oracle timed on the host cores,
+    # and the oracle's results the timed outputs are checked against
+    leg = None
     cpu = None
+    acc = None
     if rank == 0 and not args.no_cpu_baseline:
-        Ts = calibrate_oracle_steps(args.cpu_seconds)
-        v, dt, cores = oracle_sample(Ts)
+        leg = OracleLeg()
+        Ts = leg.calibrate(args.config, args.cpu_seconds)
+        v, dt, cores = leg.sample(args.config, Ts)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "full %s grid, %d steps (%.1f s), FP64 C oracle" % (
                    "x".join(map(str, SHAPE)), Ts, dt)}
+        acc = accuracy(torch, binding, stream, y_timed,
+                       leg.reference((args.config, dtype), x_host, c, T_STEPS), dev)
+
+    # --- the other configurations of the workload family, each timed the same
+    # way; reported beside the headline, not folded into it
+    variants = {}
+    if not args.no_variants:
+        variants = measure_variants(torch, binding, dev, stream, flush, sampler, leg, sms)
+    sampler.stop()
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": list(SHAPE), "T": T_STEPS,
-                       "fold_m": used_m, "block_b": used_b, "tile_y": plan.get("last_tile_y"),
-                       "engine": engine, "counterparts": used_cp,
-                       "precision": ["fp32", "bf16x3", "bf16x1"][args.precision],
-                       "l2": "flushed between timed steps (512 MB write)",
-                       "parallelism": "replicas" if ws > 1 else "single"},
-            "roofline": {"bound": bound, "achieved": r_ach, "peak": r_peak, "unit": r_unit,
-                         "frac": r_ach / r_peak, "traffic": traffic,
-                         "peak_source": peak_kind if bound == "hbm" else
-                         ("MEASURED_PEAKS.json bf16_tflops_sustained" if bound == "tensor" else
-                          "152 SMs x 128 FP32 FMA/clk x 2 flop x measured max SM clock"),
-                         "kernel": ("k_tc2d_grouped" if grouped else "k_tc2d")
-                                   if engine == "tensor-core" else
-                                   ("k_sweep3d" if len(SHAPE) == 3 else "k_sweep2d"),
-                         "pass_ms": pass_ms, "alg_bytes_per_launch": alg_bytes,
-                         "alg_flops_per_launch": alg_flops,
-                         "hbm_view": {"achieved_gbs": achieved, "peak_gbs": peak,
-                                      "frac": achieved / peak}},
+            "config": workload_config(args.config),
+            "run": {"fold_m": facts["m"], "block_b": facts["b"],
+                    "tile_y": facts.get("tile_y"), "engine": facts["engine"],
+                    "counterparts": facts.get("counterparts", 0),
+                    "tc_kernel": facts.get("tc_kernel"),
+                    "precision": ["fp32", "bf16x3", "bf16x1"][args.precision],
+                    "chosen_by": "autotuner" if args.fold_m == 0 else "command line",
+                    "parallelism": "replicas" if ws > 1 else "single"},
+            "l2": "flushed between timed steps (512 MB write)",
+            "accuracy": acc,
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(npts * 4),
                     "d2h_bytes_per_step": int(npts * 4)},
             "gpu_launches": int(launches),
             "clocks": clocks,
+            "sm_count": sms,
             "variants": variants,
         }
         print(json.dumps(line), flush=True)
@@ -530,12 +741,12 @@ def main():
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
                     help="0 = FP32 CUDA cores, 1 = BF16x3 tensor cores, 2 = BF16x1")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the CPU-baseline leg (and with it the accuracy checks)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: timed loop only, no L2 flush buffer, no extra legs")
     args = ap.parse_args()
-    select_config(args.config)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -228,8 +228,7 @@ stencil_status_t stencil_fold_counterparts(int W, const double *folded, int max_
 /*
  * T plain steps of a 1D periodic stencil without allocating any memory.
  * The paper has no counterpart of this call: it serves callers that cannot
- * call cudaMalloc -- code running while a CUDA graph is captured in a mode
- * that forbids allocation, code inside a framework whose allocator owns all
+ * call cudaMalloc -- code inside a framework whose own allocator owns all
  * device memory, and deployments that must not touch the allocator after
  * start-up.  stencil_run needs a plan, which allocates; this call does not.
  *   in, out   n device elements of `dtype` (F32 or F64); in == out allowed.

@@ -43,6 +43,11 @@ struct Padded {
     size_t elems = 0;
 };
 
+// Raises a kernel's dynamic shared-memory limit to the current device's
+// opt-in maximum, once per (kernel, device); the attribute is per device, so
+// a library used on several GPUs sets it on each.
+cudaError_t smem_optin(const void *kernel);
+
 // ---- 2D CUDA-core sweep (plain, folded, temporally blocked) ---------------
 constexpr int kTileX2D = 128;   // output columns per CTA tile
 constexpr int kThreads2D = 256;

@@ -322,13 +322,8 @@ size_t batched_smem_bytes(int buf_floats, int nwork, int nstage)
 
 cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s)
 {
-    static cudaError_t once = [] {
-        int dev = 0, maxs = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        return cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-    }();
-    if (once != cudaSuccess) return once;
+    const cudaError_t e = smem_optin((const void *)k_batched);
+    if (e != cudaSuccess) return e;
     k_batched<<<grid, kThreadsBatched, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -336,7 +331,7 @@ cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream
 int batched_ctas_per_sm(size_t smem)
 {
     int n = 0;
-    cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem_optin((const void *)k_batched) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched, kThreadsBatched, smem) != cudaSuccess)
         return 0;
     return n;

@@ -63,14 +63,8 @@ __global__ void __launch_bounds__(NT1) k_sweep1d(const __grid_constant__ Sweep1D
 template <typename T, int R>
 cudaError_t launch_t(const Sweep1DArgs &a, cudaStream_t s)
 {
-    static cudaError_t once = [] {
-        int dev = 0, maxs = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        return cudaFuncSetAttribute(k_sweep1d<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    maxs);
-    }();
-    if (once != cudaSuccess) return once;
+    const cudaError_t e = smem_optin((const void *)k_sweep1d<T, R>);
+    if (e != cudaSuccess) return e;
     const int H = a.b * R;
     const size_t smem = 2 * sizeof(T) * (size_t)(a.tile + 2 * H);
     const long long nt = (a.n + a.tile - 1) / a.tile;

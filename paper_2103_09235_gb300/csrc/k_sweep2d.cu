@@ -130,19 +130,12 @@ __global__ void __launch_bounds__(threads2d<RB, M, PAT>(), min_blocks<RB, M>())
     }
 }
 
-// Opt every instantiation into the largest dynamic shared memory once, so
-// launches need no attribute call.
+// Opt every instantiation into the largest dynamic shared memory, once per
+// device (the attribute is per device).
 template <int RB, int M, int PAT>
 cudaError_t prepare_t()
 {
-    static cudaError_t once = [] {
-        int dev = 0, maxs = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        return cudaFuncSetAttribute(k_sweep2d<RB, M, PAT>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-    }();
-    return once;
+    return smem_optin((const void *)k_sweep2d<RB, M, PAT>);
 }
 
 // Threads per CTA of a launch: the instance's own count, or 256 when asked

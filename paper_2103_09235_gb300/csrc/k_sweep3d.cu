@@ -165,14 +165,7 @@ __global__ void __launch_bounds__(NT3)
 template <int RB, int M, int PAT>
 cudaError_t prepare3()
 {
-    static cudaError_t once = [] {
-        int dev = 0, maxs = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        return cudaFuncSetAttribute(k_sweep3d<RB, M, PAT>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-    }();
-    return once;
+    return smem_optin((const void *)k_sweep3d<RB, M, PAT>);
 }
 
 template <int RB, int M, int PAT>

@@ -217,14 +217,7 @@ namespace {
 template <int RB, int M, int PAT>
 cudaError_t prepare_tb()
 {
-    static cudaError_t once = [] {
-        int dev = 0, maxs = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        return cudaFuncSetAttribute(k_sweep3d_tb<RB, M, PAT>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-    }();
-    return once;
+    return smem_optin((const void *)k_sweep3d_tb<RB, M, PAT>);
 }
 
 template <int RB, int M, int PAT>

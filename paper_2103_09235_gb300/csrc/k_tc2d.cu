@@ -43,31 +43,13 @@ constexpr int PANEL_BYTES = kTcPanelElems * 2;  // 6144
 constexpr int LBO_B = 64 * 16;                  // K-chunk stride of a panel (64 rows x 16 B)
 constexpr uint32_t TMEM_COLS = 128;             // two 64-column accumulators
 
-// ---- tcgen05 wrappers ------------------------------------------------------
-
-
-
-
-
-
-
-
-// ---- bounded waits shared by all roles --------------------------------------
-
+// Barriers, tensor-memory address and abort flag shared by the warp roles.
 struct Ctl {
     uint64_t stage_full[2], stage_empty[2], a_full[2], a_empty[2], d_full[2], d_empty[2];
     uint32_t tmem_base;
     int abort;
     int epi_ok[2][4];  // per-iteration votes of the four epilogue warps
 };
-
-
-
-}  // namespace
-}  // namespace sg
-
-namespace sg {
-namespace {
 
 // Shared-memory layout (bytes from the 1024-aligned base):
 //   [0, 1024)           control block (barriers, tensor-memory address, abort flag)
@@ -410,13 +392,8 @@ double tc2d_build_panels(const double *cm, int R, uint16_t *out)
 cudaError_t launch_tc2d(const CUtensorMap &map, const CUtensorMap &dmap, const TC2DArgs &a,
                         int grid, size_t smem, cudaStream_t s)
 {
-    static cudaError_t once = [] {
-        int dev = 0, maxs = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        return cudaFuncSetAttribute(k_tc2d, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-    }();
-    if (once != cudaSuccess) return once;
+    const cudaError_t e = smem_optin((const void *)k_tc2d);
+    if (e != cudaSuccess) return e;
     k_tc2d<<<grid, NT, smem, s>>>(map, dmap, a);
     return cudaGetLastError();
 }

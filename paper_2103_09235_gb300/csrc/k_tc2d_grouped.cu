@@ -488,13 +488,8 @@ double tc2dg_build_panels(const double *cm, int R, uint16_t *out)
 cudaError_t launch_tc2dg(const CUtensorMap &map, const TC2DArgs &a,
                         int grid, size_t smem, cudaStream_t s)
 {
-    static cudaError_t once = [] {
-        int dev = 0, maxs = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        return cudaFuncSetAttribute(k_tc2d_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
-    }();
-    if (once != cudaSuccess) return once;
+    const cudaError_t e = smem_optin((const void *)k_tc2d_grouped);
+    if (e != cudaSuccess) return e;
     k_tc2d_grouped<<<grid, NT, smem, s>>>(map, a);
     return cudaGetLastError();
 }

@@ -1,9 +1,8 @@
 // A 1D stencil run that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured in a mode that forbids allocation, code embedded in a
-// framework whose own allocator owns all device memory, and real-time or
-// pre-allocated deployments that must not touch the allocator after start-up.
+// Some callers cannot call cudaMalloc: code embedded in a framework whose own
+// allocator owns all device memory, and real-time or pre-allocated
+// deployments that must not touch the allocator after start-up.
 // stencil_run needs a plan, and a plan allocates its scratch on first use, so
 // such callers get this entry point instead.  Its intermediate grid lives in a
 // file-scope device array of fixed size; the caller passes only the input and

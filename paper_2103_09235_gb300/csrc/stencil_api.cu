@@ -7,7 +7,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <set>
+#include <utility>
 #include <vector>
 
 #include "plan.h"
@@ -28,6 +30,23 @@ stencil_status_t cuda_fail(cudaError_t e, const char *what)
 {
     set_error("%s: %s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? STENCIL_ERR_OOM : STENCIL_ERR_CUDA;
+}
+
+cudaError_t smem_optin(const void *kernel)
+{
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return cudaSuccess;
+    int maxs = 0;
+    e = cudaDeviceGetAttribute(&maxs, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+    if (e == cudaSuccess) done.insert({kernel, dev});
+    return e;
 }
 
 static int taps_count(int ndim, int r)
