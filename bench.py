@@ -307,15 +307,23 @@ def full_passes(T: int, m: int, b: int) -> int:
     return (T // m) // b
 
 
+def sweep_flops(npts, R, nnz, cp_k):
+    """Algorithmic flops of one sweep: the folded stencil's multiply-adds, or
+    in counterpart form K vertical and K horizontal folds of 2R+1 taps."""
+    if cp_k:
+        return npts * 2.0 * (2 * cp_k * (2 * R + 1))
+    return npts * (2.0 * nnz - 1)
+
+
 def pass_roofline(npts, m, b, R, nnz, cp_k, esz, pass_ms, engine, sms):
     """Roofline of one pass of b fused sweeps of the m-folded stencil."""
+    return roofline_of(2.0 * esz * npts, b * sweep_flops(npts, R, nnz, cp_k), pass_ms, esz,
+                       engine, sms)
+
+
+def roofline_of(alg_bytes, alg_flops, pass_ms, esz, engine, sms):
+    """t_roof = max(bytes / HBM, flops / pipe peak) against a measured time."""
     hbm, hbm_src = hbm_peak()
-    alg_bytes = 2.0 * esz * npts
-    if cp_k:
-        # counterpart form: K vertical and K horizontal folds of 2R+1 taps
-        alg_flops = npts * b * 2.0 * (2 * cp_k * (2 * R + 1))
-    else:
-        alg_flops = npts * b * (2.0 * nnz - 1)
     if engine == "tensor-core":
         pk, pk_src, pipe = (*tensor_peak(), "tensor")
     elif esz == 8:
@@ -377,21 +385,27 @@ def measure_run(torch, binding, stream, flush, plan, x, y, T, m, npts, esz, sms,
     f = plan_facts(plan, x.dim())
     mu, bu = max(1, f["m"]), max(1, f["b"])
     n = full_passes(T, mu, bu)
-    pass_ms = ms_full
+    R = mu * plan.radius
+    nnz = int(np.count_nonzero(plan.folded_coeffs(mu)))
+    cp_k = f.get("counterparts", 0)
     if n >= 2:
         T2 = T - (n - 1) * mu * bu
         ms2 = _time_runs(torch, stream, flush,
                          lambda: plan.run(x, y, T2, fold_m=m, stream=stream), reps=reps)
         pass_ms = max(1e-6, (ms_full - ms2) / (n - 1))
-    elif n == 1:
-        pass_ms = ms_full
+        roof = pass_roofline(npts, mu, bu, R, nnz, cp_k, esz, pass_ms, f["engine"], sms)
+    else:
+        # fewer than two full passes: the whole run is the unit (its partial
+        # folded pass and plain remainder pass, import and export included)
+        q, rem = divmod(T, mu)
+        npass = -(-q // bu) + (1 if rem else 0)
+        nnz1 = int(np.count_nonzero(plan.folded_coeffs(1)))
+        flops = q * sweep_flops(npts, R, nnz, cp_k) + rem * (2.0 * nnz1 - 1) * npts
+        roof = roofline_of(npass * 2.0 * esz * npts, flops, ms_full, esz, f["engine"], sms)
+        roof["unit_of_work"] = "whole run (%d passes)" % npass
     # leave y holding the full run's output for the accuracy check
     plan.run(x, y, T, fold_m=m, stream=stream)
     plan.sync(stream)
-    R = mu * plan.radius
-    nnz = int(np.count_nonzero(plan.folded_coeffs(mu)))
-    cp_k = f.get("counterparts", 0)
-    roof = pass_roofline(npts, mu, bu, R, nnz, cp_k, esz, pass_ms, f["engine"], sms)
     roof["kernel"] = kernel_name(f["engine"], f.get("tc_kernel") == "grouped", x.dim(), bu, cp_k)
     return ms_full, f, roof
 

@@ -78,12 +78,39 @@ typedef enum {
 stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t *shape,
                               int radius, const double *coeffs, stencil_dtype_t dtype);
 
+/* Flags of stencil_plan_ex. */
+typedef enum {
+    STENCIL_FLAG_NONPERIODIC = 1u   /* a non-periodic boundary: not supported, since
+                                       folding is exact only on periodic grids      */
+} stencil_flags_t;
+
+/*
+ * stencil_plan for grids whose rows (and planes) are not densely packed,
+ * e.g. a sub-array of a larger allocation or rows padded for alignment (the
+ * same problem, Section 1; the layout is the caller's).
+ *   pitch_elems  NULL = dense; else ndim-1 strides in elements, C order:
+ *                2D {row stride}, 3D {plane stride, row stride}, with
+ *                row stride >= shape[ndim-1] and plane stride >= row stride *
+ *                shape[1].  Ignored for 1D.  Every in/out grid later given to
+ *                stencil_run / stencil_run_batched with this plan uses these
+ *                strides; the points between rows and planes are never read
+ *                or written.  Host grids use them too.
+ *   flags        0 (periodic, the only boundary this library implements) or
+ *                STENCIL_FLAG_NONPERIODIC, which returns UNSUPPORTED.
+ * Other arguments, ownership and errors as for stencil_plan; additionally
+ * INVALID_ARG for pitches below the dense strides or unknown flag bits.
+ */
+stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64_t *shape,
+                                 int radius, const double *coeffs, stencil_dtype_t dtype,
+                                 const int64_t *pitch_elems, unsigned flags);
+
 /*
  * Sets a tuning option (all optional).  Keys:
  *   "precision"     stencil_precision_t; BF16 modes run folded 2D sweeps (m > 1,
  *                   m*r <= 8) on the tensor cores; plain steps stay on CUDA cores.
  *   "block_b"       temporal-blocking depth: folded sweeps per memory round trip
- *                   (0 = automatic).
+ *                   (0 = automatic; 1..64, and 2D/3D passes take as many as their
+ *                   halo allows).
  *   "tile_y"        rows per CTA tile of the 2D CUDA-core sweep (0 = automatic: 32
  *                   for single sweeps, 64 for blocked ones, 160 in counterpart form,
  *                   lowered until the tile fits in shared memory).
@@ -119,10 +146,16 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
  *   "graph"         1 = capture each distinct run (pointers, T, m, options) once into
  *                   a CUDA graph and replay it (default 1); 0 = launch kernel by kernel.
  *                   A run on a stream that is itself being captured is never graphed.
- *   "fault_withhold_copy"  test hook: 1 = the 2D CUDA-core sweep and the single-sweep
- *                   3D kernel never issue a CTA's first copy, so their bounded waits
- *                   run out and stencil_sync
- *                   reports STENCIL_ERR_TIMEOUT (no GPU fault; the context stays usable).
+ *   "fault_withhold_copy"  test hook: 1 = the 2D CUDA-core sweep and both 3D kernels
+ *                   never issue a CTA's first copy, so their bounded waits run out
+ *                   and stencil_sync reports STENCIL_ERR_TIMEOUT (no GPU fault; the
+ *                   context stays usable).
+ *   "fault_withhold_dep"   test hook: 1 = in a batched run led by this plan every
+ *                   dependency on a previous pass counts as unmet, so the work
+ *                   queue's bounded dependency wait runs out (TIMEOUT, as above).
+ *   "fault_withhold_mma"   test hook: 1 = the tensor-core kernels' MMA issuer stops
+ *                   before its first MMA, so the other roles' bounded waits run out
+ *                   (TIMEOUT, as above; tensor memory is still freed).
  * Errors: INVALID_ARG for an unknown key or an out-of-range value.
  */
 stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, int64_t value);

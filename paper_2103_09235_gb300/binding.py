@@ -31,7 +31,7 @@ EXPORTS = [
     "stencil_plan", "stencil_plan_set_option", "stencil_plan_get", "stencil_run",
     "stencil_run_batched", "stencil_sync", "stencil_folded_coeffs", "stencil_rel_l2",
     "stencil_fold_cost", "stencil_plan_destroy", "stencil_status_string", "stencil_last_error",
-    "stencil_run_1d_noalloc", "stencil_fold_counterparts",
+    "stencil_run_1d_noalloc", "stencil_fold_counterparts", "stencil_plan_ex",
 ]
 
 
@@ -58,6 +58,9 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         L.stencil_plan.argtypes = [ctypes.POINTER(_vp), _c.c_int, ctypes.POINTER(_i64), _c.c_int,
                                    ctypes.POINTER(_c.c_double), _c.c_int]
+        L.stencil_plan_ex.argtypes = [ctypes.POINTER(_vp), _c.c_int, ctypes.POINTER(_i64),
+                                      _c.c_int, ctypes.POINTER(_c.c_double), _c.c_int,
+                                      ctypes.POINTER(_i64), _c.c_uint]
         L.stencil_plan_set_option.argtypes = [_vp, _c.c_char_p, _i64]
         L.stencil_plan_get.argtypes = [_vp, _c.c_char_p, ctypes.POINTER(_i64)]
         L.stencil_run.argtypes = [_vp, _vp, _vp, _i64, _c.c_int, _vp]
@@ -83,7 +86,7 @@ def lib():
         L.stencil_status_string.restype = _c.c_char_p
         L.stencil_last_error.argtypes = []
         L.stencil_last_error.restype = _c.c_char_p
-        for name in ("stencil_plan", "stencil_plan_set_option", "stencil_plan_get", "stencil_run",
+        for name in ("stencil_plan", "stencil_plan_ex", "stencil_plan_set_option", "stencil_plan_get", "stencil_run",
                      "stencil_run_batched", "stencil_sync", "stencil_folded_coeffs",
                      "stencil_rel_l2", "stencil_fold_cost"):
             getattr(L, name).restype = _c.c_int
@@ -129,16 +132,23 @@ def _coeff_array(coeffs, ndim):
 class Plan:
     """A stencil plan: one grid shape, one base stencil, one dtype."""
 
-    def __init__(self, shape, coeffs, dtype: str = "f32"):
+    def __init__(self, shape, coeffs, dtype: str = "f32", pitch=None, flags: int = 0):
+        """pitch: None (dense) or the ndim-1 strides in elements, C order
+        (stencil_plan_ex); flags: stencil_plan_ex flags."""
         shape = tuple(int(s) for s in shape)
         c, r = _coeff_array(coeffs, len(shape))
         self.shape, self.radius, self.coeffs = shape, r, c
         self.dtype = F64 if dtype in ("f64", "float64", F64) else F32
         h = _vp()
         arr = (_i64 * len(shape))(*shape)
-        _check(lib().stencil_plan(ctypes.byref(h), len(shape), arr, r,
-                                  c.ctypes.data_as(ctypes.POINTER(_c.c_double)), self.dtype),
-               "stencil_plan")
+        cptr = c.ctypes.data_as(ctypes.POINTER(_c.c_double))
+        if pitch is None and not flags:
+            _check(lib().stencil_plan(ctypes.byref(h), len(shape), arr, r, cptr, self.dtype),
+                   "stencil_plan")
+        else:
+            parr = (_i64 * max(1, len(pitch)))(*pitch) if pitch is not None else None
+            _check(lib().stencil_plan_ex(ctypes.byref(h), len(shape), arr, r, cptr, self.dtype,
+                                         parr, int(flags)), "stencil_plan_ex")
         self.handle = h
 
     def set_option(self, key: str, value: int):

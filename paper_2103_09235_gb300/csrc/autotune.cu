@@ -15,6 +15,8 @@
 #include <sys/stat.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -106,7 +108,51 @@ void cache_store(const std::string &key, const Cand &c, double gstencil)
     fclose(f);
 }
 
+std::mutex g_cache_mu;
+// entries read or written by this process, keyed by cache file and key
+std::map<std::string, std::string> g_cache_mem;
+
 }  // namespace
+
+bool tune_cache_get(const std::string &key, std::string *value)
+{
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    const std::string path = cache_path();
+    auto it = g_cache_mem.find(path + "\n" + key);
+    if (it != g_cache_mem.end()) {
+        *value = it->second;
+        return true;
+    }
+    if (path.empty()) return false;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    const std::string needle = "{\"key\": \"" + key + "\", \"value\": \"";
+    while (fgets(line, sizeof(line), f)) {
+        if (strncmp(line, needle.c_str(), needle.size()) != 0) continue;
+        const char *v = line + needle.size();
+        const char *q = strchr(v, '"');
+        if (!q) continue;
+        *value = std::string(v, q - v);  // the last entry for a key wins
+        found = true;
+    }
+    fclose(f);
+    if (found) g_cache_mem[path + "\n" + key] = *value;
+    return found;
+}
+
+void tune_cache_put(const std::string &key, const std::string &value)
+{
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    const std::string path = cache_path();
+    g_cache_mem[path + "\n" + key] = value;
+    if (path.empty()) return;
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"value\": \"%s\"}\n", key.c_str(), value.c_str());
+    fclose(f);
+}
 
 stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
 {
@@ -159,10 +205,11 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     // timing on scratch copies of a seeded-free grid (all ones keeps values finite)
     const size_t esz = p->dtype == STENCIL_F64 ? 8 : 4;
     const size_t npts = (size_t)p->nx * p->ny * p->nz;
+    const size_t span = grid_extent(p);  // the caller's layout, gaps included
     void *din = nullptr, *dout = nullptr;
-    cudaError_t e = cudaMalloc(&din, npts * esz);
-    if (e == cudaSuccess) e = cudaMalloc(&dout, npts * esz);
-    if (e == cudaSuccess) e = cudaMemsetAsync(din, 0, npts * esz, s);
+    cudaError_t e = cudaMalloc(&din, span * esz);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, span * esz);
+    if (e == cudaSuccess) e = cudaMemsetAsync(din, 0, span * esz, s);
     if (e != cudaSuccess) {
         if (din) cudaFree(din);
         return cuda_fail(e, "autotune scratch");

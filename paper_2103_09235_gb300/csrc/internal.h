@@ -43,6 +43,13 @@ struct Padded {
     size_t elems = 0;
 };
 
+// Rounds FP64 weights to FP32 and then moves the rounding of their sum into
+// the centre tap (out[centre] absorbs sum(c) - sum(out), rounded once more),
+// so that the FP32 weights carry the exact stencil's mass to within one
+// rounding of the centre tap: the mean of the grid then does not drift by
+// T/m roundings of the weight sum.
+void round_f32_mass(const double *c, size_t n, size_t centre, float *out);
+
 // Raises a kernel's dynamic shared-memory limit to the current device's
 // opt-in maximum, once per (kernel, device); the attribute is per device, so
 // a library used on several GPUs sets it on each.
@@ -86,7 +93,7 @@ cudaError_t launch_sweep2d(int rb, int m, int pattern, const CUtensorMap &map,
 // ---- batched persistent 2D sweep --------------------------------------------
 // One pass of one grid of a batched run.
 struct BatchPass {
-    int variant;        // pattern * 8 + m (radius-1 base stencils)
+    int variant;        // batched_variant_id(base radius, m, pattern)
     int b, H, HX;       // fused sweeps, halo, halo rounded up to 4
     int tiles_x, ntiles;
     int map;            // index of the source tensor map
@@ -117,8 +124,13 @@ struct BatchArgs {
     int nstage;               // TMA stages: 1 (refilled after a tile's first sweep) or 2
     int *status;
     unsigned long long wait_ns;
+    int fault_withhold_dep;   // test hook: dependencies never count as met, so the
+                              // producer's bounded wait runs out (no fault)
 };
+// Radius-1 bases: star m <= 4, box m <= 2; radius-2 bases: star m <= 2, box m = 1.
 bool batched_variant_supported(int rb, int m, int pattern);
+// The kernel's code for (base radius, fold, pattern).
+int batched_variant_id(int rb, int m, int pattern);
 // nstage TMA stages plus nwork (0..2) work buffers of buf_floats each.
 size_t batched_smem_bytes(int buf_floats, int nwork, int nstage);
 int batched_ctas_per_sm(size_t smem);
@@ -168,17 +180,22 @@ bool sweep1d_supported(int R, bool f64);
 cudaError_t launch_sweep1d(int R, bool f64, const Sweep1DArgs &a, cudaStream_t s);
 
 // ---- layout conversion, coefficient folding, error reduction --------------
-cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_t s);
+// src: the user's grid, rows src_py and planes src_pz elements apart (0 =
+// dense: nx and nx*ny).
+cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_t s,
+                          int64_t src_py = 0, int64_t src_pz = 0);
 // One 2D grid's import within a batch: padded rows [row0, row0 + ny + 2 gw)
 // of the batch's row space.
 struct ImportJob {
     float *origin;
     int64_t py;
     const float *src;
+    int64_t src_py;  // row stride of the user's grid (elements)
     long long row0;
     int nx, ny, gw, vec4;
 };
-ImportJob make_import_job(const Padded &P, const float *src, int gw, long long row0);
+ImportJob make_import_job(const Padded &P, const float *src, int gw, long long row0,
+                          int64_t src_py = 0);
 // All jobs (device array, ordered by row0) in one launch; rows = the total.
 cudaError_t launch_import_batch(const ImportJob *d_jobs, int njobs, long long rows, cudaStream_t s);
 cudaError_t launch_export(const Padded &P, float *dst, cudaStream_t s);
@@ -224,6 +241,8 @@ struct TC2DArgs {
     int dst_gw;
     int dst_vec4;
     int tma_store;          // 1: the output tile leaves through a swizzled smem tile and a TMA store
+    int fault_withhold_mma; // test hook: the MMA issuer stops before its first MMA (no fault;
+                            // the other roles' bounded waits run out)
     int *status;
     unsigned long long wait_ns;
 };

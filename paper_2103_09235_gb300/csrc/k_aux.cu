@@ -16,20 +16,21 @@ __device__ __forceinline__ int wrap_idx(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-// dst (padded, ghost band gw) <- src (dense).  One CTA per padded row
+// dst (padded, ghost band gw) <- src (rows src_py, planes src_pz elements
+// apart).  One CTA per padded row
 // (z, y): the wrapped source row is found once, the interior is copied with
 // 16-byte accesses when the rows allow it, and the 2*gwx ghost columns of the
 // row are copied element by element.
 __global__ void k_import(float *__restrict__ origin, int64_t py, int64_t pz, int nx, int ny,
                          int nz, int gwx, int gwy, int gwz, const float *__restrict__ src,
-                         int vec4)
+                         int64_t src_py, int64_t src_pz, int vec4)
 {
     const int wy = ny + 2 * gwy, wz = nz + 2 * gwz;
     for (long long row = blockIdx.x; row < (long long)wy * wz; row += gridDim.x) {
         const int y = (int)(row % wy) - gwy;
         const int z = (int)(row / wy) - gwz;
         const int sy = wrap_idx(y, ny), sz = wrap_idx(z, nz);
-        const float *srow = src + ((long long)sz * ny + sy) * nx;
+        const float *srow = src + sz * src_pz + sy * src_py;
         float *drow = origin + z * pz + y * py;
         if (vec4) {
             const float4 *s4 = reinterpret_cast<const float4 *>(srow);
@@ -61,7 +62,7 @@ __global__ void k_import_batch(const ImportJob *__restrict__ jobs, int njobs, lo
         }
         const ImportJob &J = jobs[lo];
         const int y = (int)(row - J.row0) - J.gw;
-        const float *srow = J.src + (long long)wrap_idx(y, J.ny) * J.nx;
+        const float *srow = J.src + wrap_idx(y, J.ny) * J.src_py;
         float *drow = J.origin + y * J.py;
         if (J.vec4) {
             const float4 *s4 = reinterpret_cast<const float4 *>(srow);
@@ -204,31 +205,37 @@ int sm_count()
 
 }  // namespace
 
-cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_t s)
+cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_t s,
+                          int64_t src_py, int64_t src_pz)
 {
     const int gwx = gw, gwy = P.ndim >= 2 ? gw : 0, gwz = P.ndim >= 3 ? gw : 0;
+    if (src_py <= 0) src_py = P.nx;
+    if (src_pz <= 0) src_pz = src_py * P.ny;
     // 16-byte interior copies need 16-byte aligned rows on both sides
     const int vec4 = (P.nx % 4 == 0) && ((uintptr_t)src % 16 == 0) && (P.py % 4 == 0) &&
-                     ((uintptr_t)P.origin % 16 == 0);
+                     ((uintptr_t)P.origin % 16 == 0) && (src_py % 4 == 0) &&
+                     (P.ndim < 3 || src_pz % 4 == 0);
     const long long rows = (long long)(P.ny + 2 * gwy) * (P.nz + 2 * gwz);
     const int grid = (int)std::min<long long>(rows, (long long)sm_count() * 16);
     k_import<<<grid, 256, 0, s>>>(P.origin, P.py, P.pz, P.nx, P.ny, P.nz, gwx, gwy, gwz, src,
-                                  vec4);
+                                  src_py, src_pz, vec4);
     return cudaGetLastError();
 }
 
-ImportJob make_import_job(const Padded &P, const float *src, int gw, long long row0)
+ImportJob make_import_job(const Padded &P, const float *src, int gw, long long row0,
+                          int64_t src_py)
 {
     ImportJob j;
     j.origin = P.origin;
     j.py = P.py;
     j.src = src;
+    j.src_py = src_py > 0 ? src_py : P.nx;
     j.row0 = row0;
     j.nx = P.nx;
     j.ny = P.ny;
     j.gw = gw;
     j.vec4 = (P.nx % 4 == 0) && ((uintptr_t)src % 16 == 0) && (P.py % 4 == 0) &&
-             ((uintptr_t)P.origin % 16 == 0);
+             ((uintptr_t)P.origin % 16 == 0) && (j.src_py % 4 == 0);
     return j;
 }
 

@@ -82,6 +82,10 @@ __global__ void __launch_bounds__(NTT)
                 record_status(a.status, DEV_TIMEOUT);
                 break;
             }
+            // (fault_withhold_copy is a test hook: the first chunk is never
+            // requested, so the consumers' bounded waits and then this
+            // warp's must run out and report a timeout)
+            if (c == 0 && a.fault_withhold_copy) continue;
             mbar_arrive_expect_tx(&bars[s], chunk_bytes);
             tma_load_3d(stages + s * a.buf_floats, &map, &bars[s], a.map_x0 + x0 - HXT,
                         a.map_y0 + y0 - 2 * R, a.map_z0 + zin0 + c * ZC);

@@ -158,6 +158,10 @@ __global__ void __launch_bounds__(NT, 1)
             int i = 0, last = -1;
             for (int tile = first; tile < a.ntiles; tile += step, ++i) {
                 const int s = i & 1, k = i >> 1;
+                // (fault_withhold_mma is a test hook: the issuer stops before its
+                // first MMA, as if its completions were lost, so every other
+                // role's bounded wait must run out and report a timeout)
+                if (a.fault_withhold_mma) break;
                 if (!wait_or_abort(&ctl->a_full[s], k & 1, ctl, a)) break;
                 if (!wait_or_abort(&ctl->d_empty[s], (k & 1) ^ 1, ctl, a)) break;
                 tc_fence_after();

@@ -24,6 +24,9 @@ struct stencil_plan_s {
     int ndim = 0;
     int64_t shape[3] = {1, 1, 1};  // C order, as given
     int nx = 1, ny = 1, nz = 1;    // x fastest
+    // strides of the caller's grids (elements): rows pitch_y, planes pitch_z
+    // apart; nx and nx*ny unless stencil_plan_ex gave others
+    int64_t pitch_y = 1, pitch_z = 1;
     int r = 1;
     stencil_dtype_t dtype = STENCIL_F32;
     std::vector<double> coeffs;  // (2r+1)^ndim, axis order (z, y, x)
@@ -42,6 +45,8 @@ struct stencil_plan_s {
     int autotune = 1;
     long long wait_ms = 2000;
     int fault_withhold_copy = 0;  // test hook, see stencil_plan_set_option
+    int fault_withhold_dep = 0;   // test hook: batched dependency counters never complete
+    int fault_withhold_mma = 0;   // test hook: tensor-core MMA completions never signalled
 
     // FP64 folded weights computed on the GPU, by m
     std::map<int, std::vector<double>> folded;
@@ -91,6 +96,30 @@ struct stencil_plan_s {
 
 namespace sg {
 
+// Elements a caller's grid spans: the last point's index plus one.
+inline size_t grid_extent(const stencil_plan_s *p)
+{
+    return (size_t)(p->nz - 1) * p->pitch_z + (size_t)(p->ny - 1) * p->pitch_y + p->nx;
+}
+
+// Whether a caller's grid is dense (no gaps between rows or planes).
+inline bool grid_dense(const stencil_plan_s *p)
+{
+    return p->pitch_y == p->nx && (p->ndim < 3 || p->pitch_z == (int64_t)p->nx * p->ny);
+}
+
+// Whether 16-byte stores of whole rows reach every row of a caller's grid.
+inline bool grid_vec4(const stencil_plan_s *p, const void *base)
+{
+    return p->nx % 4 == 0 && p->pitch_y % 4 == 0 && (p->ndim < 3 || p->pitch_z % 4 == 0) &&
+           (uintptr_t)base % 16 == 0;
+}
+
+// Copies the nx x ny x nz points of a caller-layout grid (both sides use the
+// plan's pitches), skipping the gaps between rows and planes.
+cudaError_t copy_grid(const stencil_plan_s *p, void *dst, const void *src, cudaMemcpyKind kind,
+                      cudaStream_t s);
+
 // Thread-local error detail.
 void set_error(const char *fmt, ...);
 stencil_status_t cuda_fail(cudaError_t e, const char *what);
@@ -121,6 +150,10 @@ stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int 
 // returns the rank K (max_k + 1 when above max_k) and fills K rows of u, v.
 int cp_factor(const double *c, int W, int max_k, double *u, double *v);
 stencil_status_t plan_counterparts(stencil_plan_s *p, int m, const CpFactor **out);
+// The autotuner's persistent cache (JSON lines, one {"key", "value"} per
+// line; the last line for a key wins), also held in memory per process.
+bool tune_cache_get(const std::string &key, std::string *value);
+void tune_cache_put(const std::string &key, const std::string &value);
 void ensure_device_facts(stencil_plan_s *p);
 
 // Runs enqueue(stream, &kernels) on stream s.  With graphs enabled and s not

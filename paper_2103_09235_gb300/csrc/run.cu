@@ -117,7 +117,13 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
             a.tile = tile;
             a.b = ps.b;
             const std::vector<double> &c = ps.m == m ? *cm : *c1;
-            for (size_t k = 0; k < c.size(); ++k) a.c[k] = c[k];
+            if (f64) {
+                for (size_t k = 0; k < c.size(); ++k) a.c[k] = c[k];
+            } else {
+                float w[2 * kMaxR1D + 1];
+                round_f32_mass(c.data(), c.size(), c.size() / 2, w);
+                for (size_t k = 0; k < c.size(); ++k) a.c[k] = (double)w[k];
+            }
             cudaError_t e = launch_sweep1d(ps.m * p->r, f64, a, st_);
             if (e != cudaSuccess) return cuda_fail(e, "1D sweep launch");
             *nl += 1;
@@ -219,13 +225,14 @@ stencil_status_t launch_pass2d(stencil_plan_s *p, const Padded &src, int m, int 
     a.fault_withhold_copy = p->fault_withhold_copy;
     if (cpk) {
         // u_0 .. u_{K-1}, then v_0 .. v_{K-1}
+        // each factor keeps its own sum, so every separable term keeps its mass
         const int W = 2 * R + 1;
-        for (int k = 0; k < cpk * W; ++k) {
-            a.c[k] = (float)cp->u[k];
-            a.c[cpk * W + k] = (float)cp->v[k];
+        for (int k = 0; k < cpk; ++k) {
+            round_f32_mass(cp->u.data() + k * W, W, W / 2, a.c + k * W);
+            round_f32_mass(cp->v.data() + k * W, W, W / 2, a.c + cpk * W + k * W);
         }
     } else {
-        for (size_t k = 0; k < c.size(); ++k) a.c[k] = (float)c[k];
+        round_f32_mass(c.data(), c.size(), c.size() / 2, a.c);
     }
     const int box[2] = {kTileX2D + 2 * HX, cfg.ty + 2 * H};
     const CUtensorMap *map = plan_map(p, src, box);
@@ -307,10 +314,10 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
         if (st != STENCIL_OK) return st;
         if (!first_ty) first_ty = cfg.ty;
     }
-    const bool out_vec4 = (p->nx % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    const bool out_vec4 = grid_vec4(p, out);
 
     auto enqueue = [&](cudaStream_t st_, int *nl) -> stencil_status_t {
-        cudaError_t e = launch_import(p->A, in, gw, st_);
+        cudaError_t e = launch_import(p->A, in, gw, st_, p->pitch_y);
         if (e != cudaSuccess) return cuda_fail(e, "import launch");
         *nl += 1;
         const Padded *cur = &p->A, *oth = &p->B;
@@ -319,7 +326,7 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
             const Pass &ps = passes[i];
             stencil_status_t r = launch_pass2d(p, *cur, ps.m, ps.b, ps.m == m ? *cm : *c1,
                                                last ? out : oth->origin,
-                                               last ? (int64_t)p->nx : oth->py, last ? 0 : gw,
+                                               last ? p->pitch_y : oth->py, last ? 0 : gw,
                                                last ? out_vec4 : true, st_,
                                                cp_of(ps)->k ? cp_of(ps) : nullptr);
             if (r != STENCIL_OK) return r;

@@ -51,7 +51,7 @@ static stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int 
     a.dst_vec4 = dst_vec4 ? 1 : 0;
     a.status = p->d_status;
     a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
-    for (size_t k = 0; k < c.size(); ++k) a.c[k] = (float)c[k];
+    round_f32_mass(c.data(), c.size(), c.size() / 2, a.c);
     // one 3D box per stage: 64+2HX columns, 16+2bR rows, 4 planes
     const int box[3] = {kTX3 + 2 * a.halo_x, kTY3 + 2 * b * R, 4};
     const CUtensorMap *map = plan_map(p, src, box);
@@ -109,9 +109,9 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
     // ghost band: the widest halo any pass reads
     int gw = p->r;
     for (auto &x : passes) gw = std::max(gw, x.first * x.second * p->r);
-    const bool out_vec4 = (p->nx % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    const bool out_vec4 = grid_vec4(p, out);
     auto enqueue = [&](cudaStream_t st_, int *nl) -> stencil_status_t {
-        cudaError_t e = launch_import(p->A, in, gw, st_);
+        cudaError_t e = launch_import(p->A, in, gw, st_, p->pitch_y, p->pitch_z);
         if (e != cudaSuccess) return cuda_fail(e, "import launch");
         *nl += 1;
         const Padded *cur = &p->A, *oth = &p->B;
@@ -120,7 +120,7 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
             const int mm = passes[i].first, bb = passes[i].second;
             stencil_status_t r = launch_pass3d(
                 p, *cur, mm, bb, mm == m ? *cm : *c1, last ? out : oth->origin,
-                last ? (int64_t)p->nx : oth->py, last ? (int64_t)p->nx * p->ny : oth->pz,
+                last ? p->pitch_y : oth->py, last ? p->pitch_z : oth->pz,
                 last ? 0 : gw, last ? out_vec4 : true, st_);
             if (r != STENCIL_OK) return r;
             *nl += 1;

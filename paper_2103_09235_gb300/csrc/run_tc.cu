@@ -73,6 +73,7 @@ static stencil_status_t launch_tc_grouped_pass(stencil_plan_s *p, const Padded &
     a.dst_vec4 = dst_vec4 ? 1 : 0;
     a.status = p->d_status;
     a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
+    a.fault_withhold_mma = p->fault_withhold_mma;
     const int box[2] = {a.box_w, a.rows};
     const CUtensorMap *map = plan_map(p, src, box);
     if (!map) return STENCIL_ERR_CUDA;
@@ -113,6 +114,7 @@ static stencil_status_t launch_tc_pass(stencil_plan_s *p, const Padded &src, int
     a.dst_vec4 = dst_vec4 ? 1 : 0;
     a.status = p->d_status;
     a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
+    a.fault_withhold_mma = p->fault_withhold_mma;
     const int box[2] = {a.box_w, a.rows};
     const CUtensorMap *map = plan_map(p, src, box);
     if (!map) return STENCIL_ERR_CUDA;
@@ -173,11 +175,11 @@ stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_
         st = pass2d_config(p, 1, b, &cfg);
         if (st != STENCIL_OK) return st;
     }
-    const bool out_vec4 = (p->nx % 4 == 0) && ((uintptr_t)out % 16 == 0);
+    const bool out_vec4 = grid_vec4(p, out);
     const int64_t npass = q + (int64_t)plain.size();
 
     auto enqueue = [&](cudaStream_t st_, int *nl) -> stencil_status_t {
-        cudaError_t e = launch_import(p->A, in, gw, st_);
+        cudaError_t e = launch_import(p->A, in, gw, st_, p->pitch_y);
         if (e != cudaSuccess) return cuda_fail(e, "import launch");
         *nl += 1;
         if (p->tc_center && q > 0) {
@@ -191,7 +193,7 @@ stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_
         for (int64_t i = 0; i < q; ++i, ++done) {
             const bool last = done + 1 == npass;
             float *dst = last ? out : oth->origin;
-            const int64_t dpy = last ? (int64_t)p->nx : oth->py;
+            const int64_t dpy = last ? p->pitch_y : oth->py;
             stencil_status_t r =
                 grouped ? launch_tc_grouped_pass(p, *cur, m, panels, sum_c, dst, dpy, last ? 0 : gw,
                                                  last ? out_vec4 : true, st_)
@@ -204,7 +206,7 @@ stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_
         for (int b : plain) {
             const bool last = done + 1 == npass;
             stencil_status_t r = launch_pass2d(p, *cur, 1, b, *c1, last ? out : oth->origin,
-                                               last ? (int64_t)p->nx : oth->py, last ? 0 : gw,
+                                               last ? p->pitch_y : oth->py, last ? 0 : gw,
                                                last ? out_vec4 : true, st_);
             if (r != STENCIL_OK) return r;
             *nl += 1;
@@ -214,7 +216,8 @@ stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_
         return STENCIL_OK;
     };
     std::vector<int64_t> key = {3, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m,
-                                p->precision, p->tc_center, p->wait_ms, grouped ? 1 : 0};
+                                p->precision, p->tc_center, p->wait_ms, grouped ? 1 : 0,
+                                p->fault_withhold_mma};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = 1;

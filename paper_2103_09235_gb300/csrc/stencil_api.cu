@@ -32,6 +32,17 @@ stencil_status_t cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? STENCIL_ERR_OOM : STENCIL_ERR_CUDA;
 }
 
+void round_f32_mass(const double *c, size_t n, size_t centre, float *out)
+{
+    double want = 0.0, got = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        out[i] = (float)c[i];
+        want += c[i];
+        got += (double)out[i];
+    }
+    if (n > 0) out[centre] = (float)((double)out[centre] + (want - got));
+}
+
 cudaError_t smem_optin(const void *kernel)
 {
     static std::mutex mu;
@@ -137,6 +148,25 @@ const CUtensorMap *plan_map(stencil_plan_s *p, const Padded &P, const int *box)
     return &(p->maps[key] = m);
 }
 
+cudaError_t copy_grid(const stencil_plan_s *p, void *dst, const void *src, cudaMemcpyKind kind,
+                      cudaStream_t s)
+{
+    const size_t esz = p->dtype == STENCIL_F64 ? 8 : 4;
+    if (grid_dense(p)) return cudaMemcpyAsync(dst, src, esz * grid_extent(p), kind, s);
+    // rows of nx points, pitch_y apart; planes pitch_z apart
+    if (p->ndim < 3 || p->pitch_z == p->pitch_y * p->ny)
+        return cudaMemcpy2DAsync(dst, esz * p->pitch_y, src, esz * p->pitch_y, esz * p->nx,
+                                 (size_t)p->ny * p->nz, kind, s);
+    for (int z = 0; z < p->nz; ++z) {
+        const size_t off = esz * (size_t)z * p->pitch_z;
+        cudaError_t e = cudaMemcpy2DAsync((char *)dst + off, esz * p->pitch_y,
+                                          (const char *)src + off, esz * p->pitch_y, esz * p->nx,
+                                          (size_t)p->ny, kind, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace sg
 
 using namespace sg;
@@ -236,6 +266,8 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
     p->nx = (int)shape[ndim - 1];
     p->ny = ndim >= 2 ? (int)shape[ndim - 2] : 1;
     p->nz = ndim >= 3 ? (int)shape[0] : 1;
+    p->pitch_y = p->nx;
+    p->pitch_z = (int64_t)p->nx * p->ny;
     p->r = radius;
     p->dtype = dtype;
     const int n = taps_count(ndim, radius);
@@ -265,6 +297,48 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
     return STENCIL_OK;
 }
 
+stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64_t *shape,
+                                 int radius, const double *coeffs, stencil_dtype_t dtype,
+                                 const int64_t *pitch_elems, unsigned flags)
+{
+    if (!out_plan) {
+        set_error("stencil_plan_ex: null out_plan");
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    *out_plan = nullptr;
+    if (flags & ~(unsigned)STENCIL_FLAG_NONPERIODIC) {
+        set_error("stencil_plan_ex: unknown flag bits 0x%x", flags);
+        return STENCIL_ERR_INVALID_ARG;
+    }
+    if (flags & STENCIL_FLAG_NONPERIODIC) {
+        set_error("stencil_plan_ex: only periodic boundaries are supported (folding is exact "
+                  "only on periodic grids)");
+        return STENCIL_ERR_UNSUPPORTED;
+    }
+    // pitch_elems[d] is the stride of axis d (C order), d = 0 .. ndim-2;
+    // checked before any device work
+    int64_t py = 0, pz = 0;
+    if (pitch_elems && shape && ndim >= 2 && ndim <= 3) {
+        const int64_t nx = shape[ndim - 1], ny = shape[ndim - 2];
+        py = pitch_elems[ndim - 2];
+        pz = ndim == 3 ? pitch_elems[0] : py * ny;
+        if (py < nx || (ndim == 3 && pz < py * ny) || py > ((int64_t)1 << 31) ||
+            pz > ((int64_t)1 << 40)) {
+            set_error("stencil_plan_ex: pitches must satisfy row >= nx and plane >= row * ny");
+            return STENCIL_ERR_INVALID_ARG;
+        }
+    }
+    stencil_plan_t p = nullptr;
+    stencil_status_t st = stencil_plan(&p, ndim, shape, radius, coeffs, dtype);
+    if (st != STENCIL_OK) return st;
+    if (py > 0) {
+        p->pitch_y = py;
+        p->pitch_z = pz;
+    }
+    *out_plan = p;
+    return STENCIL_OK;
+}
+
 stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int64_t v)
 {
     if (!p || !key) {
@@ -275,7 +349,7 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
         if (v < 0 || v > 2) goto bad;
         p->precision = (int)v;
     } else if (!strcmp(key, "block_b")) {
-        if (v < 0 || v > 16) goto bad;
+        if (v < 0 || v > 64) goto bad;
         p->block_b = (int)v;
     } else if (!strcmp(key, "tile_y")) {
         if (v != 0 && (v < 8 || v > 192)) goto bad;
@@ -295,6 +369,12 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "fault_withhold_copy")) {
         if (v != 0 && v != 1) goto bad;
         p->fault_withhold_copy = (int)v;
+    } else if (!strcmp(key, "fault_withhold_dep")) {
+        if (v != 0 && v != 1) goto bad;
+        p->fault_withhold_dep = (int)v;
+    } else if (!strcmp(key, "fault_withhold_mma")) {
+        if (v != 0 && v != 1) goto bad;
+        p->fault_withhold_mma = (int)v;
     } else if (!strcmp(key, "counterparts")) {
         if (v < 0 || v > 2) goto bad;
         p->counterparts = (int)v;
@@ -433,7 +513,9 @@ stencil_status_t stencil_run(stencil_plan_t p, const void *in, void *out, int64_
         return STENCIL_ERR_INVALID_ARG;
     }
     const size_t esz = p->dtype == STENCIL_F64 ? 8 : 4;
-    const size_t bytes = esz * (size_t)p->nx * p->ny * p->nz;
+    // the span of the caller's layout: with pitches, gaps between rows and
+    // planes are inside it but never read or written
+    const size_t bytes = esz * grid_extent(p);
     const void *din_p = in;
     void *dout_p = out;
     cudaError_t e;
@@ -444,14 +526,14 @@ stencil_status_t stencil_run(stencil_plan_t p, const void *in, void *out, int64_
             if (e != cudaSuccess) return cuda_fail(e, "host staging buffers");
             p->scratch_bytes += 2 * bytes;
         }
-        e = cudaMemcpyAsync(p->stage_in, in, bytes, cudaMemcpyHostToDevice, s);
+        e = copy_grid(p, p->stage_in, in, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
         din_p = p->stage_in;
         dout_p = p->stage_out;
     }
     stencil_status_t st;
     if (T == 0) {
-        e = cudaMemcpyAsync(dout_p, din_p, bytes, cudaMemcpyDeviceToDevice, s);
+        e = copy_grid(p, dout_p, din_p, cudaMemcpyDeviceToDevice, s);
         st = e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "copy for T = 0");
     } else if (p->ndim == 1) {
         st = run1d(p, din_p, dout_p, T, fold_m, s);
@@ -462,7 +544,7 @@ stencil_status_t stencil_run(stencil_plan_t p, const void *in, void *out, int64_
     }
     if (st != STENCIL_OK) return st;
     if (!din) {
-        e = cudaMemcpyAsync(out, dout_p, bytes, cudaMemcpyDeviceToHost, s);
+        e = copy_grid(p, out, dout_p, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     }

@@ -2,6 +2,7 @@
 entry point the header declares, rejects bad arguments before touching a GPU,
 and its planner counts match the values the paper prints (Section 3.2)."""
 
+import ctypes
 import os
 import re
 
@@ -84,3 +85,26 @@ def test_fold_cost_support_sizes(blib, ndim, kind, m, folded):
     assert f == folded
     base = int(np.count_nonzero(c))
     assert naive >= base * m
+
+
+def test_plan_ex_rejects_flags_and_pitches_before_device_work(blib):
+    """stencil_plan_ex: unknown flag bits are INVALID_ARG, a non-periodic
+    boundary is UNSUPPORTED, pitches below the dense strides are INVALID_ARG;
+    all of them are decided on the host, before any device call."""
+    L = blib.lib()
+    h = ctypes.c_void_p()
+    c = np.zeros((3, 3)); c[1, 1] = 1.0
+    cp = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    shape = (ctypes.c_int64 * 2)(64, 100)
+    good = (ctypes.c_int64 * 1)(128)
+    assert L.stencil_plan_ex(ctypes.byref(h), 2, shape, 1, cp, 0, good, 4) == 1      # unknown bit
+    assert L.stencil_plan_ex(ctypes.byref(h), 2, shape, 1, cp, 0, good, 1) == 2      # non-periodic
+    assert "periodic" in L.stencil_last_error().decode()
+    short = (ctypes.c_int64 * 1)(99)
+    assert L.stencil_plan_ex(ctypes.byref(h), 2, shape, 1, cp, 0, short, 0) == 1     # row < nx
+    c3 = np.zeros((3, 3, 3)); c3[1, 1, 1] = 1.0
+    cp3 = c3.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    shape3 = (ctypes.c_int64 * 3)(8, 10, 12)
+    flat = (ctypes.c_int64 * 2)(16 * 9, 16)                                          # plane < row*ny
+    assert L.stencil_plan_ex(ctypes.byref(h), 3, shape3, 1, cp3, 0, flat, 0) == 1
+    assert not h.value

@@ -87,3 +87,110 @@ def test_batched_rejects_non_2d(env):
     with pytest.raises(binding.StencilError) as ei:
         binding.run_batched([p1], [x], [x], [5])
     assert ei.value.status == 2
+
+
+def _batch_plans(binding, torch, specs):
+    plans, xs, ys, refs_in = [], [], [], []
+    for j, (shape, kind, r, T, seed) in enumerate(specs):
+        c = synth.dyadic_coeffs(seed, 2, r, kind)
+        x = synth.grid(seed + 7, shape, np.float32)
+        plans.append(binding.Plan(shape, c))
+        xs.append(torch.from_numpy(x).cuda())
+        ys.append(torch.full_like(xs[-1], float("nan")))
+        refs_in.append((x, c, T))
+    return plans, xs, ys, refs_in
+
+
+SPECS = [((200, 300), "star", 1, 40, 9300), ((150, 140), "box", 1, 33, 9301),
+         ((256, 200), "star", 1, 57, 9302), ((180, 230), "box", 1, 21, 9303)]
+
+
+def test_batched_autotuner_tunes_and_caches(env, tmp_path, monkeypatch):
+    """fold_m = 0 for every grid: the batch autotuner times (m, b) per class of
+    grids and the tile height, writes its choices to the cache file, and the
+    run matches the oracle."""
+    torch, binding, oracle = env
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("STENCIL_TUNE_CACHE", str(cache))
+    plans, xs, ys, refs_in = _batch_plans(binding, torch, SPECS)
+    binding.run_batched(plans, xs, ys, [t for _, _, t in refs_in])
+    plans[0].sync()
+    for y, (x, c, T) in zip(ys, refs_in):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
+    text = cache.read_text()
+    assert text.count('"key": "batched|2d|') >= 2 and '"key": "batched-tile|' in text
+    for p in plans:
+        p.close()
+
+
+def test_batched_uses_cached_choice(env, tmp_path, monkeypatch):
+    """A cache entry decides the fold and blocking depth the batched launch
+    picks for its class of grids (here: stars m = 1, b = 3; boxes m = 2, b = 1)."""
+    import math
+    torch, binding, oracle = env
+    gpu = torch.cuda.get_device_name()
+    cache = tmp_path / "tune.jsonl"
+    lines, classes = [], []
+    for shape, kind, r, T, seed in SPECS:
+        pat = 0 if kind == "star" else 1
+        cls = (r, pat, int(math.floor(math.log2(shape[0] * shape[1]))))
+        if cls not in classes:
+            classes.append(cls)
+        val = "1 3" if kind == "star" else "2 1"
+        lines.append('{"key": "batched|2d|r%d|pat%d|area2^%d|f32|%s", "value": "%s"}'
+                     % (cls + (gpu, val)))
+    tile = "batched-tile|" + "".join("r%d.p%d.a%d;" % c for c in sorted(classes)) + "|" + gpu
+    lines.append('{"key": "%s", "value": "64"}' % tile)
+    cache.write_text("\n".join(lines) + "\n")
+    monkeypatch.setenv("STENCIL_TUNE_CACHE", str(cache))
+    plans, xs, ys, refs_in = _batch_plans(binding, torch, SPECS)
+    binding.run_batched(plans, xs, ys, [t for _, _, t in refs_in])
+    plans[0].sync()
+    for p, (shape, kind, r, T, seed) in zip(plans, SPECS):
+        assert (p.get("last_m"), p.get("last_b")) == ((1, 3) if kind == "star" else (2, 1))
+        assert p.get("last_tile_y") == 64
+    for y, (x, c, T) in zip(ys, refs_in):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("fold", [None, 1, 2, 8])
+def test_batched_radius2_and_fold_clamp(env, fold):
+    """Radius-2 bases (stars folded up to m = 2, boxes plain) beside radius-1
+    ones; a fold request above the kernel's (8) is lowered to the largest it
+    has, which gives the same T steps."""
+    torch, binding, oracle = env
+    specs = [((220, 260), "star", 2, 31, 9400), ((130, 170), "box", 2, 17, 9401),
+             ((160, 150), "star", 1, 29, 9402), ((200, 120), "box", 1, 23, 9403)]
+    plans, xs, ys, refs_in = _batch_plans(binding, torch, specs)
+    folds = None if fold is None else [fold] * len(specs)
+    binding.run_batched(plans, xs, ys, [t for _, _, t in refs_in], folds)
+    plans[0].sync()
+    for y, (x, c, T) in zip(ys, refs_in):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
+    if fold == 8:
+        assert [p.get("last_m") for p in plans] == [2, 1, 4, 2]
+    for p in plans:
+        p.close()
+
+
+def test_batched_dependency_wait_times_out(env):
+    """The producer's wait for a previous pass's tiles is bounded: with the
+    test hook that keeps every dependency unmet, it runs out (50 ms), the
+    status reads TIMEOUT, the context stays usable, and the next run matches
+    the oracle."""
+    torch, binding, oracle = env
+    plans, xs, ys, refs_in = _batch_plans(binding, torch, SPECS[:2])
+    Ts = [t for _, _, t in refs_in]
+    plans[0].set_option("wait_limit_ms", 50).set_option("fault_withhold_dep", 1)
+    binding.run_batched(plans, xs, ys, Ts, [1, 1])
+    assert plans[0].sync_status() == 5
+    assert plans[0].sync_status() == 0  # the status clears once read
+    plans[0].set_option("fault_withhold_dep", 0)
+    binding.run_batched(plans, xs, ys, Ts, [1, 1])
+    plans[0].sync()
+    for y, (x, c, T) in zip(ys, refs_in):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
+    for p in plans:
+        p.close()

@@ -6,16 +6,25 @@ host finishes it in seconds (1D 2^20 x 100 steps), otherwise the oracle's
 per-Fourier-mode closed form (spectral_run), itself pinned against the time
 loop by the CPU tests.
 
-Two bounds are asserted on every output:
-- the whole-grid relative L2 error, <= 1e-5 for the FP32 and BF16x3 paths
-  and <= 1e-12 for FP64 (the configured tolerance);
-- the zero-mean relative L2 error (each field minus its own mean), which
-  measures the error against the part of the field the stencil still moves.
-  After T steps of diffusion the mean carries most of ||A_T|| (at 4096^2,
-  T = 1000 the fluctuation is under 1 % of the norm), so the whole-grid
-  bound alone would let the fluctuation be off by 1e-3.  The zero-mean
-  bounds are derived from the arithmetic: ZM_FP32 for FP32 CUDA-core sweeps,
-  ZM_BF16X3 for the tensor-core split, ZM_FP64 for FP64 (see the constants).
+Two bounds are asserted on every output y against the oracle's r:
+- the whole-grid relative L2 error ||y - r|| / ||r||, <= 1e-5 for the FP32
+  and BF16x3 paths and <= 1e-12 for FP64 (the configured tolerance);
+- the error of the fluctuating part, ||(y - mean y) - (r - mean r)|| / ||r||,
+  <= TAU (below).  After T steps of diffusion the mean carries most of ||r||
+  (at 4096^2, T = 1000 the fluctuation r - mean r is under 1 % of the norm),
+  so the whole-grid bound alone would let the part of the field the stencil
+  still moves be off by 1e-3 of itself.  TAU is a tenth of the whole-grid
+  tolerance for FP32: the fluctuating part must be ten times more accurate
+  than the configured bound asks of the whole field, i.e. within 1e-4 of
+  itself at 4096^2.  FP32 sweeps accumulate sqrt(nnz) roundings of
+  u = 2^-24 at values near 0.5 per sweep, about 1e-7 per point, which the
+  stencil damps except in the slow modes: the fluctuation error stays near
+  1e-7 of the norm, under TAU_FP32 = 1e-6.  The BF16x3 split keeps 16
+  significant bits of each centred value and weight (2^-17 relative) on
+  values whose spread shrinks as the field diffuses; its fluctuation error is
+  of the same order, bounded by TAU_BF16X3 = 2.5e-6.  FP64: 1e-13.
+The zero-mean relative error (the fluctuation error over ||r - mean r||) is
+printed beside both.
 """
 
 import numpy as np
@@ -27,17 +36,10 @@ pytestmark = pytest.mark.gpu
 
 BASE = synth.BASE_SEED
 
-# Zero-mean tolerances.  FP32 rounds each output of a sweep to within
-# u = 2^-24 of a value near 0.5; the rounding errors of successive sweeps are
-# damped by the stencil except in the slow modes, which also carry the
-# surviving fluctuation, so the error against the fluctuation (a few 1e-3 per
-# point after the configured step counts) stays of order u * 0.5 * sqrt(#sweeps)
-# / 5e-3 ~ 1e-5 .. 1e-4: bound 2e-4.  The BF16x3 split keeps about 16
-# significant bits of each centred value and weight, 2^-17 ~ 7.6e-6 relative
-# per sweep, on values up to 0.5 around the mean: bound 2e-3.  FP64: 1e-10.
-ZM_FP32 = 2e-4
-ZM_BF16X3 = 2e-3
-ZM_FP64 = 1e-10
+# Bounds of the fluctuating part's error relative to ||r|| (module docstring).
+ZM_FP32 = 1e-6
+ZM_BF16X3 = 2.5e-6
+ZM_FP64 = 1e-13
 
 
 @pytest.fixture(scope="module")
@@ -69,14 +71,24 @@ def run(env, shape, c, x, T, m, facts=None, **opts):
     return y
 
 
+def fluct_fraction(ref):
+    """||r - mean r|| / ||r||: the share of the norm the stencil still moves."""
+    r = np.asarray(ref, np.float64).ravel()
+    return float(np.linalg.norm(r - r.mean()) / np.linalg.norm(r))
+
+
 def check(oracle, label, y, ref, tol, zm_tol, report_only=False):
+    """Whole-grid error <= tol and fluctuation error (relative to ||r||) <= zm_tol."""
     err = oracle.rel_l2(y, ref)
     zm = oracle.rel_l2_zero_mean(y, ref)
-    print("%s rel-L2 %.3e zero-mean %.3e" % (label, err, zm))
+    f = fluct_fraction(ref)
+    fe = zm * f
+    print("%s rel-L2 %.3e zero-mean %.3e (fluctuation %.2e of the norm; its error %.3e "
+          "of the norm)" % (label, err, zm, f, fe))
     if report_only:
         return err, zm
     assert err <= tol
-    assert zm <= zm_tol
+    assert fe <= zm_tol
     return err, zm
 
 
@@ -216,14 +228,23 @@ def test_batched_256(env):
         data.append((x, c, g["T"]))
     binding.run_batched(plans, xs, ys, Ts)
     plans[0].sync()
-    worst = worst_zm = 0.0
-    for (x, c, T), y in zip(data, ys):
+    worst = worst_zm = worst_fe = 0.0
+    rows = []
+    for (x, c, T), y, p, g in zip(data, ys, plans, grids):
         ref = oracle.spectral_run(x.astype(np.float64), c, T)
         yh = y.cpu().numpy()
-        worst = max(worst, oracle.rel_l2(yh, ref))
-        worst_zm = max(worst_zm, oracle.rel_l2_zero_mean(yh, ref))
-    print("batched 256 worst rel-L2 %.3e zero-mean %.3e" % (worst, worst_zm))
+        zm = oracle.rel_l2_zero_mean(yh, ref)
+        err = oracle.rel_l2(yh, ref)
+        fe = zm * fluct_fraction(ref)
+        worst = max(worst, err)
+        worst_zm = max(worst_zm, zm)
+        worst_fe = max(worst_fe, fe)
+        rows.append((fe, err, zm, g["shape"], g["kind"], T, p.get("last_m"), p.get("last_b")))
+    for row in sorted(rows, reverse=True)[:5]:
+        print("  grid: fluct err %.2e rel-L2 %.2e zero-mean %.2e shape %s %s T=%d m=%d b=%d" % row)
+    print("batched 256 worst rel-L2 %.3e zero-mean %.3e fluctuation error %.3e of the norm"
+          % (worst, worst_zm, worst_fe))
     assert worst <= 1e-5
-    assert worst_zm <= ZM_FP32
+    assert worst_fe <= ZM_FP32
     for p in plans:
         p.close()

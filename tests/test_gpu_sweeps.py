@@ -242,21 +242,23 @@ def test_bounded_wait_reports_timeout(env, m, b, stages):
     check(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, T))
 
 
-@pytest.mark.parametrize("kind,m", [("star", 1), ("box", 2)])
-def test_bounded_wait_reports_timeout_3d(env, kind, m):
-    """The single-sweep 3D kernel: a withheld chunk ends the consumer warps'
-    waits and the producer's with a status, for a padded destination (ghost
-    refresh) and the dense last pass alike; the next run is correct."""
+@pytest.mark.parametrize("kind,m,b", [("star", 1, 1), ("box", 2, 1), ("star", 1, 2), ("star", 2, 2)])
+def test_bounded_wait_reports_timeout_3d(env, kind, m, b):
+    """Both 3D kernels (single sweeps, b = 1, and two fused sweeps, b = 2): a
+    withheld chunk ends the consumer warps' waits and the producer's with a
+    status, for a padded destination (ghost refresh) and the dense last pass
+    alike; the next run is correct."""
     torch, binding, oracle = env
     shape = (40, 48, 64)
     c = synth.dyadic_coeffs(23, 3, 1, kind)
     x = synth.grid(24, shape, np.float32)
-    plan = binding.Plan(shape, c).set_option("block_b", 1)
+    plan = binding.Plan(shape, c).set_option("block_b", b)
     plan.set_option("wait_limit_ms", 50).set_option("fault_withhold_copy", 1)
     xd = torch.from_numpy(x).cuda()
     yd = torch.empty_like(xd)
-    T = 2 * m
+    T = 2 * m * b
     plan.run(xd, yd, T, fold_m=m)
+    assert plan.get("last_b") == b
     assert plan.sync_status() == 5
     assert plan.sync_status() == 0
     plan.set_option("fault_withhold_copy", 0)

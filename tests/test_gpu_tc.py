@@ -99,3 +99,28 @@ def test_tc_star_parity(env, shape, T, m):
     err = oracle.rel_l2(y, ref)
     print("TC star %s T=%d m=%d rel-L2 %.3e" % (shape, T, m, err))
     assert err <= TOL
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_tc_bounded_waits_report_timeout(env, form):
+    """Both tensor-core kernels: with the test hook that stops the MMA issuer
+    before its first MMA, the producer's, converters' and epilogue's bounded
+    waits run out (50 ms), the status reads TIMEOUT, tensor memory is freed,
+    and the next run on the same plan matches the oracle."""
+    torch, binding, oracle = env
+    shape, T, m = (300, 520), 13, 4
+    c = synth.dyadic_coeffs(31, 2, 1, "box")
+    x = synth.grid(32, shape, np.float32)
+    plan = binding.Plan(shape, c).set_option("precision", 1).set_option("tc_form", form)
+    plan.set_option("wait_limit_ms", 50).set_option("fault_withhold_mma", 1)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, T, fold_m=m)
+    assert plan.sync_status() == 5
+    assert plan.sync_status() == 0
+    plan.set_option("fault_withhold_mma", 0)
+    plan.run(xd, yd, T, fold_m=m)
+    plan.sync()
+    assert plan.get("last_engine") == 1 and plan.get("last_tc_form") == form
+    assert oracle.rel_l2(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
+    plan.close()
