@@ -426,6 +426,12 @@ VARIANTS = [
     ("heat1d_2pow20_T100_fp64", "heat1d", 1, {}, "f64"),
     ("heat1d_2pow20_T100_fp32_autotuned", "heat1d", 0, {}, "f32"),
     ("heat1d_2pow20_T100_fp64_autotuned", "heat1d", 0, {}, "f64"),
+    ("heat1d_2pow20_T100_fp64_m16_overlapped", "heat1d", 16, {"block_b": 32, "tessellate": 0},
+     "f64"),
+    ("heat1d_2pow20_T100_fp64_m16_tessellated", "heat1d", 16, {"block_b": 32, "tessellate": 1},
+     "f64"),
+    ("heat1d_2pow20_T100_fp32_m6_tessellated", "heat1d", 6, {"block_b": 64, "tessellate": 1},
+     "f32"),
     ("box8192_T512_plain_fp32", "box8192", 1, {"block_b": 1}, "f32"),
     ("box8192_T512_cuda_core_m2b2", "box8192", 2, {"block_b": 2}, "f32"),
     ("box8192_T512_cuda_core_autotuned", "box8192", 0, {}, "f32"),

@@ -125,6 +125,11 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *                   (chosen by the autotuner, else the kernel's own size), 256 =
  *                   two half-size CTAs per SM for folded sweeps that run 512.
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
+ *   "center"        2D/3D CUDA-core runs and batches: 1 = store the grid minus its mean
+ *                   mu (from an FP64 sum of the input) and add mu * (sum c)^T to the
+ *                   output, so that FP32 sums round values near zero rather than near
+ *                   mu (default 1; the run is linear, so the result is the same T
+ *                   steps); 0 = store the values as they are.
  *   "counterparts"  2D CUDA-core sweeps in counterpart form (Section 3.3 vertical then
  *                   horizontal folding; Section 3.5 counterpart reuse): when c^(m)
  *                   factors exactly as a sum of K <= 2 separable terms u_k (x) v_k, a
@@ -141,6 +146,13 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *                   radius: grouped from R = m*r >= 6 (default).
  *   "tc_tma_store"  1 = per-offset tensor-core tiles leave through a TMA store when the
  *                   destination allows it (default 1); 0 = direct stores.
+ *   "tessellate"    1D passes: 1 = exact tessellate tiling (Section 3.4): per pass of b
+ *                   steps, tiles first advance their shrinking triangles, then the
+ *                   inverted triangles around the tile boundaries finish every point,
+ *                   with no step computed twice (two launches per pass; used where
+ *                   the tile of 2048 FP64 / 4096 FP32 points is at least 2*b*R wide);
+ *                   0 = overlapped tiles that recompute their rim (default).  The
+ *                   autotuner tries both.
  *   "wait_limit_ms" bound of every device-side wait (default 2000).
  *   "autotune"      1 = time candidates when stencil_run gets fold_m = 0 (default 1).
  *   "graph"         1 = capture each distinct run (pointers, T, m, options) once into
@@ -166,6 +178,7 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, i
  * first pass), "last_tc_form" (1 per-offset, 2 grouped: the tensor-core kernel
  * of the last tensor-core run), "last_cp" (separable terms K of the last 2D
  * CUDA-core run's folded passes in counterpart form, 0 = direct form),
+ * "last_tess" (1 if the last 1D run's first pass was tessellated exactly),
  * "launches" (kernels the plan has launched so far),
  * "scratch_bytes" (device bytes the plan owns).
  */
@@ -257,6 +270,17 @@ stencil_status_t stencil_fold_cost(int ndim, int radius, const double *coeffs, i
  */
 stencil_status_t stencil_fold_counterparts(int W, const double *folded, int max_k, int *k_out,
                                            double *u_out, double *v_out);
+
+/*
+ * Host-only schedule of the exact tessellate tiling (Section 3.4) that the
+ * "tessellate" option runs: for one tile of W points in a line of such tiles,
+ * b steps of a radius-R stencil, stage1[i] and stage2[i] receive how many of
+ * the b steps point i takes in the triangle stage and in the inverted-triangle
+ * stage (they sum to b).  W = 9, b = 4, R = 1 gives 0,1,2,3,4,3,2,1,0 and
+ * 4,3,2,1,0,1,2,3,4.  stage1 and stage2 hold W ints each.  Needs no GPU.
+ * Errors: INVALID_ARG for W < 2*b*R, b < 1, R < 1 or a null pointer.
+ */
+stencil_status_t stencil_tessellation_counts(int W, int b, int R, int *stage1, int *stage2);
 
 /*
  * T plain steps of a 1D periodic stencil without allocating any memory.

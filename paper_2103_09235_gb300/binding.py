@@ -32,6 +32,7 @@ EXPORTS = [
     "stencil_run_batched", "stencil_sync", "stencil_folded_coeffs", "stencil_rel_l2",
     "stencil_fold_cost", "stencil_plan_destroy", "stencil_status_string", "stencil_last_error",
     "stencil_run_1d_noalloc", "stencil_fold_counterparts", "stencil_plan_ex",
+    "stencil_tessellation_counts",
 ]
 
 
@@ -80,6 +81,9 @@ def lib():
                                                 ctypes.POINTER(_c.c_double),
                                                 ctypes.POINTER(_c.c_double)]
         L.stencil_fold_counterparts.restype = _c.c_int
+        L.stencil_tessellation_counts.argtypes = [_c.c_int, _c.c_int, _c.c_int,
+                                                  ctypes.POINTER(_c.c_int), ctypes.POINTER(_c.c_int)]
+        L.stencil_tessellation_counts.restype = _c.c_int
         L.stencil_plan_destroy.argtypes = [_vp]
         L.stencil_plan_destroy.restype = None
         L.stencil_status_string.argtypes = [_c.c_int]
@@ -262,3 +266,12 @@ def run_1d_noalloc(x, y, coeffs, T: int, stream=None):
 
 def status_string(code: int) -> str:
     return lib().stencil_status_string(int(code)).decode()
+
+
+def tessellation_counts(W: int, b: int, R: int):
+    """(stage-1, stage-2) steps per point of one tile; host only."""
+    s1 = (_c.c_int * W)()
+    s2 = (_c.c_int * W)()
+    _check(lib().stencil_tessellation_counts(int(W), int(b), int(R), s1, s2),
+           "stencil_tessellation_counts")
+    return list(s1), list(s2)

@@ -29,11 +29,12 @@ namespace sg {
 
 namespace {
 
-constexpr const char *kLibVersion = "5";
+constexpr const char *kLibVersion = "6";
 
 struct Cand {
     int engine;  // 0 CUDA core, 1 tensor core
     int m, b, ty;
+    int tess;    // 1D: exact tessellate tiling instead of overlapped tiles
 };
 
 uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull)
@@ -85,10 +86,12 @@ bool cache_lookup(const std::string &key, Cand *c)
     const std::string needle = "\"key\": \"" + key + "\"";
     while (fgets(line, sizeof(line), f)) {
         if (!strstr(line, needle.c_str())) continue;
-        Cand t;
+        Cand t{0, 1, 1, 0, 0};
         const char *q = strstr(line, "\"engine\": ");
         if (q && sscanf(q, "\"engine\": %d, \"m\": %d, \"b\": %d, \"tile_y\": %d", &t.engine, &t.m,
                         &t.b, &t.ty) == 4) {
+            const char *ts = strstr(line, "\"tess\": ");
+            if (ts) sscanf(ts, "\"tess\": %d", &t.tess);
             *c = t;  // the last entry for a key wins
             found = true;
         }
@@ -103,8 +106,8 @@ void cache_store(const std::string &key, const Cand &c, double gstencil)
     if (path.empty()) return;
     FILE *f = fopen(path.c_str(), "a");
     if (!f) return;
-    fprintf(f, "{\"key\": \"%s\", \"engine\": %d, \"m\": %d, \"b\": %d, \"tile_y\": %d, \"gstencil_s\": %.1f}\n",
-            key.c_str(), c.engine, c.m, c.b, c.ty, gstencil);
+    fprintf(f, "{\"key\": \"%s\", \"engine\": %d, \"m\": %d, \"b\": %d, \"tile_y\": %d, \"tess\": %d, \"gstencil_s\": %.1f}\n",
+            key.c_str(), c.engine, c.m, c.b, c.ty, c.tess, gstencil);
     fclose(f);
 }
 
@@ -157,12 +160,13 @@ void tune_cache_put(const std::string &key, const std::string &value)
 stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
 {
     const std::string key = cache_key(p);
-    Cand best{0, 1, 1, 0};
+    Cand best{0, 1, 1, 0, 0};
     if (cache_lookup(key, &best)) {
         p->tuned_engine = best.engine;
         p->tuned_m = best.m;
         p->tuned_b = best.b;
         p->tuned_ty = best.ty;
+        p->tuned_tess = best.tess;
         return STENCIL_OK;
     }
     // candidate list
@@ -182,11 +186,17 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
             // (2m+1)/m multiply-adds per step but saves m-1 shared-memory
             // round trips, and FP64 in particular is bound by the former
             if (sweep1d_supported(R, p->dtype == STENCIL_F64))
-                for (int b : {16, 32, 64}) cands.push_back({0, m, b, 0});
+                for (int b : {16, 32, 64}) {
+                    cands.push_back({0, m, b, 0, 0});
+                    // exact tessellate tiling (Section 3.4) of the same passes
+                    const int w = p->dtype == STENCIL_F64 ? 2048 : 4096;
+                    if (tess1d_fits(p->nx, w, std::min<int64_t>(b, 48 / m + 1), R))
+                        cands.push_back({0, m, b, 0, 1});
+                }
         } else if (p->ndim == 3) {
-            if (sweep3d_supported(p->r, m, p->pattern)) cands.push_back({0, m, 1, 0});
+            if (sweep3d_supported(p->r, m, p->pattern)) cands.push_back({0, m, 1, 0, 0});
             if (sweep3d_tb_supported(p->r, m, p->pattern) && 2 * R <= std::min(kGhost, nmin))
-                cands.push_back({0, m, 2, 0});
+                cands.push_back({0, m, 2, 0, 0});
         } else {
             // a direct kernel, or the counterpart form of c^(m) (which also
             // reaches the folds with no direct kernel, m = 6 and 8)
@@ -196,12 +206,12 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
                 for (int b : {1, 2, 3, 4, 6, 8})
                     if (b * R <= std::min(kGhost, nmin) && (m > 1 || b <= 8))
                         for (int ty : {32, 64, 96, 128, 160})
-                            if (ty + 2 * b * R <= 256) cands.push_back({0, m, b, ty});
+                            if (ty + 2 * b * R <= 256) cands.push_back({0, m, b, ty, 0});
             if (m > 1 && p->precision != STENCIL_PREC_FP32 && tc2d_supported(R))
-                cands.push_back({1, m, 1, 0});
+                cands.push_back({1, m, 1, 0, 0});
         }
     }
-    if (cands.empty()) cands.push_back({0, 1, 1, 0});
+    if (cands.empty()) cands.push_back({0, 1, 1, 0, 0});
     // timing on scratch copies of a seeded-free grid (all ones keeps values finite)
     const size_t esz = p->dtype == STENCIL_F64 ? 8 : 4;
     const size_t npts = (size_t)p->nx * p->ny * p->nz;
@@ -218,6 +228,7 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int saved_prec = p->precision, saved_b = p->block_b, saved_ty = p->tile_y;
+    const int saved_tess = p->tessellate;
     const int saved_graph = p->use_graph;
     p->use_graph = 0;  // tuning runs are not worth capturing
     const int64_t T = 48;
@@ -226,6 +237,7 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
         p->precision = c.engine == 1 ? (saved_prec ? saved_prec : STENCIL_PREC_BF16X3) : STENCIL_PREC_FP32;
         p->block_b = c.b;
         p->tile_y = c.ty;
+        p->tessellate = c.tess;
         stencil_status_t st = STENCIL_OK;
         auto once = [&]() {
             if (p->ndim == 1) return run1d(p, din, dout, T, c.m, s);
@@ -249,6 +261,7 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     p->precision = saved_prec;
     p->block_b = saved_b;
     p->tile_y = saved_ty;
+    p->tessellate = saved_tess;
     p->use_graph = saved_graph;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -259,6 +272,7 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     p->tuned_m = best.m;
     p->tuned_b = best.b;
     p->tuned_ty = best.ty;
+    p->tuned_tess = best.tess;
     cache_store(key, best, best_rate);
     return STENCIL_OK;
 }

@@ -179,11 +179,31 @@ struct Sweep1DArgs {
 bool sweep1d_supported(int R, bool f64);
 cudaError_t launch_sweep1d(int R, bool f64, const Sweep1DArgs &a, cudaStream_t s);
 
+// ---- 1D exact tessellate tiling (k_tess1d.cu, tess1d.h) --------------------
+struct Tess1DArgs {
+    const void *src;
+    void *dst;
+    void *par0, *par1;  // the two Jacobi arrays (n points each): edge values between stages
+    long long n;
+    int W;              // tile width; the last tile also takes n mod W
+    int ntiles;         // max(1, n / W)
+    int wmax;           // widest tile
+    int b;              // steps per pass
+    double c[2 * kMaxR1D + 1];
+};
+// Whether b steps of radius R tessellate n points in tiles of W.
+bool tess1d_fits(long long n, int W, int b, int R);
+// Both stages of one pass (two launches); radii as sweep1d_supported.
+cudaError_t launch_tess1d(int R, bool f64, const Tess1DArgs &a, cudaStream_t s);
+
 // ---- layout conversion, coefficient folding, error reduction --------------
 // src: the user's grid, rows src_py and planes src_pz elements apart (0 =
 // dense: nx and nx*ny).
+// mean_sum: when given, the grid is stored centred: every value minus
+// mu = (float)(mean_sum[0] * inv_n).
 cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_t s,
-                          int64_t src_py = 0, int64_t src_pz = 0);
+                          int64_t src_py = 0, int64_t src_pz = 0,
+                          const double *mean_sum = nullptr, double inv_n = 0.0);
 // One 2D grid's import within a batch: padded rows [row0, row0 + ny + 2 gw)
 // of the batch's row space.
 struct ImportJob {
@@ -193,12 +213,30 @@ struct ImportJob {
     int64_t src_py;  // row stride of the user's grid (elements)
     long long row0;
     int nx, ny, gw, vec4;
+    // centred storage (k_center.cu): the grid's FP64 sum (null: not centred),
+    // 1 / points, and the output the final bias mu * factor is added to
+    double *mean_sum;
+    double inv_n;
+    float *out;
+    int64_t out_py;
+    double factor;
 };
 ImportJob make_import_job(const Padded &P, const float *src, int gw, long long row0,
                           int64_t src_py = 0);
 // All jobs (device array, ordered by row0) in one launch; rows = the total.
 cudaError_t launch_import_batch(const ImportJob *d_jobs, int njobs, long long rows, cudaStream_t s);
 cudaError_t launch_export(const Padded &P, float *dst, cudaStream_t s);
+// Centred storage (k_center.cu).  acc[0] += the FP64 sum of a caller-layout grid.
+cudaError_t launch_grid_sum(const float *src, int nx, int ny, int nz, int64_t py, int64_t pz,
+                            double *acc, cudaStream_t s);
+// dst += (float)(mu * factor), mu = (float)(mean_sum[0] * inv_n), over a caller-layout grid.
+cudaError_t launch_add_bias(float *dst, int nx, int ny, int nz, int64_t py, int64_t pz,
+                            const double *mean_sum, double inv_n, double factor, cudaStream_t s);
+// The same two steps for every job of a batch (rows as for launch_import_batch).
+cudaError_t launch_grid_sum_batch(const ImportJob *d_jobs, int njobs, long long rows,
+                                  cudaStream_t s);
+cudaError_t launch_add_bias_batch(const ImportJob *d_jobs, int njobs, long long rows,
+                                  cudaStream_t s);
 // c^(m) by m-1 convolutions with c (FP64 on the GPU); work holds 2*(2mr+1)^ndim doubles.
 cudaError_t launch_fold_power(int ndim, int r, int m, const double *d_c, double *d_out,
                               double *d_work, cudaStream_t s);

@@ -23,9 +23,12 @@ __device__ __forceinline__ int wrap_idx(int v, int n)
 // row are copied element by element.
 __global__ void k_import(float *__restrict__ origin, int64_t py, int64_t pz, int nx, int ny,
                          int nz, int gwx, int gwy, int gwz, const float *__restrict__ src,
-                         int64_t src_py, int64_t src_pz, int vec4)
+                         int64_t src_py, int64_t src_pz, int vec4,
+                         const double *__restrict__ mean_sum, double inv_n)
 {
     const int wy = ny + 2 * gwy, wz = nz + 2 * gwz;
+    // centred storage: every value minus the grid mean, rounded to FP32 once
+    const float mu = mean_sum ? (float)(mean_sum[0] * inv_n) : 0.f;
     for (long long row = blockIdx.x; row < (long long)wy * wz; row += gridDim.x) {
         const int y = (int)(row % wy) - gwy;
         const int z = (int)(row / wy) - gwz;
@@ -35,13 +38,16 @@ __global__ void k_import(float *__restrict__ origin, int64_t py, int64_t pz, int
         if (vec4) {
             const float4 *s4 = reinterpret_cast<const float4 *>(srow);
             float4 *d4 = reinterpret_cast<float4 *>(drow);
-            for (int i = threadIdx.x; i < nx / 4; i += blockDim.x) d4[i] = s4[i];
+            for (int i = threadIdx.x; i < nx / 4; i += blockDim.x) {
+                const float4 v = s4[i];
+                d4[i] = make_float4(v.x - mu, v.y - mu, v.z - mu, v.w - mu);
+            }
         } else {
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) drow[i] = srow[i];
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) drow[i] = srow[i] - mu;
         }
         for (int i = threadIdx.x; i < 2 * gwx; i += blockDim.x) {
             const int x = i < gwx ? i - gwx : nx + (i - gwx);
-            drow[x] = srow[wrap_idx(x, nx)];
+            drow[x] = srow[wrap_idx(x, nx)] - mu;
         }
     }
 }
@@ -64,16 +70,20 @@ __global__ void k_import_batch(const ImportJob *__restrict__ jobs, int njobs, lo
         const int y = (int)(row - J.row0) - J.gw;
         const float *srow = J.src + wrap_idx(y, J.ny) * J.src_py;
         float *drow = J.origin + y * J.py;
+        const float mu = J.mean_sum ? (float)(J.mean_sum[0] * J.inv_n) : 0.f;
         if (J.vec4) {
             const float4 *s4 = reinterpret_cast<const float4 *>(srow);
             float4 *d4 = reinterpret_cast<float4 *>(drow);
-            for (int i = lane; i < J.nx / 4; i += 32) d4[i] = s4[i];
+            for (int i = lane; i < J.nx / 4; i += 32) {
+                const float4 v = s4[i];
+                d4[i] = make_float4(v.x - mu, v.y - mu, v.z - mu, v.w - mu);
+            }
         } else {
-            for (int i = lane; i < J.nx; i += 32) drow[i] = srow[i];
+            for (int i = lane; i < J.nx; i += 32) drow[i] = srow[i] - mu;
         }
         for (int i = lane; i < 2 * J.gw; i += 32) {
             const int x = i < J.gw ? i - J.gw : J.nx + (i - J.gw);
-            drow[x] = srow[wrap_idx(x, J.nx)];
+            drow[x] = srow[wrap_idx(x, J.nx)] - mu;
         }
     }
 }
@@ -206,7 +216,7 @@ int sm_count()
 }  // namespace
 
 cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_t s,
-                          int64_t src_py, int64_t src_pz)
+                          int64_t src_py, int64_t src_pz, const double *mean_sum, double inv_n)
 {
     const int gwx = gw, gwy = P.ndim >= 2 ? gw : 0, gwz = P.ndim >= 3 ? gw : 0;
     if (src_py <= 0) src_py = P.nx;
@@ -218,7 +228,7 @@ cudaError_t launch_import(const Padded &P, const float *src, int gw, cudaStream_
     const long long rows = (long long)(P.ny + 2 * gwy) * (P.nz + 2 * gwz);
     const int grid = (int)std::min<long long>(rows, (long long)sm_count() * 16);
     k_import<<<grid, 256, 0, s>>>(P.origin, P.py, P.pz, P.nx, P.ny, P.nz, gwx, gwy, gwz, src,
-                                  src_py, src_pz, vec4);
+                                  src_py, src_pz, vec4, mean_sum, inv_n);
     return cudaGetLastError();
 }
 
@@ -230,6 +240,11 @@ ImportJob make_import_job(const Padded &P, const float *src, int gw, long long r
     j.py = P.py;
     j.src = src;
     j.src_py = src_py > 0 ? src_py : P.nx;
+    j.mean_sum = nullptr;
+    j.inv_n = 0.0;
+    j.out = nullptr;
+    j.out_py = 0;
+    j.factor = 1.0;
     j.row0 = row0;
     j.nx = P.nx;
     j.ny = P.ny;

@@ -57,6 +57,9 @@ struct stencil_plan_s {
     int *d_status = nullptr;
     sg::Padded A, B;                          // 2D / 3D working grids
     void *d1a = nullptr, *d1b = nullptr;      // 1D working grids
+    void *d1p0 = nullptr, *d1p1 = nullptr;    // 1D tessellation: edge values between stages
+    int tessellate = 0;                       // 1D passes by exact tessellate tiling
+    int center = 1;                           // 2D/3D CUDA-core runs store the grid minus its mean
     void *stage_in = nullptr, *stage_out = nullptr;  // host-pointer staging
     double *d_acc = nullptr;                  // small FP64 reduction buffer
     std::map<int, uint16_t *> panels;         // tensor-core Toeplitz panels by m
@@ -90,8 +93,9 @@ struct stencil_plan_s {
     int last_tc_form = 0;  // tensor-core kernel of the last tensor-core run (1 or 2)
     int last_ty = 0;  // tile height of the last 2D CUDA-core run's first pass
     int last_cp = 0;  // counterpart terms of the last 2D CUDA-core run's folded passes (0 = direct)
+    int last_tess = 0;  // 1 if the last 1D run's folded passes used exact tessellate tiling
     // autotuner choice for fold_m = 0: m, b, tile_y, engine (m = 0: not tuned yet)
-    int tuned_m = 0, tuned_b = 0, tuned_ty = 0, tuned_engine = 0;
+    int tuned_m = 0, tuned_b = 0, tuned_ty = 0, tuned_engine = 0, tuned_tess = 0;
 };
 
 namespace sg {
@@ -155,6 +159,15 @@ stencil_status_t plan_counterparts(stencil_plan_s *p, int m, const CpFactor **ou
 bool tune_cache_get(const std::string &key, std::string *value);
 void tune_cache_put(const std::string &key, const std::string &value);
 void ensure_device_facts(stencil_plan_s *p);
+// Centred storage of a CUDA-core 2D/3D run (k_center.cu): the device FP64
+// slot the input's sum goes to, 1 / points, and (sum c)^T, the factor of the
+// mean over the run.
+struct CentredRun {
+    bool on;
+    double *sum;
+    double inv_n, factor;
+};
+CentredRun centred_run(stencil_plan_s *p, int64_t T);
 
 // Runs enqueue(stream, &kernels) on stream s.  With graphs enabled and s not
 // itself being captured, the work is captured once per key on a private

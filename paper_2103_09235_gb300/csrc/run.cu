@@ -4,6 +4,7 @@
 // encode tensor maps and launch the sweep kernels in stream order, replaying
 // a captured CUDA graph for repeated runs.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -43,6 +44,18 @@ void ensure_device_facts(stencil_plan_s *p)
     if (p->sm_count <= 0) p->sm_count = 1;
 }
 
+CentredRun centred_run(stencil_plan_s *p, int64_t T)
+{
+    CentredRun c;
+    c.on = p->center != 0;
+    c.sum = p->d_acc + 1;  // d_acc[0] belongs to the tensor-core path's own centring
+    c.inv_n = 1.0 / ((double)p->nx * p->ny * p->nz);
+    double sc = 0.0;
+    for (double v : p->coeffs) sc += v;
+    c.factor = pow(sc, (double)T);  // the mean's gain over T steps: (sum c)^T
+    return c;
+}
+
 void clear_graphs(stencil_plan_s *p)
 {
     for (auto &kv : p->graphs) cudaGraphExecDestroy(kv.second.exec);
@@ -58,6 +71,7 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
         int b;
         ~RestoreB() { p->block_b = b; }
     } restore_b{p, saved_b};
+    const bool auto_fold = m == 0;
     if (m == 0) {
         if (p->tuned_m == 0 && p->autotune) {
             stencil_status_t st = autotune2d(p, s);
@@ -66,6 +80,7 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
         m = p->tuned_m > 0 ? p->tuned_m : 1;
         if (p->block_b == 0 && p->tuned_b > 0) p->block_b = p->tuned_b;
     }
+    const bool use_tess = auto_fold ? p->tuned_tess != 0 : p->tessellate != 0;
     const bool f64 = p->dtype == STENCIL_F64;
     const size_t esz = f64 ? 8 : 4;
     const int R = m * p->r;
@@ -95,6 +110,19 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
     std::vector<Pass> passes;
     for (int64_t d = 0; d < q; d += bsteps) passes.push_back({m, (int)std::min<int64_t>(bsteps, q - d)});
     for (int64_t d = 0; d < rem; d += bsteps) passes.push_back({1, (int)std::min<int64_t>(bsteps, rem - d)});
+    // passes that tessellate exactly (Section 3.4) where their b steps fit the tile
+    std::vector<char> tess_pass(passes.size(), 0);
+    bool any_tess = false;
+    for (size_t i = 0; i < passes.size(); ++i) {
+        tess_pass[i] = use_tess && tess1d_fits(p->nx, tile, passes[i].b, passes[i].m * p->r);
+        any_tess = any_tess || tess_pass[i];
+    }
+    if (any_tess && !p->d1p0) {
+        cudaError_t e = cudaMalloc(&p->d1p0, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&p->d1p1, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "1D tessellation scratch");
+        p->scratch_bytes += 2 * bytes;
+    }
 
     auto enqueue = [&](cudaStream_t st_, int *nl) -> stencil_status_t {
         const void *src = in;
@@ -110,33 +138,54 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
             const bool last = i + 1 == passes.size();
             void *dst = last ? out : bufs[nb];
             if (!last && dst == src) dst = bufs[nb ^ 1];
-            Sweep1DArgs a;
-            a.src = src;
-            a.dst = dst;
-            a.n = p->nx;
-            a.tile = tile;
-            a.b = ps.b;
             const std::vector<double> &c = ps.m == m ? *cm : *c1;
+            double wts[2 * kMaxR1D + 1];
             if (f64) {
-                for (size_t k = 0; k < c.size(); ++k) a.c[k] = c[k];
+                for (size_t k = 0; k < c.size(); ++k) wts[k] = c[k];
             } else {
                 float w[2 * kMaxR1D + 1];
                 round_f32_mass(c.data(), c.size(), c.size() / 2, w);
-                for (size_t k = 0; k < c.size(); ++k) a.c[k] = (double)w[k];
+                for (size_t k = 0; k < c.size(); ++k) wts[k] = (double)w[k];
             }
-            cudaError_t e = launch_sweep1d(ps.m * p->r, f64, a, st_);
+            cudaError_t e;
+            if (tess_pass[i]) {
+                Tess1DArgs t;
+                t.src = src;
+                t.dst = dst;
+                t.par0 = p->d1p0;
+                t.par1 = p->d1p1;
+                t.n = p->nx;
+                t.W = tile;
+                t.ntiles = (int)std::max<int64_t>(1, p->nx / tile);
+                t.wmax = (int)(p->nx - (int64_t)(t.ntiles - 1) * tile);
+                t.b = ps.b;
+                for (size_t k = 0; k < c.size(); ++k) t.c[k] = wts[k];
+                e = launch_tess1d(ps.m * p->r, f64, t, st_);
+                *nl += 2;
+            } else {
+                Sweep1DArgs a;
+                a.src = src;
+                a.dst = dst;
+                a.n = p->nx;
+                a.tile = tile;
+                a.b = ps.b;
+                for (size_t k = 0; k < c.size(); ++k) a.c[k] = wts[k];
+                e = launch_sweep1d(ps.m * p->r, f64, a, st_);
+                *nl += 1;
+            }
             if (e != cudaSuccess) return cuda_fail(e, "1D sweep launch");
-            *nl += 1;
             src = dst;
             nb ^= 1;
         }
         return STENCIL_OK;
     };
-    std::vector<int64_t> key = {1, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, bsteps};
+    std::vector<int64_t> key = {1, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, bsteps,
+                                any_tess ? 1 : 0};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = bsteps;
     p->last_engine = 0;
+    p->last_tess = (!passes.empty() && tess_pass[0]) ? 1 : 0;
     return st;
 }
 
@@ -315,9 +364,18 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
         if (!first_ty) first_ty = cfg.ty;
     }
     const bool out_vec4 = grid_vec4(p, out);
+    const CentredRun cr = centred_run(p, T);
 
     auto enqueue = [&](cudaStream_t st_, int *nl) -> stencil_status_t {
-        cudaError_t e = launch_import(p->A, in, gw, st_, p->pitch_y);
+        cudaError_t e = cudaSuccess;
+        if (cr.on) {
+            e = cudaMemsetAsync(cr.sum, 0, sizeof(double), st_);
+            if (e == cudaSuccess)
+                e = launch_grid_sum(in, p->nx, p->ny, 1, p->pitch_y, p->pitch_z, cr.sum, st_);
+            if (e != cudaSuccess) return cuda_fail(e, "grid sum launch");
+            *nl += 1;
+        }
+        e = launch_import(p->A, in, gw, st_, p->pitch_y, 0, cr.on ? cr.sum : nullptr, cr.inv_n);
         if (e != cudaSuccess) return cuda_fail(e, "import launch");
         *nl += 1;
         const Padded *cur = &p->A, *oth = &p->B;
@@ -333,10 +391,17 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
             *nl += 1;
             std::swap(cur, oth);
         }
+        if (cr.on) {
+            e = launch_add_bias(out, p->nx, p->ny, 1, p->pitch_y, p->pitch_z, cr.sum, cr.inv_n,
+                                cr.factor, st_);
+            if (e != cudaSuccess) return cuda_fail(e, "bias launch");
+            *nl += 1;
+        }
         return STENCIL_OK;
     };
     std::vector<int64_t> key = {2, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, b,
-                                p->tile_y, p->wait_ms, p->fault_withhold_copy, cpm->k, cp1->k};
+                                p->tile_y, p->wait_ms, p->fault_withhold_copy, cpm->k, cp1->k,
+                                cr.on ? 1 : 0};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = b;

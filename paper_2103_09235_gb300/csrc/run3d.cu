@@ -110,8 +110,18 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
     int gw = p->r;
     for (auto &x : passes) gw = std::max(gw, x.first * x.second * p->r);
     const bool out_vec4 = grid_vec4(p, out);
+    const CentredRun cr = centred_run(p, T);
     auto enqueue = [&](cudaStream_t st_, int *nl) -> stencil_status_t {
-        cudaError_t e = launch_import(p->A, in, gw, st_, p->pitch_y, p->pitch_z);
+        cudaError_t e = cudaSuccess;
+        if (cr.on) {
+            e = cudaMemsetAsync(cr.sum, 0, sizeof(double), st_);
+            if (e == cudaSuccess)
+                e = launch_grid_sum(in, p->nx, p->ny, p->nz, p->pitch_y, p->pitch_z, cr.sum, st_);
+            if (e != cudaSuccess) return cuda_fail(e, "grid sum launch");
+            *nl += 1;
+        }
+        e = launch_import(p->A, in, gw, st_, p->pitch_y, p->pitch_z, cr.on ? cr.sum : nullptr,
+                          cr.inv_n);
         if (e != cudaSuccess) return cuda_fail(e, "import launch");
         *nl += 1;
         const Padded *cur = &p->A, *oth = &p->B;
@@ -126,10 +136,16 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
             *nl += 1;
             std::swap(cur, oth);
         }
+        if (cr.on) {
+            e = launch_add_bias(out, p->nx, p->ny, p->nz, p->pitch_y, p->pitch_z, cr.sum,
+                                cr.inv_n, cr.factor, st_);
+            if (e != cudaSuccess) return cuda_fail(e, "bias launch");
+            *nl += 1;
+        }
         return STENCIL_OK;
     };
     std::vector<int64_t> key = {4, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, b,
-                                p->wait_ms, p->fault_withhold_copy};
+                                p->wait_ms, p->fault_withhold_copy, cr.on ? 1 : 0};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = b;

@@ -93,6 +93,7 @@ struct BatchBuild {
     int njobs = 0;
     long long import_rows = 0;
     int tile_y = 0;
+    double *d_sums = nullptr;  // per-job FP64 grid sums (centred storage), null if none
 };
 
 // Flattens the batch with per-grid (m, b) choices and a tile height of at
@@ -225,28 +226,41 @@ stencil_status_t flatten_batch(int n, stencil_plan_s *const *plans, const void *
         for (auto &G : gp)
             if (r < G.npass)
                 for (int t = 0; t < G.ntiles; ++t) items.push_back({G.first_pass + r, t});
-    // imports of every grid that steps, in one launch
+    // imports of every grid that steps, in one launch; grids of centred plans
+    // are stored minus their mean (an FP64 sum per grid in the sums block)
+    // and get mean * (sum c)^T added to their outputs at the end
     std::vector<ImportJob> jobs;
     long long import_rows = 0;
+    bool any_centred = false;
     for (const GridPlan &G : gp) {
         if (G.T == 0) continue;
-        jobs.push_back(make_import_job(G.p->A, G.in, G.gw, import_rows, G.p->pitch_y));
+        ImportJob j = make_import_job(G.p->A, G.in, G.gw, import_rows, G.p->pitch_y);
+        if (G.p->center) {
+            double sc = 0.0;
+            for (double v : G.p->coeffs) sc += v;
+            j.inv_n = 1.0 / ((double)G.p->nx * G.p->ny);
+            j.out = G.out;
+            j.out_py = G.p->pitch_y;
+            j.factor = pow(sc, (double)G.T);
+            any_centred = true;  // mean_sum is set once the device block exists
+        }
+        jobs.push_back(j);
         import_rows += G.p->ny + 2 * G.gw;
     }
-    // one device block: maps | passes | items | coefs | import jobs | done | next
+    // one device block: maps | passes | items | coefs | import jobs | sums | done | next
     const size_t o_maps = 0;
     const size_t o_pass = round_up((int)(maps.size() * sizeof(CUtensorMap)), 256);
     const size_t o_item = o_pass + round_up((int)(passes.size() * sizeof(BatchPass) + 1), 256);
     const size_t o_coef = o_item + round_up((int)(items.size() * sizeof(BatchItem) + 1), 256);
     const size_t o_jobs = o_coef + round_up((int)(coefs.size() * sizeof(float) + 1), 256);
-    const size_t o_done = o_jobs + round_up((int)(jobs.size() * sizeof(ImportJob) + 1), 256);
+    const size_t o_sums = o_jobs + round_up((int)(jobs.size() * sizeof(ImportJob) + 1), 256);
+    const size_t o_done = o_sums + round_up((int)(jobs.size() * sizeof(double) + 1), 256);
     const size_t total = o_done + (passes.size() + 1) * sizeof(int) + 256;
     std::vector<unsigned char> host(total, 0);
     if (!maps.empty()) memcpy(host.data() + o_maps, maps.data(), maps.size() * sizeof(CUtensorMap));
     if (!passes.empty()) memcpy(host.data() + o_pass, passes.data(), passes.size() * sizeof(BatchPass));
     if (!items.empty()) memcpy(host.data() + o_item, items.data(), items.size() * sizeof(BatchItem));
     if (!coefs.empty()) memcpy(host.data() + o_coef, coefs.data(), coefs.size() * sizeof(float));
-    if (!jobs.empty()) memcpy(host.data() + o_jobs, jobs.data(), jobs.size() * sizeof(ImportJob));
     const size_t smem = batched_smem_bytes(buf_floats, nwork, nstage);
     if (smem > (size_t)p0->max_smem) {
         set_error("stencil_run_batched: shared memory");
@@ -254,6 +268,10 @@ stencil_status_t flatten_batch(int n, stencil_plan_s *const *plans, const void *
     }
     unsigned char *dev = nullptr;
     cudaError_t e = cudaMalloc(&dev, total);
+    double *d_sums = reinterpret_cast<double *>(dev + o_sums);
+    for (size_t k = 0; k < jobs.size(); ++k)
+        if (jobs[k].out) jobs[k].mean_sum = d_sums + k;
+    if (!jobs.empty()) memcpy(host.data() + o_jobs, jobs.data(), jobs.size() * sizeof(ImportJob));
     if (e == cudaSuccess) e = cudaMemcpy(dev, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (dev) cudaFree(dev);
@@ -281,6 +299,7 @@ stencil_status_t flatten_batch(int n, stencil_plan_s *const *plans, const void *
     bb->counters = (passes.size() + 1) * sizeof(int);
     bb->d_jobs = reinterpret_cast<const ImportJob *>(dev + o_jobs);
     bb->njobs = (int)jobs.size();
+    bb->d_sums = any_centred ? d_sums : nullptr;
     bb->import_rows = import_rows;
     bb->tile_y = tile_y;
     return STENCIL_OK;
@@ -295,6 +314,12 @@ stencil_status_t enqueue_batch(const BatchBuild &bb, cudaStream_t st_, int *nl)
         const cudaError_t err = copy_grid(G.p, G.out, G.in, cudaMemcpyDeviceToDevice, st_);
         if (err != cudaSuccess) return cuda_fail(err, "batched copy");
     }
+    if (bb.njobs > 0 && bb.d_sums) {
+        cudaError_t err = cudaMemsetAsync(bb.d_sums, 0, sizeof(double) * bb.njobs, st_);
+        if (err == cudaSuccess) err = launch_grid_sum_batch(bb.d_jobs, bb.njobs, bb.import_rows, st_);
+        if (err != cudaSuccess) return cuda_fail(err, "batched grid sums");
+        *nl += 1;
+    }
     if (bb.njobs > 0) {
         const cudaError_t err = launch_import_batch(bb.d_jobs, bb.njobs, bb.import_rows, st_);
         if (err != cudaSuccess) return cuda_fail(err, "batched import");
@@ -304,6 +329,11 @@ stencil_status_t enqueue_batch(const BatchBuild &bb, cudaStream_t st_, int *nl)
         cudaError_t err = cudaMemsetAsync(bb.a.done, 0, bb.counters, st_);
         if (err == cudaSuccess) err = launch_batched(bb.a, bb.grid, bb.smem, st_);
         if (err != cudaSuccess) return cuda_fail(err, "batched launch");
+        *nl += 1;
+    }
+    if (bb.njobs > 0 && bb.d_sums) {
+        const cudaError_t err = launch_add_bias_batch(bb.d_jobs, bb.njobs, bb.import_rows, st_);
+        if (err != cudaSuccess) return cuda_fail(err, "batched bias");
         *nl += 1;
     }
     return STENCIL_OK;
@@ -507,6 +537,7 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
         key.push_back(T[g]);
         key.push_back(fold_m ? fold_m[g] : 0);
         key.push_back(plans[g]->block_b);
+        key.push_back(plans[g]->center);
     }
     key.push_back(p0->wait_ms);
     key.push_back(p0->fault_withhold_dep);

@@ -386,6 +386,12 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "tc_tma_store")) {
         if (v != 0 && v != 1) goto bad;
         p->tc_tma_store = (int)v;
+    } else if (!strcmp(key, "center")) {
+        if (v != 0 && v != 1) goto bad;
+        p->center = (int)v;
+    } else if (!strcmp(key, "tessellate")) {
+        if (v != 0 && v != 1) goto bad;
+        p->tessellate = (int)v;
     } else if (!strcmp(key, "graph")) {
         if (v != 0 && v != 1) goto bad;
         p->use_graph = (int)v;
@@ -415,6 +421,7 @@ stencil_status_t stencil_plan_get(stencil_plan_t p, const char *key, int64_t *va
     else if (!strcmp(key, "last_engine")) *value = p->last_engine;
     else if (!strcmp(key, "last_tc_form")) *value = p->last_tc_form;
     else if (!strcmp(key, "last_cp")) *value = p->last_cp;
+    else if (!strcmp(key, "last_tess")) *value = p->last_tess;
     else if (!strcmp(key, "launches")) *value = p->launches;
     else if (!strcmp(key, "scratch_bytes")) *value = (int64_t)p->scratch_bytes;
     else {
@@ -563,6 +570,8 @@ void stencil_plan_destroy(stencil_plan_t p)
     if (p->B.alloc) cudaFree(p->B.alloc);
     if (p->d1a) cudaFree(p->d1a);
     if (p->d1b) cudaFree(p->d1b);
+    if (p->d1p0) cudaFree(p->d1p0);
+    if (p->d1p1) cudaFree(p->d1p1);
     if (p->stage_in) cudaFree(p->stage_in);
     if (p->stage_out) cudaFree(p->stage_out);
     for (auto &kv : p->panels) cudaFree(kv.second);

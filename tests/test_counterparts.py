@@ -164,3 +164,4 @@ def test_scalar_and_sparse_weights(blib, oracle_mod):
     K, u, v = blib.fold_counterparts(full, 9)
     assert K == np.linalg.matrix_rank(full) == 9
     assert np.max(np.abs(rebuilt(u, v) - full)) < 1e-13
+

@@ -130,6 +130,46 @@ def test_sweep1d_parity(env, n, T, m, dt):
         check(y, ref)
 
 
+# (n, T, m, b, dtype): exact tessellate tiling of the 1D passes (Section 3.4)
+CASES_TESS = [
+    (1 << 20, 100, 16, 32, "f64"), (1 << 20, 100, 6, 64, "f32"), (1 << 20, 100, 1, 32, "f32"),
+    (65539, 200, 4, 16, "f32"),   # ragged: the last tile takes n mod 4096 more points
+    (5000, 77, 2, 8, "f64"),      # two tiles, the second 2952 points wide
+    (3000, 40, 3, 10, "f64"),     # one tile: its boundary wraps around the line
+    (9000, 61, 16, 7, "f32"), (4100, 33, 12, 5, "f64"),
+]
+
+
+@pytest.mark.parametrize("n,T,m,b,dt", CASES_TESS)
+def test_sweep1d_tessellated(env, n, T, m, b, dt):
+    """Triangles then inverted triangles: every pass that fits the tile runs
+    in the two-stage exact tessellation and the result matches the oracle
+    (FP64 to 1e-12); the first pass reports that it was tessellated."""
+    torch, binding, oracle = env
+    c = synth.heat1d_coeffs() if n % 2 == 0 else synth.dyadic_coeffs(5, 1, 1, "box")
+    npdt = np.float64 if dt == "f64" else np.float32
+    x = synth.grid(3100 + n, (n,), npdt)
+    plan = binding.Plan((n,), c, dt).set_option("tessellate", 1).set_option("block_b", b)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, T, fold_m=m)
+    plan.sync()
+    assert plan.get("last_tess") == 1
+    ref = oracle.run(x.astype(np.float64), c, T)
+    y = yd.cpu().numpy()
+    if dt == "f64":
+        check(y, ref, tol=1e-12, abs_tol=1e-12)
+    else:
+        check(y, ref)
+    plan.run(xd, xd, T, fold_m=m)  # in place
+    plan.sync()
+    if dt == "f64":
+        check(xd.cpu().numpy(), ref, tol=1e-12, abs_tol=1e-12)
+    else:
+        check(xd.cpu().numpy(), ref)
+    plan.close()
+
+
 def test_sweep1d_radius2(env):
     _, _, oracle = env
     c = synth.dyadic_coeffs(9, 1, 2, "box")
