@@ -459,17 +459,42 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    double best = time_batch(n, plans, in, sout.data(), T, ms, bs, ty, s, e0, e1);
+    // each timing is the best of two launches, and a class is timed on its
+    // own grids only, so that its choice is not lost in the rest of the batch
+    auto best_of_two = [&](int nn, stencil_plan_s *const *pl, const void *const *ii,
+                           void *const *oo, const int64_t *tt, const std::vector<int> &mm,
+                           const std::vector<int> &bb_, int ty_) {
+        const double t0 = time_batch(nn, pl, ii, oo, tt, mm, bb_, ty_, s, e0, e1);
+        const double t1 = time_batch(nn, pl, ii, oo, tt, mm, bb_, ty_, s, e0, e1);
+        return (t0 > 0 && t1 > 0) ? std::min(t0, t1) : -1.0;
+    };
     for (auto &kv : classes) {
         const ClassKey &k = kv.first;
-        const int g0 = kv.second[0];
-        int bm = ms[g0], bbst = bs[g0];
+        const std::vector<int> &gs = kv.second;
+        if (!(ms[gs[0]] > 0)) continue;
+        std::vector<stencil_plan_s *> cp;
+        std::vector<const void *> ci;
+        std::vector<void *> co;
+        std::vector<int64_t> ct;
+        for (int g : gs) {
+            cp.push_back(plans[g]);
+            ci.push_back(in[g]);
+            co.push_back(sout[g]);
+            ct.push_back(T[g]);
+        }
+        std::vector<int> cm(gs.size()), cb(gs.size());
+        int bm = ms[gs[0]], bbst = bs[gs[0]];
+        double best = -1.0;
         for (int m = 1; m <= 4; ++m) {
-            if (!batched_variant_supported(k.r, m, k.pattern) || clamp_m(plans[g0], m) != m) continue;
+            if (!batched_variant_supported(k.r, m, k.pattern) || clamp_m(plans[gs[0]], m) != m)
+                continue;
             for (int b = 1; b <= 3; ++b) {
-                if (m == bm && b == bbst) continue;
-                apply(k, m, b);
-                const double t = time_batch(n, plans, in, sout.data(), T, ms, bs, ty, s, e0, e1);
+                for (size_t i = 0; i < gs.size(); ++i) {
+                    cm[i] = clamp_m(cp[i], m);
+                    cb[i] = clamp_b(cp[i], cm[i], b);
+                }
+                const double t = best_of_two((int)gs.size(), cp.data(), ci.data(), co.data(),
+                                             ct.data(), cm, cb, ty);
                 if (t > 0 && (best < 0 || t < best)) {
                     best = t;
                     bm = m;
@@ -482,9 +507,9 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
         snprintf(v, sizeof(v), "%d %d", bm, bbst);
         tune_cache_put(class_cache_key(k, prop.name), v);
     }
-    for (int t : {64, 96, 128}) {
-        if (t == ty) continue;
-        const double tt = time_batch(n, plans, in, sout.data(), T, ms, bs, t, s, e0, e1);
+    double best = -1.0;
+    for (int t : {128, 96, 64}) {
+        const double tt = best_of_two(n, plans, in, sout.data(), T, ms, bs, t);
         if (tt > 0 && (best < 0 || tt < best)) {
             best = tt;
             ty = t;
