@@ -68,12 +68,14 @@ typedef enum {
  *   shape     ndim extents, C order (shape[0] slowest); each >= 2*radius+1.
  *   radius    r >= 1; r <= 4 (CUDA-core sweeps take folded radius m*r <= 16).
  *   coeffs    (2r+1)^ndim doubles as described above; copied, not retained.
- *   dtype     STENCIL_F32 for 1D/2D/3D; STENCIL_F64 for 1D only.
+ *   dtype     STENCIL_F32 or STENCIL_F64.  FP64 2D/3D grids run FP64 CUDA-core
+ *             sweeps (plain or folded, folded radius m*r <= 8 in 2D, <= 4 in
+ *             3D; the precision and tensor-core options do not apply to them).
  * The plan binds the CUDA device current at the call.  It computes the FP64
  * folded weights on that device on demand (Section 3.2) and owns all scratch
  * memory, which it allocates on first use.
- * Errors: INVALID_ARG for a bad argument, UNSUPPORTED for F64 in 2D/3D,
- * OOM / CUDA on allocation or device failures.
+ * Errors: INVALID_ARG for a bad argument, OOM / CUDA on allocation or device
+ * failures.
  */
 stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t *shape,
                               int radius, const double *coeffs, stencil_dtype_t dtype);

@@ -181,7 +181,10 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
                 cost[0] < cost[1])
                 continue;  // P = |C(E)| / |C(E_lambda)| < 1: folding is not profitable
         }
-        if (p->ndim == 1) {
+        if (p->dtype == STENCIL_F64 && p->ndim >= 2) {
+            // FP64 2D/3D: one sweep per launch, folds up to the kernel's radius
+            if (R <= (p->ndim == 3 ? kMaxRF64_3D : kMaxRF64_2D)) cands.push_back({0, m, 1, 0, 0});
+        } else if (p->ndim == 1) {
             // every fold the 1D kernel has (radius up to 16): a fold costs
             // (2m+1)/m multiply-adds per step but saves m-1 shared-memory
             // round trips, and FP64 in particular is bound by the former
@@ -241,6 +244,8 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
         stencil_status_t st = STENCIL_OK;
         auto once = [&]() {
             if (p->ndim == 1) return run1d(p, din, dout, T, c.m, s);
+            if (p->dtype == STENCIL_F64)
+                return run_f64nd(p, (const double *)din, (double *)dout, T, c.m, s);
             if (p->ndim == 3) return run3d(p, (const float *)din, (float *)dout, T, c.m, s);
             return run2d(p, (const float *)din, (float *)dout, T, c.m, s);
         };

@@ -179,6 +179,26 @@ struct Sweep1DArgs {
 bool sweep1d_supported(int R, bool f64);
 cudaError_t launch_sweep1d(int R, bool f64, const Sweep1DArgs &a, cudaStream_t s);
 
+// ---- FP64 2D/3D sweeps (k_sweep_f64.cu) -----------------------------------
+constexpr int kMaxRF64_2D = 8;  // folded radius limits of the FP64 sweep
+constexpr int kMaxRF64_3D = 4;
+struct SweepF64Args {
+    const double *src;
+    double *dst;
+    long long nx, ny, nz;
+    int64_t src_py, src_pz, dst_py, dst_pz;  // row and plane strides (elements)
+    int ndim, R;
+    int tz;              // output planes per CTA (3D)
+    int bx, by;          // CTAs along x and y
+    int ntaps_dense;     // (2R+1)^ndim
+    int nnz;             // nonzero weights
+    double c[kMaxTaps3D];  // weights, dense, axis order (z, y, x)
+};
+size_t sweep_f64_smem_bytes(int ndim, int R, int tz, int nnz);
+cudaError_t launch_sweep_f64(const SweepF64Args &a, cudaStream_t s);
+int sweep_f64_block_x();
+int sweep_f64_block_y();
+
 // ---- 1D exact tessellate tiling (k_tess1d.cu, tess1d.h) --------------------
 struct Tess1DArgs {
     const void *src;

@@ -140,6 +140,9 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
                        cudaStream_t s);
 stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
                        cudaStream_t s);
+// FP64 2D and 3D grids (k_sweep_f64.cu), plain or folded.
+stencil_status_t run_f64nd(stencil_plan_s *p, const double *in, double *out, int64_t T, int m,
+                           cudaStream_t s);
 stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s);
 
 void clear_graphs(stencil_plan_s *p);

@@ -243,10 +243,6 @@ stencil_status_t stencil_plan(stencil_plan_t *out_plan, int ndim, const int64_t 
         set_error("stencil_plan: unknown dtype");
         return STENCIL_ERR_INVALID_ARG;
     }
-    if (dtype == STENCIL_F64 && ndim != 1) {
-        set_error("stencil_plan: FP64 is supported for 1D grids only");
-        return STENCIL_ERR_UNSUPPORTED;
-    }
     for (int d = 0; d < ndim; ++d) {
         if (shape[d] < 2 * radius + 1 || shape[d] > (int64_t)1 << 30) {
             set_error("stencil_plan: extent %lld outside [2r+1, 2^30]", (long long)shape[d]);
@@ -544,6 +540,8 @@ stencil_status_t stencil_run(stencil_plan_t p, const void *in, void *out, int64_
         st = e == cudaSuccess ? STENCIL_OK : cuda_fail(e, "copy for T = 0");
     } else if (p->ndim == 1) {
         st = run1d(p, din_p, dout_p, T, fold_m, s);
+    } else if (p->dtype == STENCIL_F64) {
+        st = run_f64nd(p, (const double *)din_p, (double *)dout_p, T, fold_m, s);
     } else if (p->ndim == 2) {
         st = run2d(p, (const float *)din_p, (float *)dout_p, T, fold_m, s);
     } else {

@@ -51,7 +51,7 @@ def test_plan_rejects_bad_arguments_without_gpu(blib):
     assert L.stencil_plan(ctypes.byref(h), 2, shape, 0, cp, 0) == 1        # radius
     small = (ctypes.c_int64 * 2)(2, 8)
     assert L.stencil_plan(ctypes.byref(h), 2, small, 1, cp, 0) == 1        # extent < 2r+1
-    assert L.stencil_plan(ctypes.byref(h), 2, shape, 1, cp, 1) == 2        # FP64 2D unsupported
+    assert L.stencil_plan(ctypes.byref(h), 2, shape, 1, cp, 7) == 1        # unknown dtype
     assert L.stencil_plan(ctypes.byref(h), 2, shape, 1, None, 0) == 1
     assert "stencil_plan" in L.stencil_last_error().decode()
 
