@@ -437,6 +437,7 @@ VARIANTS = [
     ("box8192_T512_cuda_core_autotuned", "box8192", 0, {}, "f32"),
     ("box8192_T512_tc_bf16x3_m4", "box8192", 4, {"precision": 1}, "f32"),
     ("box8192_T512_tc_bf16x1_m4", "box8192", 4, {"precision": 2}, "f32"),
+    ("box8192_T512_tc_tf32x3_m4", "box8192", 4, {"precision": 3}, "f32"),
     ("box8192_T512_tc_bf16x3_m6", "box8192", 6, {"precision": 1}, "f32"),
     ("box8192_T512_tc_bf16x3_m8", "box8192", 8, {"precision": 1}, "f32"),
     ("box8192_T512_tc_bf16x1_m8", "box8192", 8, {"precision": 2}, "f32"),

@@ -58,7 +58,10 @@ typedef enum {
     STENCIL_PREC_FP32 = 0,    /* CUDA-core FP32 sweeps (default)                          */
     STENCIL_PREC_BF16X3 = 1,  /* folded 2D box on tcgen05: BF16 hi/lo split, 3 products,
                                  FP32 accumulation in tensor memory                        */
-    STENCIL_PREC_BF16X1 = 2   /* as BF16X3 with the hi*hi product only (error study)      */
+    STENCIL_PREC_BF16X1 = 2,  /* as BF16X3 with the hi*hi product only (error study)      */
+    STENCIL_PREC_TF32X3 = 3   /* as BF16X3 with TF32 hi/lo operands (kind::tf32): about 22
+                                 significant bits per operand pair instead of 16; folded
+                                 radius m*r <= 4                                           */
 } stencil_precision_t;
 
 /*

@@ -273,6 +273,7 @@ constexpr int kTcN = 32;
 constexpr int kTcK = 48;
 constexpr int kTcKC = kTcK / 8;                 // 16-byte K chunks
 constexpr int kTcMaxR = 8;
+constexpr int kTcMaxRTf32 = 4;                  // TF32 panels take twice the bytes
 constexpr int kTcPanelElems = 64 * kTcK;        // one row offset: C_hi (32 rows) over C_lo (32 rows)
 constexpr int kTcGroup = 4;                     // grouped form: row offsets per MMA
 constexpr int kTcOutRows = kTcM - (kTcGroup - 1);  // grouped form: output rows per tile
@@ -305,7 +306,10 @@ struct TC2DArgs {
     unsigned long long wait_ns;
 };
 bool tc2d_supported(int R);
-size_t tc2d_smem_bytes(int R, bool tma_store);
+bool tc2d_tf32_supported(int R);
+// tf32: TF32 hi/lo operands (kind::tf32) instead of BF16 hi/lo (kind::f16).
+size_t tc2d_smem_bytes(int R, bool tma_store, bool tf32 = false);
+size_t tc2d_panel_bytes(int R, bool tf32);
 // Grouped form (k_tc2d_grouped.cu): four row offsets per MMA, 125 output rows
 // of 32 columns per tile, direct stores.
 size_t tc2dg_smem_bytes(int R, int nstage);
@@ -316,12 +320,13 @@ size_t tc2dg_panel_elems(int R);
 double tc2dg_build_panels(const double *cm, int R, uint16_t *host_out);
 cudaError_t launch_tc2dg(const CUtensorMap &map, const TC2DArgs &a, int grid, size_t smem,
                          cudaStream_t s);
-// Builds the (2R+1) BF16 Toeplitz panels of folded weights cm ((2R+1)^2,
-// row-major (dy, dx)) with the hi/lo split and the mass correction; returns
-// the FP64 sum of cm, which the epilogue multiplies by mu.
-double tc2d_build_panels(const double *cm, int R, uint16_t *host_out);
+// Builds the (2R+1) Toeplitz panels (BF16, or TF32 with tf32) of folded
+// weights cm ((2R+1)^2, row-major (dy, dx)) with the hi/lo split and the mass
+// correction into host_out (tc2d_panel_bytes bytes); returns the FP64 sum of
+// cm, which the epilogue multiplies by mu.
+double tc2d_build_panels(const double *cm, int R, void *host_out, bool tf32);
 cudaError_t launch_tc2d(const CUtensorMap &map, const CUtensorMap &dmap, const TC2DArgs &a,
-                        int grid, size_t smem, cudaStream_t s);
+                        int grid, size_t smem, cudaStream_t s, bool tf32);
 cudaError_t launch_grid_mean(const float *origin, int nx, int ny, int64_t py, double *acc,
                              cudaStream_t s);
 

@@ -1,4 +1,5 @@
-// Folded 2D box sweep on the tcgen05 tensor cores (BF16 hi/lo, FP32 accumulate).
+// Folded 2D box sweep on the tcgen05 tensor cores: BF16 hi/lo (kind::f16) or
+// TF32 hi/lo (kind::tf32) operands, FP32 accumulation.
 //
 // One sweep applies the folded weights c^(m) (radius R = m*r, Section 3.2):
 //   out[y][x0+n] = sum_{a=-R..R} sum_k X[y+a][x0-R+k] * T_a[n][k],
@@ -11,14 +12,17 @@
 //
 // Tile: M = 128 grid rows (the MMA's M) x 32 output columns.  The FP32 tile
 // plus R halo rows arrives by TMA; converter warps subtract the grid mean mu,
-// split v = x - mu into v_hi = bf16(v) and v_lo = bf16(v - v_hi) and write both
-// in the no-swizzle K-major core-matrix layout, in which every row is 16 bytes
-// away from the next within a K chunk.  The operand "rows y+a" for offset a is
-// then the same matrix with its descriptor start moved by 16*(a+R) bytes, so
-// no shifted copies are made.  Per (a, K step) one MMA of N = 64 multiplies
-// v_hi by [T_a,hi ; T_a,lo] and one of N = 32 multiplies v_lo by T_a,hi; the
-// two halves of the accumulator are added in the epilogue together with
-// mu * sum(c).  Toeplitz panels stay resident in shared memory.
+// split v = x - mu into v_hi = rnd(v) and v_lo = rnd(v - v_hi) (rnd: BF16 or
+// TF32) and write both in the no-swizzle K-major core-matrix layout, in which
+// every row is 16 bytes away from the next within a 16-byte K chunk.  The
+// operand "rows y+a" for offset a is then the same matrix with its descriptor
+// start moved by 16*(a+R) bytes, so no shifted copies are made.  An MMA takes
+// 32 bytes of K per row (16 BF16 or 8 TF32 values); per (a, K step) one MMA of
+// N = 64 multiplies v_hi by [T_a,hi ; T_a,lo] and one of N = 32 multiplies
+// v_lo by T_a,hi; the two halves of the accumulator are added in the epilogue
+// together with mu * sum(c).  Toeplitz panels stay resident in shared memory.
+// TF32 operands take twice the bytes: its A operand is single-buffered so that
+// the panels of R <= 4 still fit, and it has no single-product variant.
 //
 // Warp roles (384 threads): warp 0 issues TMA loads, warp 1 owns tensor
 // memory and issues the MMAs (one thread), warps 4-7 convert, warps 8-11
@@ -26,6 +30,7 @@
 // runs out records a timeout, raises an abort flag that ends the other roles'
 // waits, lets in-flight copies and MMAs land, frees tensor memory and returns.
 #include <cuda_bf16.h>
+#include <string.h>
 
 #include <vector>
 
@@ -39,9 +44,50 @@ namespace {
 using namespace tcore;
 
 constexpr int NT = kTcThreads;
-constexpr int PANEL_BYTES = kTcPanelElems * 2;  // 6144
-constexpr int LBO_B = 64 * 16;                  // K-chunk stride of a panel (64 rows x 16 B)
-constexpr uint32_t TMEM_COLS = 128;             // two 64-column accumulators
+constexpr int LBO_B = 64 * 16;       // K-chunk stride of a panel (64 rows x 16 B)
+constexpr uint32_t TMEM_COLS = 128;  // two 64-column accumulators
+
+// Operand format: EB bytes per element (2: BF16, 4: TF32).
+template <int EB>
+struct Fmt {
+    static constexpr int KCH = kTcK * EB / 16;      // 16-byte K chunks per row of the window
+    static constexpr int KSTEPS = kTcK * EB / 32;   // MMAs per (row offset, term)
+    static constexpr int PANEL_BYTES = 64 * kTcK * EB;
+    static constexpr int NSA = EB == 2 ? 2 : 1;     // A-operand buffers
+};
+
+// kind::tf32 instruction descriptor: FP32 accumulator, TF32 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+template <int EB>
+__device__ __forceinline__ void mma_fmt(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
+                                        uint32_t acc)
+{
+    if constexpr (EB == 2) mma_bf16(d, a, b, id, acc);
+    else mma_tf32(d, a, b, id, acc);
+}
+
+// FP32 -> TF32 (round to nearest, ties away), as a 32-bit pattern.
+__device__ __forceinline__ uint32_t to_tf32(float v)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return r;
+}
 
 // Barriers, tensor-memory address and abort flag shared by the warp roles.
 struct Ctl {
@@ -53,25 +99,27 @@ struct Ctl {
 
 // Shared-memory layout (bytes from the 1024-aligned base):
 //   [0, 1024)           control block (barriers, tensor-memory address, abort flag)
-//   A operands          stage s, part h (0 = hi, 1 = lo) at off_a + (2s+h)*a_bytes
+//   A operands          buffer s, part h (0 = hi, 1 = lo) at off_a + (2s+h)*a_bytes
 //   FP32 staging        stage s at off_stage + s*stage_bytes (TMA boxes)
-//   Toeplitz panels     (2R+1) * 6144 bytes
-//   4 KB of slack, so that no descriptor can reach past the allocation
+//   Toeplitz panels     (2R+1) * PANEL_BYTES
 //   output tile         128 x 32 FP32, 128-byte swizzled (only with the TMA store)
 struct TcLayout {
     uint32_t a_bytes, off_a, stage_bytes, off_stage, off_b, off_out, total;
 };
 
+template <int EB>
 __host__ __device__ inline TcLayout tc_layout(int R, int rows, int rows_p, int box_w, int tma_store)
 {
+    using F = Fmt<EB>;
     TcLayout L;
-    L.a_bytes = (uint32_t)(kTcKC * rows_p * 16);
+    L.a_bytes = (uint32_t)(F::KCH * rows_p * 16);
     L.off_a = 1024;
-    L.off_stage = (L.off_a + 4 * L.a_bytes + 127) / 128 * 128;
+    L.off_stage = (L.off_a + 2 * F::NSA * L.a_bytes + 127) / 128 * 128;
     L.stage_bytes = ((uint32_t)(rows * box_w * 4) + 127) / 128 * 128;
     L.off_b = L.off_stage + 2 * L.stage_bytes;
-    L.off_out = (L.off_b + (uint32_t)(2 * R + 1) * PANEL_BYTES + 1023) / 1024 * 1024;
-    L.total = tma_store ? L.off_out + kTcM * kTcN * 4 : L.off_b + (uint32_t)(2 * R + 1) * PANEL_BYTES;
+    L.off_out = (L.off_b + (uint32_t)(2 * R + 1) * F::PANEL_BYTES + 1023) / 1024 * 1024;
+    L.total = tma_store ? L.off_out + kTcM * kTcN * 4
+                        : L.off_b + (uint32_t)(2 * R + 1) * F::PANEL_BYTES;
     return L;
 }
 
@@ -88,14 +136,39 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void 
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Eight staged FP32 values of row r starting at column c0 (off: the window's
+// shift inside the staged box), minus mu.
+__device__ __forceinline__ void load8(const float *src, int off, float mu, float (&v)[8])
+{
+    if (off == 0) {  // 16-byte aligned: two vector loads
+        const float4 p0 = reinterpret_cast<const float4 *>(src)[0];
+        const float4 p1 = reinterpret_cast<const float4 *>(src)[1];
+        v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
+        v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+    } else if ((off & 1) == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 p = reinterpret_cast<const float2 *>(src)[e];
+            v[2 * e] = p.x;
+            v[2 * e + 1] = p.y;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = src[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] -= mu;
+}
 
+template <int EB>
 __global__ void __launch_bounds__(NT, 1)
     k_tc2d(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap dmap,
            const __grid_constant__ TC2DArgs a)
 {
+    using F = Fmt<EB>;
     extern __shared__ __align__(1024) unsigned char smem[];
     Ctl *ctl = reinterpret_cast<Ctl *>(smem);
-    const TcLayout L = tc_layout(a.R, a.rows, a.rows_p, a.box_w, a.tma_store);
+    const TcLayout L = tc_layout<EB>(a.R, a.rows, a.rows_p, a.box_w, a.tma_store);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = smem_u32(smem);
     const int R = a.R;
@@ -121,7 +194,7 @@ __global__ void __launch_bounds__(NT, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     {  // resident Toeplitz panels
-        const int n16 = (2 * R + 1) * PANEL_BYTES / 16;
+        const int n16 = (2 * R + 1) * F::PANEL_BYTES / 16;
         const uint4 *gp = reinterpret_cast<const uint4 *>(a.panels);
         uint4 *sp = reinterpret_cast<uint4 *>(smem + L.off_b);
         for (int i = tid; i < n16; i += NT) sp[i] = gp[i];
@@ -153,20 +226,22 @@ __global__ void __launch_bounds__(NT, 1)
     } else if (warp == 1) {
         // ---- MMA issuer
         if (lane == 0) {
-            const uint32_t id64 = idesc_bf16(kTcM, 64), id32 = idesc_bf16(kTcM, 32);
+            const uint32_t id64 = EB == 2 ? idesc_bf16(kTcM, 64) : idesc_tf32(kTcM, 64);
+            const uint32_t id32 = EB == 2 ? idesc_bf16(kTcM, 32) : idesc_tf32(kTcM, 32);
             const uint32_t lbo_a = (uint32_t)a.rows_p * 16;
             int i = 0, last = -1;
             for (int tile = first; tile < a.ntiles; tile += step, ++i) {
-                const int s = i & 1, k = i >> 1;
+                const int s = i & 1, k = i >> 1;                       // accumulator
+                const int sa = i % F::NSA, ka = i / F::NSA;            // A operand
                 // (fault_withhold_mma is a test hook: the issuer stops before its
                 // first MMA, as if its completions were lost, so every other
                 // role's bounded wait must run out and report a timeout)
                 if (a.fault_withhold_mma) break;
-                if (!wait_or_abort(&ctl->a_full[s], k & 1, ctl, a)) break;
+                if (!wait_or_abort(&ctl->a_full[sa], ka & 1, ctl, a)) break;
                 if (!wait_or_abort(&ctl->d_empty[s], (k & 1) ^ 1, ctl, a)) break;
                 tc_fence_after();
                 const uint32_t dt = tmem + (uint32_t)(s * 64);
-                const uint32_t a_hi = sbase + L.off_a + (2 * s) * L.a_bytes;
+                const uint32_t a_hi = sbase + L.off_a + (2 * sa) * L.a_bytes;
                 // descriptors of the first (row offset, K step); the others differ
                 // only in the start-address field, by whole 16-byte units
                 const uint64_t dh0 = smem_desc(a_hi, lbo_a, 128);
@@ -174,89 +249,93 @@ __global__ void __launch_bounds__(NT, 1)
                 const uint64_t db0 = smem_desc(sbase + L.off_b, LBO_B, 128);
                 const uint32_t kstep_a = (2 * lbo_a) >> 4, kstep_b = (2 * LBO_B) >> 4;
                 if (a.terms == 3) {
-                    mma_bf16(dt, dh0, db0, id64, 0u);
-                    mma_bf16(dt, dl0, db0, id32, 1u);
+                    mma_fmt<EB>(dt, dh0, db0, id64, 0u);
+                    mma_fmt<EB>(dt, dl0, db0, id32, 1u);
                     for (int ai = 0; ai <= 2 * R; ++ai) {
-                        const uint32_t oa = (uint32_t)ai, ob = (uint32_t)ai * (PANEL_BYTES >> 4);
+                        const uint32_t oa = (uint32_t)ai, ob = (uint32_t)ai * (F::PANEL_BYTES >> 4);
 #pragma unroll
-                        for (int kk = (ai == 0 ? 1 : 0); kk < kTcK / 16; ++kk) {
+                        for (int kk = (ai == 0 ? 1 : 0); kk < F::KSTEPS; ++kk) {
                             const uint64_t d_a = oa + kk * kstep_a, d_b = ob + kk * kstep_b;
-                            mma_bf16(dt, dh0 + d_a, db0 + d_b, id64, 1u);
-                            mma_bf16(dt, dl0 + d_a, db0 + d_b, id32, 1u);
+                            mma_fmt<EB>(dt, dh0 + d_a, db0 + d_b, id64, 1u);
+                            mma_fmt<EB>(dt, dl0 + d_a, db0 + d_b, id32, 1u);
                         }
                     }
                 } else {
-                    mma_bf16(dt, dh0, db0, id32, 0u);
+                    mma_fmt<EB>(dt, dh0, db0, id32, 0u);
                     for (int ai = 0; ai <= 2 * R; ++ai) {
-                        const uint32_t oa = (uint32_t)ai, ob = (uint32_t)ai * (PANEL_BYTES >> 4);
+                        const uint32_t oa = (uint32_t)ai, ob = (uint32_t)ai * (F::PANEL_BYTES >> 4);
 #pragma unroll
-                        for (int kk = (ai == 0 ? 1 : 0); kk < kTcK / 16; ++kk)
-                            mma_bf16(dt, dh0 + oa + kk * kstep_a, db0 + ob + kk * kstep_b, id32, 1u);
+                        for (int kk = (ai == 0 ? 1 : 0); kk < F::KSTEPS; ++kk)
+                            mma_fmt<EB>(dt, dh0 + oa + kk * kstep_a, db0 + ob + kk * kstep_b, id32,
+                                        1u);
                     }
                 }
-                mma_commit(&ctl->a_empty[s]);
+                mma_commit(&ctl->a_empty[sa]);
                 mma_commit(&ctl->d_full[s]);
                 last = i;
             }
             if (ctl->abort && last >= 0) drain_wait(&ctl->d_full[last & 1], (last >> 1) & 1, a);
         }
     } else if (warp >= 4 && warp < 8) {
-        // ---- converters: FP32 staging -> centred BF16 hi/lo operands
+        // ---- converters: FP32 staging -> centred hi/lo operands
         const int ct = tid - 128;
         const float mu = a.mean_sum ? (float)(a.mean_sum[0] * a.inv_n) : 0.f;
         const int off = a.halo_x - R;
         const uint32_t lbo_a = (uint32_t)a.rows_p * 16;
+        constexpr int VPC = 16 / EB;        // values per 16-byte chunk
+        constexpr int CPI = 8 / VPC;        // chunks per item of 8 values
+        constexpr int ITEMS = kTcK / 8;     // items of 8 values per row
         int i = 0;
         for (int tile = first; tile < a.ntiles; tile += step, ++i) {
             const int s = i & 1, k = i >> 1;
+            const int sa = i % F::NSA, ka = i / F::NSA;
             bool ok = wait_or_abort(&ctl->stage_full[s], k & 1, ctl, a);
-            ok = ok && wait_or_abort(&ctl->a_empty[s], (k & 1) ^ 1, ctl, a);
+            ok = ok && wait_or_abort(&ctl->a_empty[sa], (ka & 1) ^ 1, ctl, a);
             if (!__all_sync(0xffffffffu, ok)) break;
             const float *st = reinterpret_cast<const float *>(smem + L.off_stage + s * L.stage_bytes);
-            unsigned char *ahi = smem + L.off_a + (2 * s) * L.a_bytes;
+            unsigned char *ahi = smem + L.off_a + (2 * sa) * L.a_bytes;
             unsigned char *alo = ahi + L.a_bytes;
-            for (int it = ct; it < a.rows * kTcKC; it += 128) {
-                const int kc = it % kTcKC, r = it / kTcKC;
-                const float *src = st + r * a.box_w + kc * 8 + off;
+            for (int it = ct; it < a.rows * ITEMS; it += 128) {
+                const int kc8 = it % ITEMS, r = it / ITEMS;
                 float v[8];
-                if (off == 0) {  // 16-byte aligned: two vector loads
-                    const float4 p0 = reinterpret_cast<const float4 *>(src)[0];
-                    const float4 p1 = reinterpret_cast<const float4 *>(src)[1];
-                    v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
-                    v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
-                } else if ((off & 1) == 0) {
+                load8(st + r * a.box_w + kc8 * 8 + off, off, mu, v);
+                if constexpr (EB == 2) {
+                    uint32_t hw[4], lw[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const float2 p = reinterpret_cast<const float2 *>(src)[e];
-                        v[2 * e] = p.x;
-                        v[2 * e + 1] = p.y;
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]);
+                        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * e + 1]);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 =
+                            __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
+                        hw[e] = (uint32_t)__bfloat16_as_ushort(h0) |
+                                ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                        lw[e] = (uint32_t)__bfloat16_as_ushort(l0) |
+                                ((uint32_t)__bfloat16_as_ushort(l1) << 16);
                     }
+                    const uint32_t o = kc8 * lbo_a + r * 16;
+                    *reinterpret_cast<uint4 *>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 } else {
+                    uint32_t hw[8], lw[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) v[e] = src[e];
+                    for (int e = 0; e < 8; ++e) {
+                        hw[e] = to_tf32(v[e]);
+                        lw[e] = to_tf32(v[e] - __uint_as_float(hw[e]));
+                    }
+#pragma unroll
+                    for (int c = 0; c < CPI; ++c) {
+                        const uint32_t o = (kc8 * CPI + c) * lbo_a + r * 16;
+                        *reinterpret_cast<uint4 *>(ahi + o) =
+                            make_uint4(hw[4 * c], hw[4 * c + 1], hw[4 * c + 2], hw[4 * c + 3]);
+                        *reinterpret_cast<uint4 *>(alo + o) =
+                            make_uint4(lw[4 * c], lw[4 * c + 1], lw[4 * c + 2], lw[4 * c + 3]);
+                    }
                 }
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] -= mu;
-                uint32_t hw[4], lw[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]);
-                    const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * e + 1]);
-                    const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
-                    const __nv_bfloat16 l1 =
-                        __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
-                    hw[e] = (uint32_t)__bfloat16_as_ushort(h0) |
-                            ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                    lw[e] = (uint32_t)__bfloat16_as_ushort(l0) |
-                            ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-                }
-                const uint32_t o = kc * lbo_a + r * 16;
-                *reinterpret_cast<uint4 *>(ahi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4 *>(alo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
             fence_proxy_async_smem();
             mbar_arrive(&ctl->stage_empty[s]);
-            mbar_arrive(&ctl->a_full[s]);
+            mbar_arrive(&ctl->a_full[sa]);
         }
     } else if (warp >= 8) {
         // ---- epilogue: tensor memory -> registers -> global memory
@@ -338,9 +417,23 @@ __global__ void __launch_bounds__(NT, 1)
     }
 }
 
+// Host-side rounding of a double to the nearest TF32 (ties away from zero,
+// as the converters' cvt.rna does): keep 10 mantissa bits of the float.
+float tf32_round(double v)
+{
+    const float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
 }  // namespace
 
 bool tc2d_supported(int R) { return R >= 1 && R <= kTcMaxR; }
+bool tc2d_tf32_supported(int R) { return R >= 1 && R <= kTcMaxRTf32; }
 
 static void tc_geometry(int R, int *rows, int *rows_p, int *box_w, int *halo_x)
 {
@@ -350,30 +443,52 @@ static void tc_geometry(int R, int *rows, int *rows_p, int *box_w, int *halo_x)
     *box_w = round_up(kTcK + *halo_x - R, 4);
 }
 
-size_t tc2d_smem_bytes(int R, bool tma_store)
+size_t tc2d_smem_bytes(int R, bool tma_store, bool tf32)
 {
     int rows, rows_p, box_w, hx;
     tc_geometry(R, &rows, &rows_p, &box_w, &hx);
-    return tc_layout(R, rows, rows_p, box_w, tma_store ? 1 : 0).total;
+    return tf32 ? tc_layout<4>(R, rows, rows_p, box_w, tma_store ? 1 : 0).total
+                : tc_layout<2>(R, rows, rows_p, box_w, tma_store ? 1 : 0).total;
 }
 
-double tc2d_build_panels(const double *cm, int R, uint16_t *out)
+size_t tc2d_panel_bytes(int R, bool tf32)
+{
+    return (size_t)(2 * R + 1) * (tf32 ? Fmt<4>::PANEL_BYTES : Fmt<2>::PANEL_BYTES);
+}
+
+// The hi/lo split of the folded weights with the mass correction: the centre
+// tap's lo absorbs the rounding of the sum.  rnd rounds a double to the
+// operand format and back.
+template <class Rnd>
+static double split_weights(const double *cm, int R, Rnd rnd, std::vector<double> &hi,
+                            std::vector<double> &lo)
 {
     const int W = 2 * R + 1;
-    std::vector<double> hi(W * W), lo(W * W);
+    hi.assign(W * W, 0.0);
+    lo.assign(W * W, 0.0);
     double target = 0.0, got = 0.0;
     for (int i = 0; i < W * W; ++i) {
-        const __nv_bfloat16 h = __double2bfloat16(cm[i]);
-        hi[i] = (double)__bfloat162float(h);
-        lo[i] = (double)__bfloat162float(__double2bfloat16(cm[i] - hi[i]));
+        hi[i] = rnd(cm[i]);
+        lo[i] = rnd(cm[i] - hi[i]);
         target += cm[i];
         got += hi[i] + lo[i];
     }
-    // mass correction: the centre tap's lo absorbs the rounding of the sum
     const int c = R * W + R;
-    lo[c] = (double)__bfloat162float(__double2bfloat16(lo[c] + (target - got)));
+    lo[c] = rnd(lo[c] + (target - got));
+    return target;
+}
+
+double tc2d_build_panels(const double *cm, int R, void *host_out, bool tf32)
+{
+    const int W = 2 * R + 1;
+    std::vector<double> hi, lo;
+    double target;
+    if (tf32)
+        target = split_weights(cm, R, [](double v) { return (double)tf32_round(v); }, hi, lo);
+    else
+        target = split_weights(
+            cm, R, [](double v) { return (double)__bfloat162float(__double2bfloat16(v)); }, hi, lo);
     for (int ai = 0; ai < W; ++ai) {
-        uint16_t *panel = out + (size_t)ai * kTcPanelElems;
         for (int n = 0; n < 64; ++n) {
             const int nn = n & 31;
             const std::vector<double> &src = n < 32 ? hi : lo;
@@ -381,8 +496,20 @@ double tc2d_build_panels(const double *cm, int R, uint16_t *out)
                 const int b = k - nn - R;  // column offset
                 double w = 0.0;
                 if (b >= -R && b <= R) w = src[ai * W + (b + R)];
-                const __nv_bfloat16 bw = __double2bfloat16(w);
-                panel[(k / 8) * 512 + n * 8 + (k % 8)] = __bfloat16_as_ushort(bw);
+                // K-major core-matrix layout: 16-byte chunk (k / per-chunk) of row n
+                if (tf32) {
+                    uint32_t *panel = static_cast<uint32_t *>(host_out) +
+                                      (size_t)ai * (Fmt<4>::PANEL_BYTES / 4);
+                    const float f = tf32_round(w);
+                    uint32_t u;
+                    memcpy(&u, &f, 4);
+                    panel[((k / 4) * 64 + n) * 4 + (k % 4)] = u;
+                } else {
+                    uint16_t *panel = static_cast<uint16_t *>(host_out) +
+                                      (size_t)ai * (Fmt<2>::PANEL_BYTES / 2);
+                    panel[((k / 8) * 64 + n) * 8 + (k % 8)] =
+                        __bfloat16_as_ushort(__double2bfloat16(w));
+                }
             }
         }
     }
@@ -394,11 +521,17 @@ double tc2d_build_panels(const double *cm, int R, uint16_t *out)
 }
 
 cudaError_t launch_tc2d(const CUtensorMap &map, const CUtensorMap &dmap, const TC2DArgs &a,
-                        int grid, size_t smem, cudaStream_t s)
+                        int grid, size_t smem, cudaStream_t s, bool tf32)
 {
-    const cudaError_t e = smem_optin((const void *)k_tc2d);
-    if (e != cudaSuccess) return e;
-    k_tc2d<<<grid, NT, smem, s>>>(map, dmap, a);
+    if (tf32) {
+        const cudaError_t e = smem_optin((const void *)k_tc2d<4>);
+        if (e != cudaSuccess) return e;
+        k_tc2d<4><<<grid, NT, smem, s>>>(map, dmap, a);
+    } else {
+        const cudaError_t e = smem_optin((const void *)k_tc2d<2>);
+        if (e != cudaSuccess) return e;
+        k_tc2d<2><<<grid, NT, smem, s>>>(map, dmap, a);
+    }
     return cudaGetLastError();
 }
 

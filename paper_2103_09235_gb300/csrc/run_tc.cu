@@ -14,20 +14,19 @@ namespace sg {
 
 // Toeplitz panels of c^(m) for the per-offset or the grouped tensor-core
 // kernel, built once per plan.
-static stencil_status_t tc_panels(stencil_plan_s *p, int m, bool grouped, const uint16_t **out,
-                                  double *sum)
+static stencil_status_t tc_panels(stencil_plan_s *p, int m, bool grouped, bool tf32,
+                                  const uint16_t **out, double *sum)
 {
-    const int key = grouped ? m + 64 : m;
+    const int key = grouped ? m + 64 : (tf32 ? m + 128 : m);
     auto it = p->panels.find(key);
     if (it == p->panels.end()) {
         const std::vector<double> *cm = nullptr;
         stencil_status_t st = plan_folded(p, m, &cm);
         if (st != STENCIL_OK) return st;
         const int R = m * p->r;
-        std::vector<uint16_t> host(grouped ? tc2dg_panel_elems(R)
-                                           : (size_t)(2 * R + 1) * kTcPanelElems);
+        std::vector<uint16_t> host(grouped ? tc2dg_panel_elems(R) : tc2d_panel_bytes(R, tf32) / 2);
         const double wsum = grouped ? tc2dg_build_panels(cm->data(), R, host.data())
-                                    : tc2d_build_panels(cm->data(), R, host.data());
+                                    : tc2d_build_panels(cm->data(), R, host.data(), tf32);
         uint16_t *d = nullptr;
         cudaError_t e = cudaMalloc(&d, host.size() * sizeof(uint16_t));
         if (e == cudaSuccess)
@@ -115,6 +114,7 @@ static stencil_status_t launch_tc_pass(stencil_plan_s *p, const Padded &src, int
     a.status = p->d_status;
     a.wait_ns = (unsigned long long)p->wait_ms * 1000000ull;
     a.fault_withhold_mma = p->fault_withhold_mma;
+    const bool tf32 = p->precision == STENCIL_PREC_TF32X3;
     const int box[2] = {a.box_w, a.rows};
     const CUtensorMap *map = plan_map(p, src, box);
     if (!map) return STENCIL_ERR_CUDA;
@@ -123,12 +123,12 @@ static stencil_status_t launch_tc_pass(stencil_plan_s *p, const Padded &src, int
     CUtensorMap dmap;
     memset(&dmap, 0, sizeof(dmap));
     a.tma_store = 0;
-    if (p->tc_tma_store && tc2d_smem_bytes(R, true) <= (size_t)p->max_smem &&
+    if (p->tc_tma_store && tc2d_smem_bytes(R, true, tf32) <= (size_t)p->max_smem &&
         encode_store_map_2d(&dmap, dst, p->nx, p->ny, dst_py, kTcN, kTcM))
         a.tma_store = 1;
-    const size_t smem = tc2d_smem_bytes(R, a.tma_store != 0);
+    const size_t smem = tc2d_smem_bytes(R, a.tma_store != 0, tf32);
     const int grid = std::min(a.ntiles, p->sm_count);
-    cudaError_t e = launch_tc2d(*map, dmap, a, grid, smem, s);
+    cudaError_t e = launch_tc2d(*map, dmap, a, grid, smem, s, tf32);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core sweep launch");
     return STENCIL_OK;
 }
@@ -142,24 +142,28 @@ stencil_status_t run2d_tc(stencil_plan_s *p, const float *in, float *out, int64_
         set_error("tensor-core sweep: folded width %d exceeds the grid", 2 * R + 1);
         return STENCIL_ERR_INVALID_ARG;
     }
-    if (!tc2d_supported(R) || !sweep2d_supported(p->r, 1, p->pattern)) {
-        set_error("tensor-core sweep: folded radius %d unsupported (1..%d)", R, kTcMaxR);
+    const bool tf32 = p->precision == STENCIL_PREC_TF32X3;
+    if (!(tf32 ? tc2d_tf32_supported(R) : tc2d_supported(R)) ||
+        !sweep2d_supported(p->r, 1, p->pattern)) {
+        set_error("tensor-core sweep: folded radius %d unsupported (1..%d)", R,
+                  tf32 ? kTcMaxRTf32 : kTcMaxR);
         return STENCIL_ERR_UNSUPPORTED;
     }
     ensure_device_facts(p);
     // the grouped form issues about a quarter of the MMAs but pays a fixed
     // epilogue per tile: it wins for wide folds (measured on GB300: 1318 vs
     // 1002 GS/s at R = 8, 783 vs 853 at R = 4, 394 vs 643 at R = 2)
-    const bool grouped = p->tc_form == 2 || (p->tc_form == 0 && R >= kTcGroupedMinR);
+    // TF32 operands run in the per-offset kernel only
+    const bool grouped = !tf32 && (p->tc_form == 2 || (p->tc_form == 0 && R >= kTcGroupedMinR));
     if (grouped ? tc2dg_smem_bytes(R, 1) > (size_t)p->max_smem
-                : tc2d_smem_bytes(R, false) > (size_t)p->max_smem) {
+                : tc2d_smem_bytes(R, false, tf32) > (size_t)p->max_smem) {
         set_error("tensor-core sweep: shared memory");
         return STENCIL_ERR_UNSUPPORTED;
     }
     const uint16_t *panels = nullptr;
     double sum_c = 0.0;
     const std::vector<double> *c1 = nullptr;
-    stencil_status_t st = tc_panels(p, m, grouped, &panels, &sum_c);
+    stencil_status_t st = tc_panels(p, m, grouped, tf32, &panels, &sum_c);
     if (st == STENCIL_OK) st = plan_folded(p, 1, &c1);
     if (st == STENCIL_OK) st = ensure_padded(p);
     if (st != STENCIL_OK) return st;

@@ -342,7 +342,7 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
         return STENCIL_ERR_INVALID_ARG;
     }
     if (!strcmp(key, "precision")) {
-        if (v < 0 || v > 2) goto bad;
+        if (v < 0 || v > 3) goto bad;
         p->precision = (int)v;
     } else if (!strcmp(key, "block_b")) {
         if (v < 0 || v > 64) goto bad;

@@ -124,3 +124,33 @@ def test_tc_bounded_waits_report_timeout(env, form):
     assert plan.get("last_engine") == 1 and plan.get("last_tc_form") == form
     assert oracle.rel_l2(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
     plan.close()
+
+
+TF32_CASES = [((300, 520), 1, 13, 4), ((256, 256), 1, 12, 3), ((300, 520), 1, 16, 2),
+              ((130, 70), 1, 9, 4), ((200, 300), 2, 10, 2), ((97, 203), 1, 11, 4)]
+
+
+@pytest.mark.parametrize("shape,r,T,m", TF32_CASES)
+def test_tc_tf32x3_parity(env, shape, r, T, m):
+    """TF32 hi/lo operands (kind::tf32, three products): about 22 significant
+    bits per operand pair, so the error sits below the BF16x3 split's on the
+    same case; both within the FP32 tolerance."""
+    _, _, oracle = env
+    c = synth.dyadic_coeffs(500 + r, 2, r, "box")
+    x = synth.grid(600 + T, shape, np.float32)
+    ref = oracle.run(x.astype(np.float64), c, T)
+    yt = run_tc(env, shape, c, x, T, m, precision=3, form=1)
+    yb = run_tc(env, shape, c, x, T, m, precision=1, form=1)
+    et, eb = oracle.rel_l2(yt, ref), oracle.rel_l2(yb, ref)
+    print("TC %s r=%d T=%d m=%d: TF32x3 rel-L2 %.3e, BF16x3 rel-L2 %.3e" % (shape, r, T, m, et, eb))
+    assert et <= TOL
+    assert et < eb
+
+
+def test_tc_tf32x3_rejects_wide_folds(env):
+    torch, binding, _ = env
+    c = synth.dyadic_coeffs(501, 2, 1, "box")
+    plan = binding.Plan((200, 200), c).set_option("precision", 3)
+    x = torch.zeros((200, 200), device="cuda")
+    assert plan.run_status(x, x, 12, 6) == 2  # folded radius 6 > 4: UNSUPPORTED
+    plan.close()
