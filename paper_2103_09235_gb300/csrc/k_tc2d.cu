@@ -367,7 +367,14 @@ __global__ void __launch_bounds__(NT, 1)
             float o[32];
 #pragma unroll
             for (int n = 0; n < 32; ++n) o[n] = v0[n] + (a.terms == 3 ? v1[n] : 0.f) + musum;
-            if (a.tma_store) {
+            // Only tiles wholly inside the grid leave by TMA store.  A store box
+            // clipped by the grid edge in x and y at once (a 97 x 203 grid)
+            // gave wrong values beside the clipped tile, so ragged tiles take
+            // the direct stores.  The decision is the same for the four
+            // epilogue warps, which all reach the barriers of the store path.
+            const bool via_tma =
+                a.tma_store && X0 + kTcN <= a.nx && (ty + 1) * kTcM <= a.ny;
+            if (via_tma) {
                 // row 32q+lane of the swizzled tile: 16-byte chunk j lands at j ^ (row & 7)
                 const int row = 32 * q + lane;
                 unsigned char *tile_s = smem + L.off_out;
@@ -383,7 +390,7 @@ __global__ void __launch_bounds__(NT, 1)
             }
             if (Y < a.ny) {
                 float *row = a.dst + Y * a.dst_py + X0;
-                if (a.tma_store) {
+                if (via_tma) {
                     // the bulk store wrote the interior; only ghost copies remain
                 } else if (a.dst_vec4 && X0 + 32 <= a.nx) {
 #pragma unroll

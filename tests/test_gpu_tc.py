@@ -48,6 +48,9 @@ def run_tc(env, shape, c, x, T, m, precision=1, center=1, form=0):
 CASES = [
     # shape, r, T, m
     ((300, 520), 1, 13, 4),
+    # ragged in x and y, two folded sweeps and no remainder: the first sweep's
+    # ragged tiles must not leave by the clipped TMA store
+    ((97, 203), 1, 8, 4),
     ((300, 520), 1, 16, 2),
     ((256, 256), 1, 12, 3),
     ((300, 520), 1, 27, 8),
@@ -144,7 +147,9 @@ def test_tc_tf32x3_parity(env, shape, r, T, m):
     et, eb = oracle.rel_l2(yt, ref), oracle.rel_l2(yb, ref)
     print("TC %s r=%d T=%d m=%d: TF32x3 rel-L2 %.3e, BF16x3 rel-L2 %.3e" % (shape, r, T, m, et, eb))
     assert et <= TOL
-    assert et < eb
+    # the TF32 split is exact to about 2^-22, below the FP32 rounding of the
+    # accumulation and output: the error sits at the FP32 floor
+    assert et <= 3e-7
 
 
 def test_tc_tf32x3_rejects_wide_folds(env):
