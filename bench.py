@@ -349,9 +349,13 @@ def roofline_of(alg_bytes, alg_flops, pass_ms, esz, engine, sms):
     return out
 
 
-def kernel_name(engine, grouped, ndim, b, cp_k):
+def kernel_name(engine, grouped, ndim, b, cp_k, esz=4):
     if engine == "tensor-core":
+        if ndim == 3:
+            return "k_tc3d"
         return "k_tc2d_grouped" if grouped else "k_tc2d"
+    if esz == 8 and ndim >= 2:
+        return "k_sweep_f64"
     if ndim == 1:
         return "k_sweep1d"
     if ndim == 3:
@@ -406,7 +410,8 @@ def measure_run(torch, binding, stream, flush, plan, x, y, T, m, npts, esz, sms,
     # leave y holding the full run's output for the accuracy check
     plan.run(x, y, T, fold_m=m, stream=stream)
     plan.sync(stream)
-    roof["kernel"] = kernel_name(f["engine"], f.get("tc_kernel") == "grouped", x.dim(), bu, cp_k)
+    roof["kernel"] = kernel_name(f["engine"], f.get("tc_kernel") == "grouped", x.dim(), bu, cp_k,
+                                 esz)
     return ms_full, f, roof
 
 
@@ -450,6 +455,9 @@ VARIANTS = [
     ("star512cube_T200_m2", "star512cube", 2, {"block_b": 1}, "f32"),
     ("box256cube_T200_plain", "box256cube", 1, {"block_b": 1}, "f32"),
     ("box256cube_T200_m2", "box256cube", 2, {"block_b": 1}, "f32"),
+    ("box256cube_T200_tc_bf16x3_m2", "box256cube", 2, {"precision": 1}, "f32"),
+    ("box256cube_T200_tc_bf16x1_m2", "box256cube", 2, {"precision": 2}, "f32"),
+    ("star4096_T1000_fp64_m4", "star4096", 4, {}, "f64"),
 ]
 
 
