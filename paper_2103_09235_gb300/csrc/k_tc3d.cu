@@ -69,18 +69,20 @@ __host__ __device__ inline Tc3Layout tc3_layout(int R, int rows, int rows_p, int
 __device__ __forceinline__ void store_point_3d(const TC3DArgs &a, int X, int Y, int Z, float v)
 {
     const int nx = a.t.nx, ny = a.t.ny, nz = a.nz, gw = a.t.dst_gw;
-    const int sx[3] = {0, X < gw ? nx : 0, X >= nx - gw ? -nx : 0};
-    const int sy[3] = {0, Y < gw ? ny : 0, Y >= ny - gw ? -ny : 0};
-    const int sz[3] = {0, Z < gw ? nz : 0, Z >= nz - gw ? -nz : 0};
-    for (int iz = 0; iz < 3; ++iz) {
-        if (iz && !sz[iz]) continue;
-        for (int iy = 0; iy < 3; ++iy) {
-            if (iy && !sy[iy]) continue;
-            for (int ix = 0; ix < 3; ++ix) {
-                if (ix && !sx[ix]) continue;
-                if (!ix && !iy && !iz) continue;
-                a.t.dst[(int64_t)(Z + sz[iz]) * a.dst_pz + (int64_t)(Y + sy[iy]) * a.t.dst_py +
-                        X + sx[ix]] = v;
+    // the periodic image shift along each axis: 0, +n (near the low edge) or
+    // -n (near the high edge); at most one of the two for gw <= n / 2
+    const int ex = X < gw ? nx : (X >= nx - gw ? -nx : 0);
+    const int ey = Y < gw ? ny : (Y >= ny - gw ? -ny : 0);
+    const int ez = Z < gw ? nz : (Z >= nz - gw ? -nz : 0);
+    for (int iz = 0; iz < 2; ++iz) {
+        if (iz && !ez) break;
+        for (int iy = 0; iy < 2; ++iy) {
+            if (iy && !ey) break;
+            for (int ix = 0; ix < 2; ++ix) {
+                if (ix && !ex) break;
+                if (ix || iy || iz)
+                    a.t.dst[(int64_t)(Z + iz * ez) * a.dst_pz + (int64_t)(Y + iy * ey) * a.t.dst_py +
+                            X + ix * ex] = v;
             }
         }
     }
@@ -110,6 +112,14 @@ __global__ void __launch_bounds__(NT, 1)
             mbar_init(&ctl->d_empty[s], 128);
         }
         ctl->abort = 0;
+        // self-check: the layout the operands' descriptors address must lie
+        // inside the shared memory this launch has
+        uint32_t dyn = 0;
+        asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        if (dyn < L.total) {
+            record_status(a.status, DEV_CHECK);
+            ctl->abort = 1;
+        }
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -125,8 +135,11 @@ __global__ void __launch_bounds__(NT, 1)
     const uint32_t tmem = ctl->tmem_base;
     const int first = blockIdx.x, step = gridDim.x;
     const int tiles_xy = a.tiles_x * a3.tiles_y;
+    const bool skip = *(volatile int *)&ctl->abort != 0;  // the self-check failed
 
-    if (warp == 0) {
+    if (skip) {
+        // nothing but the tensor-memory release below
+    } else if (warp == 0) {
         // ---- producer: per plane step, the tile of plane z+dz and the step's panels
         if (lane == 0) {
             const uint32_t bytes = (uint32_t)(a.rows * a.box_w * 4);
@@ -267,9 +280,11 @@ __global__ void __launch_bounds__(NT, 1)
         int i = 0;
         for (int tile = first; tile < a.ntiles; tile += step, ++i) {
             const int s = i & 1, k = i >> 1;
+            __syncwarp();  // the warp is converged before its aligned tensor-memory loads
             bool ok = wait_or_abort(&ctl->d_full[s], k & 1, ctl, a);
             ok = __all_sync(0xffffffffu, ok);
             if (lane == 0) ctl->epi_ok[s][q] = ok ? 1 : 0;
+            __syncwarp();
             epi_barrier();
             const volatile int *votes = ctl->epi_ok[s];
             if (!(votes[0] && votes[1] && votes[2] && votes[3])) break;
@@ -285,27 +300,30 @@ __global__ void __launch_bounds__(NT, 1)
             const int ty = rem / a.tiles_x, tx = rem % a.tiles_x;
             const int Y = ty * kTcM + 32 * q + lane;
             const int X0 = tx * kTcN;
-            if (Y >= a.ny) continue;
-            float o[32];
+            if (Y < a.ny) {
+                float o[32];
 #pragma unroll
-            for (int n = 0; n < 32; ++n) o[n] = v0[n] + (a.terms == 3 ? v1[n] : 0.f) + musum;
-            float *row = a.dst + (int64_t)z * a3.dst_pz + (int64_t)Y * a.dst_py + X0;
-            if (a.dst_vec4 && X0 + 32 <= a.nx) {
+                for (int n = 0; n < 32; ++n) o[n] = v0[n] + (a.terms == 3 ? v1[n] : 0.f) + musum;
+                float *row = a.dst + (int64_t)z * a3.dst_pz + (int64_t)Y * a.dst_py + X0;
+                if (a.dst_vec4 && X0 + 32 <= a.nx) {
 #pragma unroll
-                for (int n = 0; n < 32; n += 4)
-                    *reinterpret_cast<float4 *>(row + n) = make_float4(o[n], o[n + 1], o[n + 2], o[n + 3]);
-            } else {
+                    for (int n = 0; n < 32; n += 4)
+                        *reinterpret_cast<float4 *>(row + n) =
+                            make_float4(o[n], o[n + 1], o[n + 2], o[n + 3]);
+                } else {
 #pragma unroll
-                for (int n = 0; n < 32; ++n)
-                    if (X0 + n < a.nx) row[n] = o[n];
+                    for (int n = 0; n < 32; ++n)
+                        if (X0 + n < a.nx) row[n] = o[n];
+                }
+                const int gw = a.dst_gw;
+                if (gw > 0 && (X0 < gw || X0 + 32 > a.nx - gw || Y < gw || Y >= a.ny - gw ||
+                               z < gw || z >= a3.nz - gw)) {
+#pragma unroll
+                    for (int n = 0; n < 32; ++n)
+                        if (X0 + n < a.nx) store_point_3d(a3, X0 + n, Y, z, o[n]);
+                }
             }
-            const int gw = a.dst_gw;
-            if (gw > 0 && (X0 < gw || X0 + 32 > a.nx - gw || Y < gw || Y >= a.ny - gw || z < gw ||
-                           z >= a3.nz - gw)) {
-#pragma unroll 1
-                for (int n = 0; n < 32; ++n)
-                    if (X0 + n < a.nx) store_point_3d(a3, X0 + n, Y, z, o[n]);
-            }
+            __syncwarp();
         }
     }
 
