@@ -351,8 +351,6 @@ def roofline_of(alg_bytes, alg_flops, pass_ms, esz, engine, sms):
 
 def kernel_name(engine, grouped, ndim, b, cp_k, esz=4):
     if engine == "tensor-core":
-        if ndim == 3:
-            return "k_tc3d"
         return "k_tc2d_grouped" if grouped else "k_tc2d"
     if esz == 8 and ndim >= 2:
         return "k_sweep_f64"
@@ -455,8 +453,6 @@ VARIANTS = [
     ("star512cube_T200_m2", "star512cube", 2, {"block_b": 1}, "f32"),
     ("box256cube_T200_plain", "box256cube", 1, {"block_b": 1}, "f32"),
     ("box256cube_T200_m2", "box256cube", 2, {"block_b": 1}, "f32"),
-    ("box256cube_T200_tc_bf16x3_m2", "box256cube", 2, {"precision": 1}, "f32"),
-    ("box256cube_T200_tc_bf16x1_m2", "box256cube", 2, {"precision": 2}, "f32"),
     ("star4096_T1000_fp64_m4", "star4096", 4, {}, "f64"),
 ]
 

@@ -200,9 +200,6 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
             if (sweep3d_supported(p->r, m, p->pattern)) cands.push_back({0, m, 1, 0, 0});
             if (sweep3d_tb_supported(p->r, m, p->pattern) && 2 * R <= std::min(kGhost, nmin))
                 cands.push_back({0, m, 2, 0, 0});
-            if (m > 1 && p->precision != STENCIL_PREC_FP32 && p->precision != STENCIL_PREC_TF32X3 &&
-                tc3d_supported(R))
-                cands.push_back({1, m, 1, 0, 0});
         } else {
             // a direct kernel, or the counterpart form of c^(m) (which also
             // reaches the folds with no direct kernel, m = 6 and 8)

@@ -330,26 +330,6 @@ cudaError_t launch_tc2d(const CUtensorMap &map, const CUtensorMap &dmap, const T
 cudaError_t launch_grid_mean(const float *origin, int nx, int ny, int64_t py, double *acc,
                              cudaStream_t s);
 
-// ---- tcgen05 folded 3D box sweep (k_tc3d.cu) --------------------------------
-// Output tiles of 128 rows x 32 columns of one plane; 2R+1 plane steps per
-// tile, each the staged tile of plane z+dz times that plane offset's 2R+1
-// Toeplitz panels (2D layout); BF16 hi/lo split.
-constexpr int kTc3MaxR = 4;
-struct TC3DArgs {
-    TC2DArgs t;         // the 2D fields (tiles_x, ntiles = all tiles, dst_py, ...)
-    int nz, tiles_y;
-    int map_z0;         // tensor-map z of the interior origin
-    int64_t dst_pz;
-};
-bool tc3d_supported(int R);
-void tc3d_geometry(int R, int *rows, int *rows_p, int *box_w, int *halo_x);
-size_t tc3d_smem_bytes(int R);
-size_t tc3d_panel_elems(int R);
-// Panels of 3D folded weights cm ((2R+1)^3, axis order (dz, dy, dx)) ordered
-// (dz, dy), with the hi/lo split and the mass correction; returns sum(cm).
-double tc3d_build_panels(const double *cm, int R, uint16_t *host_out);
-cudaError_t launch_tc3d(const CUtensorMap &map, const TC3DArgs &a, int grid, size_t smem,
-                        cudaStream_t s);
 
 // ---- tensor maps ------------------------------------------------------------
 // Encodes a tiled FP32 tensor map over a padded grid's whole allocation.

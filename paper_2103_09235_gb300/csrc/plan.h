@@ -140,9 +140,6 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
                        cudaStream_t s);
 stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
                        cudaStream_t s);
-// 3D folded sweeps on the tensor cores (k_tc3d.cu), plain remainder on CUDA cores.
-stencil_status_t run3d_tc(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
-                          cudaStream_t s);
 // One 3D CUDA-core pass of b (1 or 2) fused sweeps of c = c^(m) from padded
 // grid src to dst (padded origin or the caller's grid).
 stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m, int b,

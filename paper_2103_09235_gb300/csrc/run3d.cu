@@ -66,7 +66,6 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
                        cudaStream_t s)
 {
     int b = p->block_b;
-    bool cuda_core_only = false;
     if (m == 0) {
         if (p->tuned_m == 0 && p->autotune) {
             stencil_status_t st = autotune2d(p, s);
@@ -74,12 +73,7 @@ stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T
         }
         m = p->tuned_m > 0 ? p->tuned_m : 1;
         if (b == 0) b = p->tuned_b;
-        cuda_core_only = p->tuned_engine == 0;
     }
-    // folded sweeps on the tensor cores when a BF16 precision is asked for
-    if (m > 1 && (p->precision == STENCIL_PREC_BF16X3 || p->precision == STENCIL_PREC_BF16X1) &&
-        !cuda_core_only)
-        return run3d_tc(p, in, out, T, m, s);
     if (b <= 0) b = 1;
     if (b > 2) {
         set_error("3D sweep: at most 2 fused sweeps per pass (block_b = %d)", b);

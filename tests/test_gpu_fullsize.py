@@ -213,23 +213,6 @@ def test_3d_T200(env, shape, kind, m, b, seed):
     check(oracle, "3d %s %s m=%d b=%d" % (shape, kind, m, b), y, ref, 1e-5, ZM_FP32)
 
 
-@pytest.mark.parametrize("m,prec", [(2, 1), (2, 2)])
-def test_3d_box_tc_T200(env, m, prec):
-    """The 3D 27-point box 256^3, T = 200, folded m = 2 (125 taps) on the tensor
-    cores: 5 plane steps of 5 Toeplitz panels per output tile, BF16x3 (the
-    single-product BF16x1 error is reported, not asserted)."""
-    _, _, oracle = env
-    shape = (256, 256, 256)
-    x = synth.grid(BASE + 5, shape, np.float32)
-    c = synth.dyadic_coeffs(BASE + 5, 3, 1, "box")
-    facts = {}
-    y = run(env, shape, c, x, 200, m, facts, precision=prec)
-    assert facts["last_m"] == m and facts["last_engine"] == 1
-    ref = oracle.spectral_run(x.astype(np.float64), c, 200)
-    check(oracle, "3d box tc m=%d prec=%d" % (m, prec), y, ref, 1e-5, ZM_BF16X3,
-          report_only=prec == 2)
-
-
 def test_batched_256(env):
     """256 grids, sides uniform in [64, 1024], star/box 50/50, T uniform in [10, 500],
     one persistent launch; every grid within the bounds of its own closed form."""

@@ -160,52 +160,3 @@ def test_tc_tf32x3_rejects_wide_folds(env):
     assert plan.run_status(x, x, 12, 6) == 2  # folded radius 6 > 4: UNSUPPORTED
     plan.close()
 
-
-CASES_3D = [((20, 36, 70), "box", 1, 9, 2), ((16, 130, 40), "star", 1, 8, 2),
-            ((24, 40, 33), "box", 1, 7, 3), ((18, 20, 24), "box", 1, 9, 4),
-            ((12, 150, 64), "box", 2, 5, 2)]
-
-
-@pytest.mark.parametrize("shape,kind,r,T,m", CASES_3D)
-def test_tc3d_parity(env, shape, kind, r, T, m):
-    """3D folded stencils on the tensor cores: per output plane, 2R+1 plane
-    steps of the 2D Toeplitz contraction accumulated in tensor memory
-    (BF16x3 within the FP32 tolerance; BF16x1 reported)."""
-    torch, binding, oracle = env
-    c = synth.dyadic_coeffs(520 + T, 3, r, kind)
-    x = synth.grid(620 + T, shape, np.float32)
-    ref = oracle.run(x.astype(np.float64), c, T)
-    errs = []
-    for prec in (1, 2):
-        plan = binding.Plan(shape, c).set_option("precision", prec)
-        xd = torch.from_numpy(x).cuda()
-        yd = torch.empty_like(xd)
-        plan.run(xd, yd, T, fold_m=m)
-        plan.sync()
-        assert plan.get("last_engine") == 1 and plan.get("last_m") == m
-        errs.append(oracle.rel_l2(yd.cpu().numpy(), ref))
-        plan.close()
-    print("TC 3D %s %s r=%d T=%d m=%d: BF16x3 rel-L2 %.3e, BF16x1 rel-L2 %.3e"
-          % (shape, kind, r, T, m, errs[0], errs[1]))
-    assert errs[0] <= TOL
-    assert errs[1] > errs[0]
-
-
-def test_tc3d_bounded_waits_report_timeout(env):
-    """The 3D tensor-core kernel's waits are bounded like the 2D kernels'."""
-    torch, binding, oracle = env
-    shape, T, m = (16, 40, 64), 6, 2
-    c = synth.dyadic_coeffs(530, 3, 1, "box")
-    x = synth.grid(630, shape, np.float32)
-    plan = binding.Plan(shape, c).set_option("precision", 1)
-    plan.set_option("wait_limit_ms", 50).set_option("fault_withhold_mma", 1)
-    xd = torch.from_numpy(x).cuda()
-    yd = torch.empty_like(xd)
-    plan.run(xd, yd, T, fold_m=m)
-    assert plan.sync_status() == 5
-    assert plan.sync_status() == 0
-    plan.set_option("fault_withhold_mma", 0)
-    plan.run(xd, yd, T, fold_m=m)
-    plan.sync()
-    assert oracle.rel_l2(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= TOL
-    plan.close()
