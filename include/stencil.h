@@ -213,10 +213,19 @@ stencil_status_t stencil_run(stencil_plan_t plan, const void *in, void *out, int
 /*
  * Advances n independent grids in one persistent launch fed by a device work
  * queue (a CUDA graph is captured once per set of plans and replayed).
- *   plans     n plans, each 2D FP32, created on the current device.
- *   in, out   n device pointers each (dense grids of the matching plan).
+ *   plans     n plans, each 2D FP32 of radius 1 or 2, created on the current
+ *             device.
+ *   in, out   n device pointers each (grids in the matching plan's layout,
+ *             pitched where the plan was made by stencil_plan_ex).
  *   T         n step counts (>= 0).
  *   fold_m    n fold factors (1 plain, > 1 folded, 0 automatic) or NULL for 0.
+ *             A fold the batched kernel lacks is lowered to the largest it
+ *             has (the result is the same T steps).  With 0 and no block_b
+ *             option on the grid's plan, the fold and blocking depth come from
+ *             the batch autotuner, which times each class of grids (radius,
+ *             pattern, floor(log2 area)) and caches its choice per class and
+ *             GPU; it also picks the batch's tile height unless plans[0] sets
+ *             the "tile_y" option, which then pins it (at most 128 rows).
  * Grids must not alias one another.  Errors as for stencil_run; a timed-out
  * dependency wait is reported by stencil_sync on plans[0].
  */

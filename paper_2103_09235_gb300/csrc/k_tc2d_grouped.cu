@@ -61,25 +61,13 @@ constexpr uint32_t TMEM_COLS = 512;           // two 256-column accumulators
 constexpr uint32_t TMEM_TILE = 256;
 constexpr int XCH_FLOATS = 4 * (GRP - 1) * (GRP - 1) * kTcN;  // rows handed between warps
 
-// ---- tcgen05 wrappers ------------------------------------------------------
-
-
-
-
-
-
-
-
-// ---- bounded waits shared by all roles --------------------------------------
-
+// Barriers, the tensor-memory base and the abort flag shared by all roles.
 struct Ctl {
     uint64_t stage_full[2], stage_empty[2], a_full[2], a_empty[2], d_full[2], d_empty[2];
     uint32_t tmem_base;
     int abort;
     int epi_ok[2][4];  // per-iteration votes of the four epilogue warps
 };
-
-
 
 }  // namespace
 }  // namespace sg
@@ -111,8 +99,6 @@ __host__ __device__ inline TcLayout tc_layout(int R, int rows, int rows_p, int b
     L.total = L.off_x + XCH_FLOATS * 4;
     return L;
 }
-
-
 
 __global__ void __launch_bounds__(NT, 1)
     k_tc2d_grouped(const __grid_constant__ CUtensorMap map, const __grid_constant__ TC2DArgs a)

@@ -96,6 +96,35 @@ struct BatchBuild {
     double *d_sums = nullptr;  // per-job FP64 grid sums (centred storage), null if none
 };
 
+// The batch's one tile height for per-grid (m, b) choices: the tallest (up to
+// ty_max rows, in steps of 16) whose stages and work buffers fit for the
+// widest halo.  Passes that fuse sweeps free their stage after the first one,
+// so one stage suffices; batches of single sweeps keep two.
+int batch_tile_height(int n, stencil_plan_s *const *plans, const int64_t *T, const int *ms,
+                      const int *bs, int ty_max, size_t max_smem, int *max_h_out = nullptr,
+                      int *nwork_out = nullptr)
+{
+    int max_h = 1, nwork = 0;
+    for (int g = 0; g < n; ++g) {
+        if (T[g] == 0) continue;
+        for (auto &x : grid_passes(plans[g], T[g], ms[g], bs[g])) {
+            max_h = std::max(max_h, x.first * x.second * plans[g]->r);
+            nwork = std::max(nwork, x.second >= 3 ? 2 : x.second - 1);
+        }
+    }
+    const int nstage = nwork > 0 ? 1 : 2;
+    auto smem_for = [&](int ty) {
+        int bf = 0;
+        sweep2d_smem_bytes(ty, max_h, 1, &bf);
+        return batched_smem_bytes(bf, nwork, nstage);
+    };
+    int tile_y = ty_max;
+    while (tile_y > 16 && (smem_for(tile_y) > max_smem || tile_y + 2 * max_h > 256)) tile_y -= 16;
+    if (max_h_out) *max_h_out = max_h;
+    if (nwork_out) *nwork_out = nwork;
+    return tile_y;
+}
+
 // Flattens the batch with per-grid (m, b) choices and a tile height of at
 // most ty_max rows; uploads the work description.
 stencil_status_t flatten_batch(int n, stencil_plan_s *const *plans, const void *const *in,
@@ -110,28 +139,15 @@ stencil_status_t flatten_batch(int n, stencil_plan_s *const *plans, const void *
     std::vector<CUtensorMap> maps;
     std::vector<float> coefs;
     std::map<std::tuple<const void *, int, int>, int> map_index;
-    // one tile height for the whole batch: the tallest (up to ty_max rows)
-    // whose stages and work buffers fit for the widest halo.  Passes that
-    // fuse sweeps free their stage after the first one, so one stage
-    // suffices; batches of single sweeps keep two.
+    // one tile height for the whole batch
     int max_h = 1, nwork = 0;
-    for (int g = 0; g < n; ++g) {
-        if (T[g] == 0) continue;
-        for (auto &x : grid_passes(plans[g], T[g], ms[g], bs[g])) {
-            max_h = std::max(max_h, x.first * x.second * plans[g]->r);
-            nwork = std::max(nwork, x.second >= 3 ? 2 : x.second - 1);
-        }
-    }
+    const int tile_y = batch_tile_height(n, plans, T, ms, bs, ty_max, (size_t)p0->max_smem,
+                                         &max_h, &nwork);
     const int nstage = nwork > 0 ? 1 : 2;
-    int tile_y = ty_max;
     auto smem_for = [&](int ty, int *bf) {
         sweep2d_smem_bytes(ty, max_h, 1, bf);
         return batched_smem_bytes(*bf, nwork, nstage);
     };
-    int bf_probe = 0;
-    while (tile_y > 16 && (smem_for(tile_y, &bf_probe) > (size_t)p0->max_smem ||
-                           tile_y + 2 * max_h > 256))
-        tile_y -= 16;
     int buf_floats = 0;
     for (int g = 0; g < n; ++g) {
         stencil_plan_s *p = plans[g];
@@ -390,10 +406,11 @@ double time_batch(int n, stencil_plan_s *const *plans, const void *const *in, vo
 }
 
 // Chooses (m, b) for every automatic grid (auto_g[g]) and the batch's tile
-// height: cached choices where the cache has them, else coordinate descent
-// over one class at a time (every supported m with b in 1..3), then the tile
-// height (64, 96 or 128 rows), each candidate timed as a whole batched launch
-// that writes scratch outputs, never the caller's grids.
+// height: cached choices where the cache has them, else, for each tile height
+// of 128, 96 and 64 rows, one class at a time among the choices that keep
+// that height, then the whole batch with them; the fastest set wins, the
+// starting choices included.  Every candidate is timed as a
+// batched launch that writes scratch outputs, never the caller's grids.
 stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *const *in,
                             const int64_t *T, const std::vector<bool> &auto_g,
                             std::vector<int> &ms, std::vector<int> &bs, int *ty_out,
@@ -459,8 +476,7 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    // each timing is the best of two launches, and a class is timed on its
-    // own grids only, so that its choice is not lost in the rest of the batch
+    // each timing is the best of two launches
     auto best_of_two = [&](int nn, stencil_plan_s *const *pl, const void *const *ii,
                            void *const *oo, const int64_t *tt, const std::vector<int> &mm,
                            const std::vector<int> &bb_, int ty_) {
@@ -468,52 +484,93 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
         const double t1 = time_batch(nn, pl, ii, oo, tt, mm, bb_, ty_, s, e0, e1);
         return (t0 > 0 && t1 > 0) ? std::min(t0, t1) : -1.0;
     };
+    ensure_device_facts(p0);
+    const size_t max_smem = (size_t)p0->max_smem;
+    // The batch shares one tile height, and a class whose halo or work
+    // buffers need more shared memory shortens every grid's tiles.  So each
+    // candidate height is tried in turn: the classes are tuned one at a time
+    // on their own grids (every supported m, b in 1..3) among the choices
+    // that keep that height, and the whole batch is then timed with them.
+    // The starting choices (defaults, or a class's cached choice) at the
+    // tallest tile that fits them are the baseline a tuned set must beat.
+    // Per class, the (m, b) to cache: the largest over its grids, which the
+    // clamp to a small grid's size may have lowered.
+    std::map<ClassKey, std::pair<int, int>> best_choice;
     for (auto &kv : classes) {
-        const ClassKey &k = kv.first;
-        const std::vector<int> &gs = kv.second;
-        if (!(ms[gs[0]] > 0)) continue;
-        std::vector<stencil_plan_s *> cp;
-        std::vector<const void *> ci;
-        std::vector<void *> co;
-        std::vector<int64_t> ct;
-        for (int g : gs) {
-            cp.push_back(plans[g]);
-            ci.push_back(in[g]);
-            co.push_back(sout[g]);
-            ct.push_back(T[g]);
+        int m = 1, b = 1;
+        for (int g : kv.second) {
+            m = std::max(m, ms[g]);
+            b = std::max(b, bs[g]);
         }
-        std::vector<int> cm(gs.size()), cb(gs.size());
-        int bm = ms[gs[0]], bbst = bs[gs[0]];
-        double best = -1.0;
-        for (int m = 1; m <= 4; ++m) {
-            if (!batched_variant_supported(k.r, m, k.pattern) || clamp_m(plans[gs[0]], m) != m)
-                continue;
-            for (int b = 1; b <= 3; ++b) {
-                for (size_t i = 0; i < gs.size(); ++i) {
-                    cm[i] = clamp_m(cp[i], m);
-                    cb[i] = clamp_b(cp[i], cm[i], b);
-                }
-                const double t = best_of_two((int)gs.size(), cp.data(), ci.data(), co.data(),
-                                             ct.data(), cm, cb, ty);
-                if (t > 0 && (best < 0 || t < best)) {
-                    best = t;
-                    bm = m;
-                    bbst = b;
+        best_choice[kv.first] = {m, b};
+    }
+    std::vector<int> best_ms = ms, best_bs = bs;
+    int best_ty = batch_tile_height(n, plans, T, ms.data(), bs.data(), kBatchTileYMax, max_smem);
+    double best_t = best_of_two(n, plans, in, sout.data(), T, ms, bs, best_ty);
+    for (int ty_c : {128, 96, 64}) {
+        std::vector<int> tm = ms, tb = bs;
+        std::map<ClassKey, std::pair<int, int>> choice = best_choice;
+        for (auto &kv : classes) {
+            const ClassKey &k = kv.first;
+            const std::vector<int> &gs = kv.second;
+            std::vector<stencil_plan_s *> cp;
+            std::vector<const void *> ci;
+            std::vector<void *> co;
+            std::vector<int64_t> ct;
+            for (int g : gs) {
+                cp.push_back(plans[g]);
+                ci.push_back(in[g]);
+                co.push_back(sout[g]);
+                ct.push_back(T[g]);
+            }
+            std::vector<int> cm(gs.size()), cb(gs.size());
+            int bm = 0, bbst = 0;
+            double best = -1.0;
+            for (int m = 1; m <= 4; ++m) {
+                if (!batched_variant_supported(k.r, m, k.pattern) ||
+                    clamp_m(plans[gs[0]], m) != m)
+                    continue;
+                for (int b = 1; b <= 3; ++b) {
+                    for (size_t i = 0; i < gs.size(); ++i) {
+                        cm[i] = clamp_m(cp[i], m);
+                        cb[i] = clamp_b(cp[i], cm[i], b);
+                    }
+                    if (batch_tile_height((int)gs.size(), cp.data(), ct.data(), cm.data(),
+                                          cb.data(), ty_c, max_smem) != ty_c)
+                        continue;
+                    const double t = best_of_two((int)gs.size(), cp.data(), ci.data(),
+                                                 co.data(), ct.data(), cm, cb, ty_c);
+                    if (t > 0 && (best < 0 || t < best)) {
+                        best = t;
+                        bm = m;
+                        bbst = b;
+                    }
                 }
             }
+            if (bm == 0) continue;  // no choice keeps this height: the class keeps its start
+            choice[k] = {bm, bbst};
+            for (int g : gs) {
+                tm[g] = clamp_m(plans[g], bm);
+                tb[g] = clamp_b(plans[g], tm[g], bbst);
+            }
         }
-        apply(k, bm, bbst);
-        char v[32];
-        snprintf(v, sizeof(v), "%d %d", bm, bbst);
-        tune_cache_put(class_cache_key(k, prop.name), v);
+        const int ty_real = batch_tile_height(n, plans, T, tm.data(), tb.data(), ty_c, max_smem);
+        const double t = best_of_two(n, plans, in, sout.data(), T, tm, tb, ty_real);
+        if (t > 0 && (best_t < 0 || t < best_t)) {
+            best_t = t;
+            best_ms = tm;
+            best_bs = tb;
+            best_ty = ty_real;
+            best_choice = choice;
+        }
     }
-    double best = -1.0;
-    for (int t : {128, 96, 64}) {
-        const double tt = best_of_two(n, plans, in, sout.data(), T, ms, bs, t);
-        if (tt > 0 && (best < 0 || tt < best)) {
-            best = tt;
-            ty = t;
-        }
+    ms = best_ms;
+    bs = best_bs;
+    ty = best_ty;
+    for (auto &kv : best_choice) {
+        char v[32];
+        snprintf(v, sizeof(v), "%d %d", kv.second.first, kv.second.second);
+        tune_cache_put(class_cache_key(kv.first, prop.name), v);
     }
     char v[16];
     snprintf(v, sizeof(v), "%d", ty);
@@ -567,6 +624,7 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
     key.push_back(p0->wait_ms);
     key.push_back(p0->fault_withhold_dep);
     key.push_back(p0->autotune);
+    key.push_back(p0->tile_y);
 
     if (p0->use_graph && p0->graphs.find(key) != p0->graphs.end())  // a batch seen before
         return run_maybe_graph(p0, key, s, [](cudaStream_t, int *) { return STENCIL_ERR_CUDA; });
@@ -585,6 +643,8 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
     int ty = kBatchTileYMax;
     stencil_status_t st = tune_batch(n, plans, in, T, auto_g, ms, bs, &ty, s);
     if (st != STENCIL_OK) return st;
+    // the first plan's tile_y option pins the batch's tile height
+    if (p0->tile_y > 0) ty = std::min(p0->tile_y, kBatchTileYMax);
 
     // ---- flatten the batch (host, once per distinct batch)
     BatchBuild bb;

@@ -155,6 +155,21 @@ def test_batched_uses_cached_choice(env, tmp_path, monkeypatch):
         p.close()
 
 
+@pytest.mark.parametrize("tile", [64, 96])
+def test_batched_tile_pinned_by_first_plan(env, tile):
+    """The first plan's tile_y option pins the batch's tile height."""
+    torch, binding, oracle = env
+    plans, xs, ys, refs_in = _batch_plans(binding, torch, SPECS)
+    plans[0].set_option("tile_y", tile)
+    binding.run_batched(plans, xs, ys, [t for _, _, t in refs_in], [3, 2, 3, 2])
+    plans[0].sync()
+    assert all(p.get("last_tile_y") == tile for p in plans)
+    for y, (x, c, T) in zip(ys, refs_in):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
+    for p in plans:
+        p.close()
+
+
 @pytest.mark.parametrize("fold", [None, 1, 2, 8])
 def test_batched_radius2_and_fold_clamp(env, fold):
     """Radius-2 bases (stars folded up to m = 2, boxes plain) beside radius-1
