@@ -129,6 +129,9 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *   "cta_threads"   threads per CTA of the 2D CUDA-core sweep: 0 = automatic
  *                   (chosen by the autotuner, else the kernel's own size), 256 =
  *                   two half-size CTAs per SM for folded sweeps that run 512.
+ *   "z_chunk"       3D sweeps: output planes per CTA, a multiple of 4 in 4..1024
+ *                   (0 = automatic: 16 for a single radius-1 sweep, else 32, halved
+ *                   down to 8 while the grid has fewer than 4 CTAs per SM).
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
  *   "center"        2D/3D CUDA-core runs and batches: 1 = store the grid minus its mean
  *                   mu (from an FP64 sum of the input) and add mu * (sum c)^T to the

@@ -38,6 +38,7 @@ struct stencil_plan_s {
     int tile_y = 0;
     int stages = 0;  // TMA stages per CTA of the 2D sweep (0 = automatic)
     int cta_threads = 0;  // threads per CTA of the 2D sweep (0 = automatic, or 256)
+    int z_chunk = 0;  // output planes per CTA of the 3D sweeps (0 = automatic)
     int tc_center = 1;
     int tc_tma_store = 1;
     int tc_form = 0;  // tensor cores: 0 by folded radius, 1 one MMA per row offset, 2 grouped

@@ -32,6 +32,7 @@ stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m, int 
     // bound the tail; measured on GB300 at 512^3 and 256^3
     int zc = (b == 1 && R <= 1) ? 16 : 32;
     while (zc > 8 && (int64_t)a.ntiles_xy * ceil_div(p->nz, zc) < 4 * p->sm_count) zc /= 2;
+    if (p->z_chunk > 0) zc = p->z_chunk;  // the plan's option
     a.zchunk = zc;
     a.zchunks = ceil_div(p->nz, zc);
     a.ntiles = a.ntiles_xy * a.zchunks;

@@ -353,6 +353,9 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "cta_threads")) {
         if (v != 0 && v != 256) goto bad;
         p->cta_threads = (int)v;
+    } else if (!strcmp(key, "z_chunk")) {
+        if (v != 0 && (v < 4 || v > 1024 || v % 4)) goto bad;
+        p->z_chunk = (int)v;
     } else if (!strcmp(key, "stages")) {
         if (v < 0 || v > 6) goto bad;
         p->stages = (int)v;
