@@ -351,6 +351,8 @@ def roofline_of(alg_bytes, alg_flops, pass_ms, esz, engine, sms):
 
 def kernel_name(engine, grouped, ndim, b, cp_k, esz=4):
     if engine == "tensor-core":
+        if ndim == 3:  # one launch per plane offset, then the re-import of the result
+            return "k_tc2d per plane offset + k_import"
         return "k_tc2d_grouped" if grouped else "k_tc2d"
     if esz == 8 and ndim >= 2:
         return "k_sweep_f64"
@@ -453,6 +455,8 @@ VARIANTS = [
     ("star512cube_T200_m2", "star512cube", 2, {"block_b": 1}, "f32"),
     ("box256cube_T200_plain", "box256cube", 1, {"block_b": 1}, "f32"),
     ("box256cube_T200_m2", "box256cube", 2, {"block_b": 1}, "f32"),
+    ("box256cube_T200_tc_bf16x3_m2", "box256cube", 2, {"precision": 1}, "f32"),
+    ("box256cube_T200_tc_bf16x1_m2", "box256cube", 2, {"precision": 2}, "f32"),
     ("star4096_T1000_fp64_m4", "star4096", 4, {}, "f64"),
 ]
 
@@ -716,7 +720,8 @@ def run_gpu(args):
     # way; reported beside the headline, not folded into it
     variants = {}
     if not args.no_variants:
-        variants = measure_variants(torch, binding, dev, stream, flush, sampler, leg, sms)
+        only = [v for v in args.variants.split(",") if v] or None
+        variants = measure_variants(torch, binding, dev, stream, flush, sampler, leg, sms, only)
     sampler.stop()
 
     if rank == 0:
@@ -763,12 +768,14 @@ def main():
                     help="rows per 2D tile (0 = the autotuner's or the library's choice)")
     ap.add_argument("--tc-form", type=int, default=0, choices=[0, 1, 2],
                     help="tensor-core kernel: 0 by folded radius, 1 per row offset, 2 grouped")
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2],
-                    help="0 = FP32 CUDA cores, 1 = BF16x3 tensor cores, 2 = BF16x1")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="0 = FP32 CUDA cores, 1 = BF16x3 tensor cores, 2 = BF16x1, 3 = TF32x3")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the CPU-baseline leg (and with it the accuracy checks)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variants", default="",
+                    help="comma-separated variant names to time (default: all)")
     ap.add_argument("--ncu", action="store_true",
                     help="profiling run: timed loop only, no L2 flush buffer, no extra legs")
     args = ap.parse_args()

@@ -56,8 +56,8 @@ typedef enum {
 /* Values of the "precision" option. */
 typedef enum {
     STENCIL_PREC_FP32 = 0,    /* CUDA-core FP32 sweeps (default)                          */
-    STENCIL_PREC_BF16X3 = 1,  /* folded 2D box on tcgen05: BF16 hi/lo split, 3 products,
-                                 FP32 accumulation in tensor memory                        */
+    STENCIL_PREC_BF16X3 = 1,  /* folded 2D/3D sweeps on tcgen05: BF16 hi/lo split, 3
+                                 products, FP32 accumulation in tensor memory              */
     STENCIL_PREC_BF16X1 = 2,  /* as BF16X3 with the hi*hi product only (error study)      */
     STENCIL_PREC_TF32X3 = 3   /* as BF16X3 with TF32 hi/lo operands (kind::tf32): about 22
                                  significant bits per operand pair instead of 16; folded
@@ -111,8 +111,13 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
 
 /*
  * Sets a tuning option (all optional).  Keys:
- *   "precision"     stencil_precision_t; BF16 modes run folded 2D sweeps (m > 1,
- *                   m*r <= 8) on the tensor cores; plain steps stay on CUDA cores.
+ *   "precision"     stencil_precision_t; the BF16 and TF32 modes run folded 2D and
+ *                   3D sweeps (explicit m > 1, m*r <= 8, TF32 m*r <= 4) on the tensor
+ *                   cores; plain steps stay on CUDA cores.  A 3D folded sweep is the
+ *                   sum over the 2m*r+1 plane offsets dz of the 2D folded sweep with
+ *                   that plane slice of c^(m) applied to the plane dz away (Section
+ *                   3.3, a 3D grid as a stack of 2D slices): one tensor-core launch
+ *                   per offset over all planes, accumulated in the output grid.
  *   "block_b"       temporal-blocking depth: folded sweeps per memory round trip
  *                   (0 = automatic; 1..64, and 2D/3D passes take as many as their
  *                   halo allows).

@@ -304,6 +304,17 @@ struct TC2DArgs {
                             // the other roles' bounded waits run out)
     int *status;
     unsigned long long wait_ns;
+    // Per-offset kernel only: a stack of nplanes 2D grids (the planes of a 3D
+    // grid seen as one tall 2D array whose planes start src_plane_rows rows
+    // apart), each tile reading the plane dz away from the one it writes;
+    // outputs land dst_pz floats apart per plane and, with accumulate, are
+    // added to what the destination holds.  2D: nplanes = 1, the rest 0.
+    int tiles_y;            // tiles per plane in y
+    int nplanes;
+    int64_t src_plane_rows;
+    int dz;
+    int64_t dst_pz;
+    int accumulate;
 };
 bool tc2d_supported(int R);
 bool tc2d_tf32_supported(int R);

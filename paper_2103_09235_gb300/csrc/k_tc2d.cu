@@ -214,10 +214,15 @@ __global__ void __launch_bounds__(NT, 1)
             for (int tile = first; tile < a.ntiles; tile += step, ++i) {
                 const int s = i & 1, k = i >> 1;
                 if (!wait_or_abort(&ctl->stage_empty[s], (k & 1) ^ 1, ctl, a)) break;
-                const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+                const int per_plane = a.tiles_x * a.tiles_y;
+                const int pl = tile / per_plane, t2 = tile % per_plane;
+                const int tx = t2 % a.tiles_x, ty = t2 / a.tiles_x;
+                // rows of the source plane dz away from the output plane (2D: pl = dz = 0)
+                const int y_src = a.map_y0 + (int)((int64_t)(pl + a.dz) * a.src_plane_rows) +
+                                  ty * kTcM - R;
                 mbar_arrive_expect_tx(&ctl->stage_full[s], bytes);
                 tma_load_2d(smem + L.off_stage + s * L.stage_bytes, &map, &ctl->stage_full[s],
-                            a.map_x0 + tx * kTcN - a.halo_x, a.map_y0 + ty * kTcM - R);
+                            a.map_x0 + tx * kTcN - a.halo_x, y_src);
                 last = i;
             }
             if (ctl->abort && last >= 0)
@@ -361,19 +366,41 @@ __global__ void __launch_bounds__(NT, 1)
             tmem_ld_wait();
             tc_fence_before();
             mbar_arrive(&ctl->d_empty[s]);
-            const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+            const int per_plane = a.tiles_x * a.tiles_y;
+            const int pl = tile / per_plane, t2 = tile % per_plane;
+            const int tx = t2 % a.tiles_x, ty = t2 / a.tiles_x;
             const int Y = ty * kTcM + 32 * q + lane;
             const int X0 = tx * kTcN;
             float o[32];
 #pragma unroll
             for (int n = 0; n < 32; ++n) o[n] = v0[n] + (a.terms == 3 ? v1[n] : 0.f) + musum;
+            float *const dplane = a.dst + (int64_t)pl * a.dst_pz;
+            if (a.accumulate && Y < a.ny) {
+                // add the partial result of the other plane offsets (stacked
+                // grids take direct stores, never the TMA store)
+                const float *row = dplane + Y * a.dst_py + X0;
+                if (a.dst_vec4 && X0 + 32 <= a.nx) {
+#pragma unroll
+                    for (int n = 0; n < 32; n += 4) {
+                        const float4 t = *reinterpret_cast<const float4 *>(row + n);
+                        o[n] += t.x;
+                        o[n + 1] += t.y;
+                        o[n + 2] += t.z;
+                        o[n + 3] += t.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int n = 0; n < 32; ++n)
+                        if (X0 + n < a.nx) o[n] += row[n];
+                }
+            }
             // Only tiles wholly inside the grid leave by TMA store.  A store box
             // clipped by the grid edge in x and y at once (a 97 x 203 grid)
             // gave wrong values beside the clipped tile, so ragged tiles take
             // the direct stores.  The decision is the same for the four
             // epilogue warps, which all reach the barriers of the store path.
-            const bool via_tma =
-                a.tma_store && X0 + kTcN <= a.nx && (ty + 1) * kTcM <= a.ny;
+            const bool via_tma = a.tma_store && a.nplanes == 1 && !a.accumulate &&
+                                 X0 + kTcN <= a.nx && (ty + 1) * kTcM <= a.ny;
             if (via_tma) {
                 // row 32q+lane of the swizzled tile: 16-byte chunk j lands at j ^ (row & 7)
                 const int row = 32 * q + lane;
@@ -389,7 +416,7 @@ __global__ void __launch_bounds__(NT, 1)
                 if (tid == 256) tma_store_2d(&dmap, tile_s, X0, ty * kTcM);
             }
             if (Y < a.ny) {
-                float *row = a.dst + Y * a.dst_py + X0;
+                float *row = dplane + Y * a.dst_py + X0;
                 if (via_tma) {
                     // the bulk store wrote the interior; only ghost copies remain
                 } else if (a.dst_vec4 && X0 + 32 <= a.nx) {
@@ -402,7 +429,7 @@ __global__ void __launch_bounds__(NT, 1)
                     for (int n = 0; n < 32; ++n)
                         if (X0 + n < a.nx) row[n] = o[n];
                 }
-                if (a.dst_gw > 0 && (X0 < a.dst_gw || X0 + 32 > a.nx - a.dst_gw ||
+                if (a.dst_gw > 0 && a.nplanes == 1 && (X0 < a.dst_gw || X0 + 32 > a.nx - a.dst_gw ||
                                      Y < a.dst_gw || Y >= a.ny - a.dst_gw)) {
 #pragma unroll
                     for (int n = 0; n < 32; ++n)

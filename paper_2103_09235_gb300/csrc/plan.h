@@ -141,6 +141,10 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
                        cudaStream_t s);
 stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
                        cudaStream_t s);
+// Folded 3D sweeps on the tensor cores (explicit m > 1 with a BF16 or TF32
+// precision): per sweep, one per-offset tensor-core launch per plane offset.
+stencil_status_t run3d_tc(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
+                          cudaStream_t s);
 // One 3D CUDA-core pass of b (1 or 2) fused sweeps of c = c^(m) from padded
 // grid src to dst (padded origin or the caller's grid).
 stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m, int b,

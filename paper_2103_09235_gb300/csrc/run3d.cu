@@ -66,6 +66,8 @@ stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m, int 
 stencil_status_t run3d(stencil_plan_s *p, const float *in, float *out, int64_t T, int m,
                        cudaStream_t s)
 {
+    // an explicit fold with a BF16 or TF32 precision runs on the tensor cores
+    if (m > 1 && p->precision != STENCIL_PREC_FP32) return run3d_tc(p, in, out, T, m, s);
     int b = p->block_b;
     if (m == 0) {
         if (p->tuned_m == 0 && p->autotune) {

@@ -206,7 +206,7 @@ def test_sepbox8192_T512(env, sepbox8192, m, opts, cp):
                                                  ((256, 256, 256), "box", 1, 2, 5)])
 def test_3d_T200(env, shape, kind, m, b, seed):
     """3D 7-point star 512^3 and 27-point box 256^3, T = 200: plain, folded m = 2,
-    and two fused sweeps per pass (temporal blocking)."""
+    and two fused sweeps per pass (temporal blocking), on the CUDA cores."""
     _, _, oracle = env
     x = synth.grid(BASE + seed, shape, np.float32)
     c = synth.dyadic_coeffs(BASE + seed, 3, 1, kind)
@@ -215,6 +215,25 @@ def test_3d_T200(env, shape, kind, m, b, seed):
     assert facts["last_m"] == m and facts["last_b"] == b
     ref = oracle.spectral_run(x.astype(np.float64), c, 200)
     check(oracle, "3d %s %s m=%d b=%d" % (shape, kind, m, b), y, ref, 1e-5, ZM_FP32)
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_3d_box256_tc_T200(env, prec):
+    """27-point box 256^3, T = 200, folded m = 2 on the tensor cores (per sweep,
+    one launch per plane offset accumulated in the output): BF16x3 and TF32x3
+    within the tensor-core bounds; the single-product BF16 error reported."""
+    _, _, oracle = env
+    shape = (256, 256, 256)
+    x = synth.grid(BASE + 5, shape, np.float32)
+    c = synth.dyadic_coeffs(BASE + 5, 3, 1, "box")
+    facts = {}
+    y = run(env, shape, c, x, 200, 2, facts, precision=prec)
+    assert facts["last_m"] == 2 and facts["last_engine"] == 1
+    ref = oracle.spectral_run(x.astype(np.float64), c, 200)
+    err, _ = check(oracle, "3d box256 tc precision %d m=2" % prec, y, ref, 1e-5, ZM_TC,
+                   report_only=prec == 2)
+    if prec == 2:
+        assert err > 1e-7
 
 
 def test_batched_256(env):

@@ -160,3 +160,74 @@ def test_tc_tf32x3_rejects_wide_folds(env):
     assert plan.run_status(x, x, 12, 6) == 2  # folded radius 6 > 4: UNSUPPORTED
     plan.close()
 
+
+
+TC3D_CASES = [
+    # shape (z, y, x), kind, r, T, m
+    ((40, 36, 70), "box", 1, 7, 2),      # three folded sweeps and one plain step
+    ((20, 30, 40), "box", 1, 4, 2),      # no remainder
+    ((33, 140, 64), "star", 1, 9, 4),    # two ragged y tiles per plane
+    ((24, 24, 24), "box", 2, 5, 2),      # folded radius 4
+    ((12, 9, 70), "star", 1, 6, 2),      # ghost bands overlapping in z and y
+]
+
+
+@pytest.mark.parametrize("shape,kind,r,T,m", TC3D_CASES)
+def test_tc3d_parity(env, shape, kind, r, T, m):
+    """3D folded sweeps on the tensor cores: per sweep one per-offset launch per
+    plane offset dz, over every plane, the terms added in the output grid."""
+    torch, binding, oracle = env
+    c = synth.dyadic_coeffs(3700 + r, 3, r, kind)
+    x = synth.grid(3800 + T, shape, np.float32)
+    ref = oracle.run(x.astype(np.float64), c, T)
+    errs = {}
+    for prec in (1, 2) + ((3,) if m * r <= 4 else ()):
+        plan = binding.Plan(shape, c).set_option("precision", prec)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.empty_like(xd)
+        plan.run(xd, yd, T, fold_m=m)
+        plan.sync()
+        assert plan.get("last_engine") == 1 and plan.get("last_m") == m
+        errs[prec] = oracle.rel_l2(yd.cpu().numpy(), ref)
+        plan.close()
+    print("TC 3D %s %s r=%d T=%d m=%d: %s" % (shape, kind, r, T, m,
+          ", ".join("prec %d rel-L2 %.3e" % kv for kv in sorted(errs.items()))))
+    assert errs[1] <= TOL and errs[2] > errs[1]
+    if 3 in errs:
+        assert errs[3] <= TOL
+
+
+def test_tc3d_in_place_and_uncentred(env):
+    """in == out, and the split without subtracting the grid mean."""
+    torch, binding, oracle = env
+    shape = (30, 40, 50)
+    c = synth.dyadic_coeffs(3900, 3, 1, "box")
+    x = synth.grid(3901, shape, np.float32)
+    ref = oracle.run(x.astype(np.float64), c, 9)
+    plan = binding.Plan(shape, c).set_option("precision", 1).set_option("tc_center", 0)
+    xd = torch.from_numpy(x).cuda()
+    plan.run(xd, xd, 9, fold_m=2)
+    plan.sync()
+    assert oracle.rel_l2(xd.cpu().numpy(), ref) <= TOL
+    plan.close()
+
+
+def test_tc3d_bounded_waits_report_timeout(env):
+    """With the hook that stops the MMA issuer, the 3D tensor-core terms' waits
+    run out, the status reads TIMEOUT, and the next run matches the oracle."""
+    torch, binding, oracle = env
+    shape, T, m = (20, 30, 40), 5, 2
+    c = synth.dyadic_coeffs(3902, 3, 1, "box")
+    x = synth.grid(3903, shape, np.float32)
+    plan = binding.Plan(shape, c).set_option("precision", 1)
+    plan.set_option("wait_limit_ms", 50).set_option("fault_withhold_mma", 1)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, T, fold_m=m)
+    assert plan.sync_status() == 5
+    assert plan.sync_status() == 0
+    plan.set_option("fault_withhold_mma", 0)
+    plan.run(xd, yd, T, fold_m=m)
+    plan.sync()
+    assert oracle.rel_l2(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= TOL
+    plan.close()
