@@ -23,6 +23,26 @@ __device__ __forceinline__ double warp_sum(double s)
     return s;
 }
 
+// A lane's FP32 share of one row: 16-byte loads where the row allows them.
+// The sum only fixes the centring constant, which is subtracted and added back
+// unchanged, so the FP32 rounding of these partial sums does not reach the
+// result; FP64 then gathers the rows.
+__device__ __forceinline__ float row_share(const float *__restrict__ row, int nx, int lane)
+{
+    float fs = 0.f;
+    int x0 = 0;
+    if ((reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+        for (int i = lane; i < nx / 4; i += 32) {
+            const float4 t = r4[i];
+            fs += (t.x + t.y) + (t.z + t.w);
+        }
+        x0 = nx / 4 * 4;
+    }
+    for (int x = x0 + lane; x < nx; x += 32) fs += row[x];
+    return fs;
+}
+
 // acc[0] += sum of the nx * ny * nz points (rows py, planes pz apart).
 __global__ void k_sum_grid(const float *__restrict__ src, int nx, int ny, int nz, int64_t py,
                            int64_t pz, double *__restrict__ acc)
@@ -32,10 +52,8 @@ __global__ void k_sum_grid(const float *__restrict__ src, int nx, int ny, int nz
     const int lane = threadIdx.x & 31;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long r = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); r < rows;
-         r += nwarps) {
-        const float *row = src + (r / ny) * pz + (r % ny) * py;
-        for (int x = lane; x < nx; x += 32) s += (double)row[x];
-    }
+         r += nwarps)
+        s += (double)row_share(src + (r / ny) * pz + (r % ny) * py, nx, lane);
     s = warp_sum(s);
     if (lane == 0) atomicAdd(acc, s);
 }
@@ -77,9 +95,7 @@ __global__ void k_sum_batch(const ImportJob *__restrict__ jobs, int njobs, long 
         const ImportJob &J = jobs[job_of(jobs, njobs, row)];
         const int y = (int)(row - J.row0) - J.gw;
         if (y < 0 || y >= J.ny || !J.mean_sum) continue;
-        const float *srow = J.src + y * J.src_py;
-        double s = 0.0;
-        for (int x = lane; x < J.nx; x += 32) s += (double)srow[x];
+        double s = (double)row_share(J.src + y * J.src_py, J.nx, lane);
         s = warp_sum(s);
         if (lane == 0) atomicAdd(J.mean_sum, s);
     }

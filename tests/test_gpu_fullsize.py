@@ -156,8 +156,9 @@ def box8192(env):
 def test_box8192_T512(env, box8192, m, opts):
     """2D 9-point box 8192^2, T = 512: plain; CUDA-core folded m = 2, b = 2 (the
     autotuner's pick, 160-row tiles); folded m = 4 (9x9), 6 and 8 (17x17) on the
-    tensor cores with the BF16 hi/lo split, through both tensor-core kernels.
-    The single-product BF16 error is reported, not asserted."""
+    tensor cores with the BF16 hi/lo split, through both tensor-core kernels,
+    and with TF32 operands.  The single-product BF16 error is reported, not
+    asserted."""
     _, _, oracle = env
     x, c, ref = box8192
     facts = {}

@@ -231,3 +231,4 @@ def test_tc3d_bounded_waits_report_timeout(env):
     plan.sync()
     assert oracle.rel_l2(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= TOL
     plan.close()
+
