@@ -130,7 +130,8 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *                   pass refills a stage after the tile's first sweep, and a
  *                   counterpart-form pass after its first vertical fold, so 1
  *                   still overlaps copies with compute; a direct single-sweep
- *                   pass with 1 stage does not.
+ *                   pass with 1 stage does not.  3D single sweeps: 2 or 3
+ *                   stages of four planes (other values: 2).
  *   "cta_threads"   threads per CTA of the 2D CUDA-core sweep: 0 = automatic
  *                   (chosen by the autotuner, else the kernel's own size), 256 =
  *                   two half-size CTAs per SM for folded sweeps that run 512.

@@ -145,6 +145,7 @@ struct Sweep3DArgs {
     int halo_x;                 // R rounded up to a multiple of 4
     int map_x0, map_y0, map_z0;
     int buf_floats;             // floats per shared-memory plane slot
+    int nst;                    // single sweeps: TMA stages of the ring (2 or 3)
     float *dst;
     int64_t dst_py, dst_pz;
     int dst_gw;
@@ -154,7 +155,7 @@ struct Sweep3DArgs {
     float c[kMaxTaps3D];
 };
 bool sweep3d_supported(int rb, int m, int pattern);
-size_t sweep3d_smem_bytes(int tile_y, int R, int *buf_floats);
+size_t sweep3d_smem_bytes(int tile_y, int R, int *buf_floats, int nst = 3);
 cudaError_t launch_sweep3d(int rb, int m, int pattern, const CUtensorMap &map,
                            const Sweep3DArgs &a, int grid, size_t smem, cudaStream_t s);
 int sweep3d_ctas_per_sm(int rb, int m, int pattern, size_t smem);

@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(NT3)
     const int zin0 = z0 - R, nin = (z1 - z0) + 2 * R;  // input planes streamed
     const int nchunks = (nin + ZC - 1) / ZC;
 
+    const int NST = a.nst;          // TMA stages (2 or 3)
     uint64_t *empty = bars + NST;  // released by the 8 consumer warps
     if (tid == 0) {
         prefetch_tensormap(&map);
@@ -204,13 +205,13 @@ bool sweep3d_supported(int rb, int m, int pattern)
     return false;
 }
 
-size_t sweep3d_smem_bytes(int tile_y, int R, int *buf_floats)
+size_t sweep3d_smem_bytes(int tile_y, int R, int *buf_floats, int nst)
 {
     (void)tile_y;
     const int HX = round_up(R, 4);
     const int bf = round_up((TX3 + 2 * HX) * (TY3 + 2 * R) * ZC, 32);
     if (buf_floats) *buf_floats = bf;
-    return 1024 + (size_t)NST * bf * 4;
+    return 1024 + (size_t)nst * bf * 4;
 }
 
 int sweep3d_ctas_per_sm(int rb, int m, int pattern, size_t smem)

@@ -43,7 +43,13 @@ stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m, int 
     a.map_y0 = src.gy;
     a.map_z0 = src.gz;
     int bf = 0;
-    const size_t smem = b == 2 ? sweep3d_tb_smem_bytes(R, &bf) : sweep3d_smem_bytes(kTY3, R, &bf);
+    // ring stages of a single sweep: the plan's option (2 or 3), else 2 --
+    // measured on GB300, two stages let a fourth CTA onto each SM (shared
+    // memory held three) and were never slower: 256^3 box 377 vs 349 GS/s,
+    // 384^3 box 509 vs 476, 512^3 star m = 2 1003 vs 955, plain star equal
+    a.nst = (p->stages == 2 || p->stages == 3) ? p->stages : 2;
+    const size_t smem = b == 2 ? sweep3d_tb_smem_bytes(R, &bf)
+                               : sweep3d_smem_bytes(kTY3, R, &bf, a.nst);
     a.buf_floats = bf;
     a.dst = dst;
     a.dst_py = dst_py;

@@ -365,12 +365,14 @@ CASES_3D = [
 ]
 
 
+@pytest.mark.parametrize("stages", [0, 2, 3])
 @pytest.mark.parametrize("shape,kind,r,T,m", CASES_3D)
-def test_sweep3d_parity(env, shape, kind, r, T, m):
+def test_sweep3d_parity(env, shape, kind, r, T, m, stages):
+    """Single 3D sweeps with the automatic ring and with 2 and 3 stages."""
     _, _, oracle = env
     c = synth.dyadic_coeffs(3100 + r, 3, r, kind)
     x = synth.grid(3200 + T, shape, np.float32)
-    y, info = gpu_run(env, shape, c, x, T, m)
+    y, info = gpu_run(env, shape, c, x, T, m, block_b=1, stages=stages)
     ref = oracle.run(x.astype(np.float64), c, T)
     check(y, ref)
     assert info["m"] == m
