@@ -78,6 +78,99 @@ __global__ void __launch_bounds__(NTT) k_tess_tri(const __grid_constant__ Tess1D
     }
 }
 
+// FP32 stage 1 for radius 4 and up: each thread advances strips of 8
+// consecutive points from 16-byte shared-memory loads, as the overlapped
+// kernel does (k_sweep1d.cu).  Both arrays carry a pad so that strips cut by
+// the region's edge still load whole words; a strip writes only the points
+// of its step's region, since the points outside keep the older levels that
+// the export and stage 2 read.
+template <int R>
+struct TriStrip {
+    static constexpr int V = 8;
+    static constexpr int RP = (R + 3) / 4 * 4;
+    static constexpr int NSEG = V + 2 * RP;
+    static constexpr int PAD = RP + V;
+};
+
+template <int R>
+__host__ __device__ constexpr int tri_buf_floats(int wmax)
+{
+    return TriStrip<R>::PAD + (wmax + TriStrip<R>::V - 1) / TriStrip<R>::V * TriStrip<R>::V +
+           TriStrip<R>::PAD;
+}
+
+template <int R>
+__global__ void __launch_bounds__(NTT) k_tess_tri_f32(const __grid_constant__ Tess1DArgs a)
+{
+    using S = TriStrip<R>;
+    constexpr int V = S::V, RP = S::RP, NSEG = S::NSEG, PAD = S::PAD;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int j = blockIdx.x;
+    const long long x0 = (long long)j * a.W;
+    const int Wj = (j == a.ntiles - 1) ? (int)(a.n - x0) : a.W;
+    float *buf0 = reinterpret_cast<float *>(smem) + PAD;  // element 0 of each array
+    float *buf1 = buf0 + tri_buf_floats<R>(a.wmax);
+    const float *__restrict__ src = static_cast<const float *>(a.src);
+    float *__restrict__ dst = static_cast<float *>(a.dst);
+    float *__restrict__ par0 = static_cast<float *>(a.par0);
+    float *__restrict__ par1 = static_cast<float *>(a.par1);
+    float w[2 * R + 1];
+    load_weights<float, R>(a, w);
+
+    for (int i = threadIdx.x; i < Wj; i += NTT) {
+        const float v = src[x0 + i];
+        buf0[i] = v;
+        buf1[i] = v;  // level 0 in both arrays: never read as level 1, but defined
+    }
+    __syncthreads();
+    for (int s = 1; s <= a.b; ++s) {
+        const float *in = (s & 1) ? buf0 : buf1;
+        float *out = (s & 1) ? buf1 : buf0;
+        const int lo = tess::s1_lo(s, R), hi = tess::s1_hi(s, R, Wj);
+        const int g0 = lo / V, g1 = (hi + V - 1) / V;
+        for (int g = g0 + (int)threadIdx.x; g < g1; g += NTT) {
+            const int k0 = g * V;
+            float seg[NSEG];
+            const float4 *rp = reinterpret_cast<const float4 *>(in + k0 - RP);
+#pragma unroll
+            for (int q = 0; q < NSEG / 4; ++q) {
+                const float4 t = rp[q];
+                seg[4 * q] = t.x;
+                seg[4 * q + 1] = t.y;
+                seg[4 * q + 2] = t.z;
+                seg[4 * q + 3] = t.w;
+            }
+            float acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                float t = 0.f;
+#pragma unroll
+                for (int k = 0; k < 2 * R + 1; ++k) t = fmaf(w[k], seg[v + k - R + RP], t);
+                acc[v] = t;
+            }
+            if (k0 >= lo && k0 + V <= hi) {
+                float4 *op = reinterpret_cast<float4 *>(out + k0);
+                op[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                op[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (k0 + v >= lo && k0 + v < hi) out[k0 + v] = acc[v];
+            }
+        }
+        __syncthreads();
+    }
+    const float *top = (a.b & 1) ? buf1 : buf0;
+    const int E = tess::s2_half(a.b, R);
+    for (int i = threadIdx.x; i < Wj; i += NTT) {
+        if (i < E || i >= Wj - E) {
+            par0[x0 + i] = buf0[i];
+            par1[x0 + i] = buf1[i];
+        }
+        if (i >= tess::s1_lo(a.b, R) && i < tess::s1_hi(a.b, R, Wj)) dst[x0 + i] = top[i];
+    }
+}
+
 template <typename T, int R>
 __global__ void __launch_bounds__(NTT) k_tess_inv(const __grid_constant__ Tess1DArgs a)
 {
@@ -123,9 +216,17 @@ __global__ void __launch_bounds__(NTT) k_tess_inv(const __grid_constant__ Tess1D
 template <typename T, int R>
 cudaError_t launch_t(const Tess1DArgs &a, cudaStream_t s)
 {
-    cudaError_t e = smem_optin((const void *)k_tess_tri<T, R>);
-    if (e != cudaSuccess) return e;
-    k_tess_tri<T, R><<<a.ntiles, NTT, 2 * sizeof(T) * (size_t)a.wmax, s>>>(a);
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4 && R >= 4) {  // strips, as in k_sweep1d.cu
+        e = smem_optin((const void *)k_tess_tri_f32<R>);
+        if (e != cudaSuccess) return e;
+        k_tess_tri_f32<R><<<a.ntiles, NTT, 2 * sizeof(float) * (size_t)tri_buf_floats<R>(a.wmax),
+                            s>>>(a);
+    } else {
+        e = smem_optin((const void *)k_tess_tri<T, R>);
+        if (e != cudaSuccess) return e;
+        k_tess_tri<T, R><<<a.ntiles, NTT, 2 * sizeof(T) * (size_t)a.wmax, s>>>(a);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem2 = 4 * sizeof(T) * (size_t)tess::s2_half(a.b, R);

@@ -137,6 +137,7 @@ CASES_TESS = [
     (5000, 77, 2, 8, "f64"),      # two tiles, the second 2952 points wide
     (3000, 40, 3, 10, "f64"),     # one tile: its boundary wraps around the line
     (9000, 61, 16, 7, "f32"), (4100, 33, 12, 5, "f64"),
+    (3000, 40, 4, 8, "f32"),      # one FP32 tile of strips, its boundary wrapping around
 ]
 
 
