@@ -29,7 +29,9 @@ namespace sg {
 
 namespace {
 
-constexpr const char *kLibVersion = "6";
+constexpr const char *kLibVersion = "8";
+// Steps of a timed candidate run.
+constexpr int64_t kTuneSteps(int ndim) { return ndim == 1 ? 96 : 48; }
 
 struct Cand {
     int engine;  // 0 CUDA core, 1 tensor core
@@ -193,7 +195,7 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
                     cands.push_back({0, m, b, 0, 0});
                     // exact tessellate tiling (Section 3.4) of the same passes
                     const int w = p->dtype == STENCIL_F64 ? 2048 : 4096;
-                    if (tess1d_fits(p->nx, w, std::min<int64_t>(b, 48 / m + 1), R))
+                    if (tess1d_fits(p->nx, w, std::min<int64_t>(b, kTuneSteps(1) / m + 1), R))
                         cands.push_back({0, m, b, 0, 1});
                 }
         } else if (p->ndim == 3) {
@@ -233,8 +235,14 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     const int saved_prec = p->precision, saved_b = p->block_b, saved_ty = p->tile_y;
     const int saved_tess = p->tessellate;
     const int saved_graph = p->use_graph;
-    p->use_graph = 0;  // tuning runs are not worth capturing
-    const int64_t T = 48;
+    // 2D/3D tuning runs are not worth capturing; 1D runs are launch-bound, so
+    // their candidates are timed as the captured graphs a real run replays
+    // (the tessellated form's second launch per pass would otherwise look
+    // dearer than it is), and those graphs are dropped afterwards
+    if (p->ndim != 1) p->use_graph = 0;
+    // steps per timed run: 1D runs are short and launch-bound, so their
+    // candidates are timed over more steps, closer to a whole run
+    const int64_t T = kTuneSteps(p->ndim);
     double best_rate = -1.0;
     for (const Cand &c : cands) {
         p->precision = c.engine == 1 ? (saved_prec ? saved_prec : STENCIL_PREC_BF16X3) : STENCIL_PREC_FP32;
@@ -268,6 +276,10 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     p->tile_y = saved_ty;
     p->tessellate = saved_tess;
     p->use_graph = saved_graph;
+    if (p->ndim == 1) {
+        cudaStreamSynchronize(s);
+        clear_graphs(p);  // they name the tuning's scratch grids
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(din);

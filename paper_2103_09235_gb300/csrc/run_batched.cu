@@ -408,8 +408,9 @@ double time_batch(int n, stencil_plan_s *const *plans, const void *const *in, vo
 // Chooses (m, b) for every automatic grid (auto_g[g]) and the batch's tile
 // height: cached choices where the cache has them, else, for each tile height
 // of 128, 96 and 64 rows, one class at a time among the choices that keep
-// that height, then the whole batch with them; the fastest set wins, the
-// starting choices included.  Every candidate is timed as a
+// that height; then the starting set and the tuned sets are timed as whole
+// batches in turns, and a tuned set replaces the starting one only if it is
+// 5 % faster.  Every candidate is timed as a
 // batched launch that writes scratch outputs, never the caller's grids.
 stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *const *in,
                             const int64_t *T, const std::vector<bool> &auto_g,
@@ -506,19 +507,18 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
     }
     std::vector<int> best_ms = ms, best_bs = bs;
     int best_ty = batch_tile_height(n, plans, T, ms.data(), bs.data(), kBatchTileYMax, max_smem);
-    // whole-batch timings take the best of five launches, and a tuned set must
-    // beat the starting choices by more than the launches' spread (3 %)
-    auto best_of_five = [&](const std::vector<int> &mm, const std::vector<int> &bb_, int ty_) {
-        double best = -1.0;
-        for (int k = 0; k < 5; ++k) {
-            const double t = time_batch(n, plans, in, sout.data(), T, mm, bb_, ty_, s, e0, e1);
-            if (t <= 0) return -1.0;
-            best = best < 0 ? t : std::min(best, t);
-        }
-        return best;
+    // The starting set and the tuned sets (one per tile height) are timed as
+    // whole batches in turns, five rounds of one launch each, so that drift
+    // over the tuning run affects them alike; each keeps its best launch, and
+    // a tuned set must beat the starting one by 5 %.
+    struct SetChoice {
+        std::vector<int> ms, bs;
+        int ty;
+        std::map<ClassKey, std::pair<int, int>> choice;
+        double t;
     };
-    const double start_t = best_of_five(ms, bs, best_ty);
-    double best_t = start_t;
+    std::vector<SetChoice> sets;
+    sets.push_back({ms, bs, best_ty, best_choice, -1.0});
     for (int ty_c : {128, 96, 64}) {
         std::vector<int> tm = ms, tb = bs;
         std::map<ClassKey, std::pair<int, int>> choice = best_choice;
@@ -567,15 +567,23 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
             }
         }
         const int ty_real = batch_tile_height(n, plans, T, tm.data(), tb.data(), ty_c, max_smem);
-        const double t = best_of_five(tm, tb, ty_real);
-        if (t > 0 && (best_t < 0 || (t < best_t && t < 0.97 * start_t))) {
-            best_t = t;
-            best_ms = tm;
-            best_bs = tb;
-            best_ty = ty_real;
-            best_choice = choice;
-        }
+        sets.push_back({tm, tb, ty_real, choice, -1.0});
     }
+    for (int round = 0; round < 5; ++round)
+        for (SetChoice &c : sets) {
+            const double t = time_batch(n, plans, in, sout.data(), T, c.ms, c.bs, c.ty, s, e0, e1);
+            if (t > 0 && (c.t < 0 || t < c.t)) c.t = t;
+        }
+    size_t pick = 0;
+    for (size_t i = 1; i < sets.size(); ++i)
+        if (sets[i].t > 0 && sets[0].t > 0 && sets[i].t < 0.95 * sets[0].t &&
+            (pick == 0 || sets[i].t < sets[pick].t))
+            pick = i;
+    std::vector<int> best_ms2 = sets[pick].ms, best_bs2 = sets[pick].bs;
+    best_ty = sets[pick].ty;
+    best_choice = sets[pick].choice;
+    best_ms = best_ms2;
+    best_bs = best_bs2;
     ms = best_ms;
     bs = best_bs;
     ty = best_ty;
