@@ -379,6 +379,19 @@ def test_sweep3d_parity(env, shape, kind, r, T, m, stages):
     assert info["m"] == m
 
 
+@pytest.mark.parametrize("zc", [4, 8, 32, 1024])
+@pytest.mark.parametrize("shape,kind,m", [((150, 20, 24), "box", 1), ((100, 40, 70), "star", 2)])
+def test_sweep3d_z_chunk(env, shape, kind, m, zc):
+    """The z_chunk option (output planes per CTA): chunks shorter than the halo,
+    longer than the grid, and between all give the oracle's result."""
+    _, _, oracle = env
+    c = synth.dyadic_coeffs(3150, 3, 1, kind)
+    x = synth.grid(3151, shape, np.float32)
+    y, info = gpu_run(env, shape, c, x, 7, m, block_b=1, z_chunk=zc)
+    check(y, oracle.run(x.astype(np.float64), c, 7))
+    assert info["m"] == m
+
+
 CASES_3D_FUSED = [
     # shape (z, y, x), kind, r, T, m: two fused sweeps per pass (block_b = 2)
     ((100, 40, 70), "star", 1, 7, 1),    # three pairs and one single sweep
