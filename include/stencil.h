@@ -121,12 +121,12 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *   "block_b"       temporal-blocking depth: folded sweeps per memory round trip
  *                   (0 = automatic; 1..64, and 2D/3D passes take as many as their
  *                   halo allows).
- *   "tile_y"        rows per CTA tile of the 2D CUDA-core sweep (0 = automatic: 32
- *                   for single sweeps, 64 for blocked ones, 160 in counterpart form,
- *                   lowered until the tile fits in shared memory).
+ *   "tile_y"        rows per CTA tile of the 2D CUDA-core sweep (0 = automatic: 64,
+ *                   160 in counterpart form, lowered until the tile fits in shared
+ *                   memory).
  *   "stages"        TMA stages per CTA of the 2D CUDA-core sweep, 1..6 (0 =
- *                   automatic: 4 for single sweeps; 2 for blocked ones, or 1 when
- *                   two do not fit the tile; 1 in counterpart form).  A blocked
+ *                   automatic: 2, or 1 for blocked passes when two do not fit the
+ *                   tile; 1 in counterpart form).  A blocked
  *                   pass refills a stage after the tile's first sweep, and a
  *                   counterpart-form pass after its first vertical fold, so 1
  *                   still overlaps copies with compute; a direct single-sweep
