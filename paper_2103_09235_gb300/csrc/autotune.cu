@@ -29,7 +29,7 @@ namespace sg {
 
 namespace {
 
-constexpr const char *kLibVersion = "8";
+constexpr const char *kLibVersion = "9";
 // Steps of a timed candidate run.
 constexpr int64_t kTuneSteps(int ndim) { return ndim == 1 ? 96 : 48; }
 
@@ -37,6 +37,8 @@ struct Cand {
     int engine;  // 0 CUDA core, 1 tensor core
     int m, b, ty;
     int tess;    // 1D: exact tessellate tiling instead of overlapped tiles
+    int thr = 0;  // 2D: threads per CTA (0 = the kernel's own, 256 = two half-size CTAs)
+    int ns = 0;   // 2D: TMA stages per CTA (0 = automatic)
 };
 
 uint64_t fnv1a(const void *data, size_t n, uint64_t h = 1469598103934665603ull)
@@ -94,6 +96,8 @@ bool cache_lookup(const std::string &key, Cand *c)
                         &t.b, &t.ty) == 4) {
             const char *ts = strstr(line, "\"tess\": ");
             if (ts) sscanf(ts, "\"tess\": %d", &t.tess);
+            const char *th = strstr(line, "\"threads\": ");
+            if (th) sscanf(th, "\"threads\": %d, \"stages\": %d", &t.thr, &t.ns);
             *c = t;  // the last entry for a key wins
             found = true;
         }
@@ -108,8 +112,10 @@ void cache_store(const std::string &key, const Cand &c, double gstencil)
     if (path.empty()) return;
     FILE *f = fopen(path.c_str(), "a");
     if (!f) return;
-    fprintf(f, "{\"key\": \"%s\", \"engine\": %d, \"m\": %d, \"b\": %d, \"tile_y\": %d, \"tess\": %d, \"gstencil_s\": %.1f}\n",
-            key.c_str(), c.engine, c.m, c.b, c.ty, c.tess, gstencil);
+    fprintf(f,
+            "{\"key\": \"%s\", \"engine\": %d, \"m\": %d, \"b\": %d, \"tile_y\": %d, \"tess\": %d, "
+            "\"threads\": %d, \"stages\": %d, \"gstencil_s\": %.1f}\n",
+            key.c_str(), c.engine, c.m, c.b, c.ty, c.tess, c.thr, c.ns, gstencil);
     fclose(f);
 }
 
@@ -169,6 +175,8 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
         p->tuned_b = best.b;
         p->tuned_ty = best.ty;
         p->tuned_tess = best.tess;
+        p->tuned_thr = best.thr;
+        p->tuned_ns = best.ns;
         return STENCIL_OK;
     }
     // candidate list
@@ -211,7 +219,14 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
                 for (int b : {1, 2, 3, 4, 6, 8})
                     if (b * R <= std::min(kGhost, nmin) && (m > 1 || b <= 8))
                         for (int ty : {32, 64, 96, 128, 160})
-                            if (ty + 2 * b * R <= 256) cands.push_back({0, m, b, ty, 0});
+                            if (ty + 2 * b * R <= 256) {
+                                cands.push_back({0, m, b, ty, 0});
+                                // blocked passes also as two half-size CTAs per SM
+                                // with one stage (measured on GB300: the 8192^2 box,
+                                // m = 2, b = 2, 96-row tiles, 1737 against 1680 GS/s
+                                // for the best one-CTA shape)
+                                if (b >= 2 && ty >= 96) cands.push_back({0, m, b, ty, 0, 256, 1});
+                            }
             if (m > 1 && p->precision != STENCIL_PREC_FP32 && tc2d_supported(R))
                 cands.push_back({1, m, 1, 0, 0});
         }
@@ -233,6 +248,7 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int saved_prec = p->precision, saved_b = p->block_b, saved_ty = p->tile_y;
+    const int saved_thr = p->cta_threads, saved_ns = p->stages;
     const int saved_tess = p->tessellate;
     const int saved_graph = p->use_graph;
     // 2D/3D tuning runs are not worth capturing; 1D runs are launch-bound, so
@@ -249,6 +265,10 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
         p->block_b = c.b;
         p->tile_y = c.ty;
         p->tessellate = c.tess;
+        if (p->ndim == 2 && c.engine == 0) {
+            p->cta_threads = c.thr ? c.thr : saved_thr;
+            p->stages = c.ns ? c.ns : saved_ns;
+        }
         stencil_status_t st = STENCIL_OK;
         auto once = [&]() {
             if (p->ndim == 1) return run1d(p, din, dout, T, c.m, s);
@@ -274,6 +294,8 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     p->precision = saved_prec;
     p->block_b = saved_b;
     p->tile_y = saved_ty;
+    p->cta_threads = saved_thr;
+    p->stages = saved_ns;
     p->tessellate = saved_tess;
     p->use_graph = saved_graph;
     if (p->ndim == 1) {
@@ -290,6 +312,8 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     p->tuned_b = best.b;
     p->tuned_ty = best.ty;
     p->tuned_tess = best.tess;
+    p->tuned_thr = best.thr;
+    p->tuned_ns = best.ns;
     cache_store(key, best, best_rate);
     return STENCIL_OK;
 }

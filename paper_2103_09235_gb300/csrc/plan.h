@@ -97,6 +97,7 @@ struct stencil_plan_s {
     int last_tess = 0;  // 1 if the last 1D run's folded passes used exact tessellate tiling
     // autotuner choice for fold_m = 0: m, b, tile_y, engine (m = 0: not tuned yet)
     int tuned_m = 0, tuned_b = 0, tuned_ty = 0, tuned_engine = 0, tuned_tess = 0;
+    int tuned_thr = 0, tuned_ns = 0;  // 2D: CTA size and stages of the tuned choice
 };
 
 namespace sg {

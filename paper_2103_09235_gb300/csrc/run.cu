@@ -305,9 +305,14 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
     int b = p->block_b;
     struct Restore {
         stencil_plan_s *p;
-        int ty;
-        ~Restore() { p->tile_y = ty; }
-    } restore{p, p->tile_y};
+        int ty, thr, ns;
+        ~Restore()
+        {
+            p->tile_y = ty;
+            p->cta_threads = thr;
+            p->stages = ns;
+        }
+    } restore{p, p->tile_y, p->cta_threads, p->stages};
     bool cuda_core_only = false;
     if (m == 0) {
         if (p->tuned_m == 0 && p->autotune) {
@@ -321,6 +326,8 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
         m = p->tuned_m;
         if (b == 0) b = p->tuned_b;
         if (p->tile_y == 0) p->tile_y = p->tuned_ty;
+        if (p->cta_threads == 0) p->cta_threads = p->tuned_thr;
+        if (p->stages == 0) p->stages = p->tuned_ns;
         cuda_core_only = p->tuned_engine == 0;
     }
 
