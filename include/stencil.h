@@ -134,7 +134,8 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *                   stages of four planes (other values: 2).
  *   "cta_threads"   threads per CTA of the 2D CUDA-core sweep: 0 = automatic
  *                   (chosen by the autotuner, else the kernel's own size), 256 =
- *                   two half-size CTAs per SM for folded sweeps that run 512.
+ *                   two half-size CTAs per SM for folded sweeps that run 512,
+ *                   and, on plans[0] of stencil_run_batched, for the batch.
  *   "z_chunk"       3D sweeps: output planes per CTA, a multiple of 4 in 4..1024
  *                   (0 = automatic: 16 for a single radius-1 sweep, else 32, halved
  *                   down to 8 while the grid has fewer than 4 CTAs per SM).
@@ -193,6 +194,8 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, i
  * of the last tensor-core run), "last_cp" (separable terms K of the last 2D
  * CUDA-core run's folded passes in counterpart form, 0 = direct form),
  * "last_tess" (1 if the last 1D run's first pass was tessellated exactly),
+ * "last_threads" (threads per CTA of the last stencil_run_batched launch: 512,
+ * or 256 for two CTAs per SM),
  * "launches" (kernels the plan has launched so far),
  * "scratch_bytes" (device bytes the plan owns).
  */
@@ -234,7 +237,10 @@ stencil_status_t stencil_run(stencil_plan_t plan, const void *in, void *out, int
  *             the batch autotuner, which times each class of grids (radius,
  *             pattern, floor(log2 area)) and caches its choice per class and
  *             GPU; it also picks the batch's tile height unless plans[0] sets
- *             the "tile_y" option, which then pins it (at most 128 rows).
+ *             the "tile_y" option, which then pins it (at most 128 rows), and
+ *             the CTA shape: 512 threads, one CTA per SM, or 256 threads, two
+ *             per SM with tiles that fit half an SM's shared memory (pinned
+ *             by "cta_threads" 256 on plans[0]).
  * Grids must not alias one another.  Errors as for stencil_run; a timed-out
  * dependency wait is reported by stencil_sync on plans[0].
  */

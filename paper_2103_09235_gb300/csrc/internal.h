@@ -133,8 +133,11 @@ bool batched_variant_supported(int rb, int m, int pattern);
 int batched_variant_id(int rb, int m, int pattern);
 // nstage TMA stages plus nwork (0..2) work buffers of buf_floats each.
 size_t batched_smem_bytes(int buf_floats, int nwork, int nstage);
-int batched_ctas_per_sm(size_t smem);
-cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s);
+// threads of the batched CTA for a plan's cta_threads option (256: the
+// half-size CTA, two per SM; else the 512-thread CTA, one per SM)
+int batched_threads(int cta_threads);
+int batched_ctas_per_sm(size_t smem, int threads);
+cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, int threads, cudaStream_t s);
 
 // ---- 3D CUDA-core sweep (streaming along z) -------------------------------
 struct Sweep3DArgs {

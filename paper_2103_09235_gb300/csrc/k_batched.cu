@@ -6,8 +6,8 @@
 // passes into a work list of (pass, tile) items ordered round by round: all
 // grids' first passes, then all grids' second passes, and so on.
 //
-// A CTA is 15 consumer warps that run the tile body and one producer warp
-// (one active lane) that feeds them:
+// A CTA is 15 consumer warps (or 7, two CTAs per SM) that run the tile body
+// and one producer warp (one active lane) that feeds them:
 //   producer: pop an item from the device queue (one atomic counter), wait
 //             (bounded) until every tile of the grid's previous pass is
 //             counted done, write the item's description into one of two
@@ -36,12 +36,12 @@ namespace {
 
 using namespace tile2d;
 
-// 15 consumer warps and the producer: 16 warps keep four per SM sub-partition,
-// so every thread may hold 128 registers.
-constexpr int kConsumers = 480;                    // threads that run the tile body
-constexpr int kThreadsBatched = kConsumers + 32;   // plus the producer warp
-constexpr int kCoefSlot = 96;                      // floats of weights per stage (>= 81)
-using ConsumerSync = NamedSync<kConsumers>;
+// Two CTA shapes, both at 128 registers a thread: 15 consumer warps and the
+// producer (512 threads, one CTA per SM), or 7 consumer warps and the producer
+// (256 threads, two CTAs per SM, each with half the shared memory).
+constexpr int kConsumersWide = 480;  // threads that run the tile body
+constexpr int kConsumersHalf = 224;
+constexpr int kCoefSlot = 96;  // floats of weights per stage (>= 81)
 
 // One stage's work description, written by the producer before its arrive on
 // the stage's full barrier.
@@ -90,7 +90,8 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// OR of a predicate over the consumer threads (named barrier 1).
+// OR of a predicate over the NC consumer threads (named barrier 1).
+template <int NC>
 __device__ __forceinline__ bool consumers_any(bool v)
 {
     uint32_t r;
@@ -100,7 +101,7 @@ __device__ __forceinline__ bool consumers_any(bool v)
         "bar.red.or.pred q, 1, %2, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(r)
-        : "r"((uint32_t)v), "n"(kConsumers)
+        : "r"((uint32_t)v), "n"(NC)
         : "memory");
     return r != 0;
 }
@@ -110,8 +111,9 @@ __host__ __device__ constexpr int variant_code(int rb, int m, int pattern)
     return (rb - 1) * 16 + pattern * 8 + m;
 }
 
-// Runs the tile body of the variant (base radius, pattern, m).
-template <class Hook>
+// Runs the tile body of the variant (base radius, pattern, m) on the consumer
+// threads that Sync names.
+template <class Sync, class Hook>
 __device__ __forceinline__ void run_variant(const StageMeta &md, const float *stage, float *w0,
                                             float *w1, int TY, const SmemCoef &cf,
                                             const Hook &stage_free)
@@ -121,11 +123,11 @@ __device__ __forceinline__ void run_variant(const StageMeta &md, const float *st
     case variant_code(RB_, M_, P_): {                                                           \
         if constexpr (Strip<RB_, M_, P_>::NNZ <= 25) {                                          \
             const RegCoef<(2 * M_ * RB_ + 1) * (2 * M_ * RB_ + 1)> rc(cf.c);                    \
-            process_tile<RB_, M_, P_, ConsumerSync>(stage, w0, w1, TY, md.H, md.HX, md.b, rc,   \
+            process_tile<RB_, M_, P_, Sync>(stage, w0, w1, TY, md.H, md.HX, md.b, rc,   \
                                                     o, md.gx0, md.gy0, md.vx, md.vy,            \
                                                     stage_free);                                \
         } else {                                                                                \
-            process_tile<RB_, M_, P_, ConsumerSync>(stage, w0, w1, TY, md.H, md.HX, md.b, cf,   \
+            process_tile<RB_, M_, P_, Sync>(stage, w0, w1, TY, md.H, md.HX, md.b, cf,   \
                                                     o, md.gx0, md.gy0, md.vx, md.vy,            \
                                                     stage_free);                                \
         }                                                                                       \
@@ -266,8 +268,11 @@ __device__ __forceinline__ void produce(const BatchArgs &a, uint64_t *full, uint
     }
 }
 
-__global__ void __launch_bounds__(kThreadsBatched, 1) k_batched(const __grid_constant__ BatchArgs a)
+template <int NC>
+__global__ void __launch_bounds__(NC + 32, NC + 32 <= 256 ? 2 : 1)
+    k_batched(const __grid_constant__ BatchArgs a)
 {
+    using ConsumerSync = NamedSync<NC>;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem);  // full[2], done[2], sfree[2]
     uint64_t *done_bar = full + 2;
@@ -289,14 +294,14 @@ __global__ void __launch_bounds__(kThreadsBatched, 1) k_batched(const __grid_con
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid >= kConsumers) {
-        if (tid == kConsumers) produce(a, full, done_bar, sfree, meta, cslot, base);
+    if (tid >= NC) {
+        if (tid == NC) produce(a, full, done_bar, sfree, meta, cslot, base);
         return;
     }
     for (int k = 0;; ++k) {
         const int p = k & 1;
         const bool landed = mbar_wait_bounded(&full[p], (k >> 1) & 1, a.wait_ns);
-        if (consumers_any(!landed)) {
+        if (consumers_any<NC>(!landed)) {
             if (tid == 0) record_status(a.status, DEV_TIMEOUT);
             break;
         }
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kThreadsBatched, 1) k_batched(const __grid_con
         auto stage_free = [&]() {
             if (tid == 0) mbar_arrive(free_bar);
         };
-        run_variant(md, base + (k % S) * a.buf_floats, w0, w1, a.tile_y,
+        run_variant<ConsumerSync>(md, base + (k % S) * a.buf_floats, w0, w1, a.tile_y,
                     SmemCoef{cslot + p * kCoefSlot}, stage_free);
         ConsumerSync::sync();  // the item's buffers and slot are free again
         if (tid == 0) {
@@ -337,19 +342,29 @@ size_t batched_smem_bytes(int buf_floats, int nwork, int nstage)
     return 1024 + (size_t)(nstage + nwork) * buf_floats * 4 + 2 * BUF_PAD * 4;
 }
 
-cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_batched(const BatchArgs &a, int grid, size_t smem, int threads, cudaStream_t s)
 {
-    const cudaError_t e = smem_optin((const void *)k_batched);
+    const bool half = threads == kConsumersHalf + 32;
+    const void *fn = half ? (const void *)k_batched<kConsumersHalf> : (const void *)k_batched<kConsumersWide>;
+    const cudaError_t e = smem_optin(fn);
     if (e != cudaSuccess) return e;
-    k_batched<<<grid, kThreadsBatched, smem, s>>>(a);
+    if (half)
+        k_batched<kConsumersHalf><<<grid, threads, smem, s>>>(a);
+    else
+        k_batched<kConsumersWide><<<grid, kConsumersWide + 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-int batched_ctas_per_sm(size_t smem)
+int batched_threads(int cta_threads) { return cta_threads == 256 ? kConsumersHalf + 32 : kConsumersWide + 32; }
+
+int batched_ctas_per_sm(size_t smem, int threads)
 {
+    const bool half = threads == kConsumersHalf + 32;
+    const void *fn = half ? (const void *)k_batched<kConsumersHalf> : (const void *)k_batched<kConsumersWide>;
     int n = 0;
-    if (smem_optin((const void *)k_batched) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batched, kThreadsBatched, smem) != cudaSuccess)
+    if (smem_optin(fn) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, half ? threads : kConsumersWide + 32, smem) !=
+        cudaSuccess)
         return 0;
     return n;
 }

@@ -69,7 +69,7 @@ struct stencil_plan_s {
     size_t scratch_bytes = 0;
 
     // cached launch facts
-    int sm_count = 0, max_smem = 0;
+    int sm_count = 0, max_smem = 0, max_smem_sm = 0;  // SMs, shared bytes per CTA (opt-in) and per SM
     struct PassCfg {
         int ty, bf, grid, nstages, threads;
         size_t smem;
@@ -93,6 +93,7 @@ struct stencil_plan_s {
     int last_m = 0, last_b = 0, last_engine = 0;
     int last_tc_form = 0;  // tensor-core kernel of the last tensor-core run (1 or 2)
     int last_ty = 0;  // tile height of the last 2D CUDA-core run's first pass
+    int last_threads = 0;  // threads per CTA of the last batched launch
     int last_cp = 0;  // counterpart terms of the last 2D CUDA-core run's folded passes (0 = direct)
     int last_tess = 0;  // 1 if the last 1D run's folded passes used exact tessellate tiling
     // autotuner choice for fold_m = 0: m, b, tile_y, engine (m = 0: not tuned yet)

@@ -41,6 +41,7 @@ void ensure_device_facts(stencil_plan_s *p)
     if (p->sm_count) return;
     cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
     cudaDeviceGetAttribute(&p->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    cudaDeviceGetAttribute(&p->max_smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
     if (p->sm_count <= 0) p->sm_count = 1;
 }
 

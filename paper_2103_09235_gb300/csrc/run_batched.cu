@@ -93,8 +93,19 @@ struct BatchBuild {
     int njobs = 0;
     long long import_rows = 0;
     int tile_y = 0;
+    int threads = 0;           // CTA size of the launch
     double *d_sums = nullptr;  // per-job FP64 grid sums (centred storage), null if none
 };
+
+// Shared memory a batched CTA may use: all a CTA may opt into, or, for the
+// half-size CTA, half an SM's less the 1 KB the runtime reserves per CTA, so
+// that two fit on every SM.
+size_t batch_smem_budget(const stencil_plan_s *p0, int threads)
+{
+    const size_t all = (size_t)p0->max_smem;
+    if (threads == batched_threads(0) || p0->max_smem_sm <= 0) return all;
+    return std::min(all, (size_t)p0->max_smem_sm / 2 - 1024);
+}
 
 // The batch's one tile height for per-grid (m, b) choices: the tallest (up to
 // ty_max rows, in steps of 16) whose stages and work buffers fit for the
@@ -125,11 +136,12 @@ int batch_tile_height(int n, stencil_plan_s *const *plans, const int64_t *T, con
     return tile_y;
 }
 
-// Flattens the batch with per-grid (m, b) choices and a tile height of at
-// most ty_max rows; uploads the work description.
+// Flattens the batch with per-grid (m, b) choices, a tile height of at most
+// ty_max rows and CTAs of the given threads (256 or 512); uploads the work
+// description.
 stencil_status_t flatten_batch(int n, stencil_plan_s *const *plans, const void *const *in,
                                void *const *out, const int64_t *T, const int *ms, const int *bs,
-                               int ty_max, BatchBuild *bb)
+                               int ty_max, int threads, BatchBuild *bb)
 {
     stencil_plan_s *p0 = plans[0];
     ensure_device_facts(p0);
@@ -141,7 +153,7 @@ stencil_status_t flatten_batch(int n, stencil_plan_s *const *plans, const void *
     std::map<std::tuple<const void *, int, int>, int> map_index;
     // one tile height for the whole batch
     int max_h = 1, nwork = 0;
-    const int tile_y = batch_tile_height(n, plans, T, ms, bs, ty_max, (size_t)p0->max_smem,
+    const int tile_y = batch_tile_height(n, plans, T, ms, bs, ty_max, batch_smem_budget(p0, threads),
                                          &max_h, &nwork);
     const int nstage = nwork > 0 ? 1 : 2;
     auto smem_for = [&](int ty, int *bf) {
@@ -310,7 +322,8 @@ stencil_status_t flatten_batch(int n, stencil_plan_s *const *plans, const void *
     a.wait_ns = (unsigned long long)p0->wait_ms * 1000000ull;
     a.fault_withhold_dep = p0->fault_withhold_dep;
     bb->smem = smem;
-    const int occ = std::max(1, batched_ctas_per_sm(smem));
+    bb->threads = threads;
+    const int occ = std::max(1, batched_ctas_per_sm(smem, bb->threads));
     bb->grid = std::max(1, std::min(a.nitems, occ * p0->sm_count));
     bb->counters = (passes.size() + 1) * sizeof(int);
     bb->d_jobs = reinterpret_cast<const ImportJob *>(dev + o_jobs);
@@ -343,7 +356,7 @@ stencil_status_t enqueue_batch(const BatchBuild &bb, cudaStream_t st_, int *nl)
     }
     if (bb.a.nitems > 0) {
         cudaError_t err = cudaMemsetAsync(bb.a.done, 0, bb.counters, st_);
-        if (err == cudaSuccess) err = launch_batched(bb.a, bb.grid, bb.smem, st_);
+        if (err == cudaSuccess) err = launch_batched(bb.a, bb.grid, bb.smem, bb.threads, st_);
         if (err != cudaSuccess) return cuda_fail(err, "batched launch");
         *nl += 1;
     }
@@ -384,10 +397,10 @@ std::string class_cache_key(const ClassKey &k, const char *gpu)
 // (after one untimed launch), or a negative value if it cannot run.
 double time_batch(int n, stencil_plan_s *const *plans, const void *const *in, void *const *out,
                   const int64_t *T, const std::vector<int> &ms, const std::vector<int> &bs,
-                  int ty, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
+                  int ty, int threads, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1)
 {
     BatchBuild bb;
-    if (flatten_batch(n, plans, in, out, T, ms.data(), bs.data(), ty, &bb) != STENCIL_OK) {
+    if (flatten_batch(n, plans, in, out, T, ms.data(), bs.data(), ty, threads, &bb) != STENCIL_OK) {
         if (bb.dev) cudaFree(bb.dev);
         return -1.0;
     }
@@ -405,20 +418,28 @@ double time_batch(int n, stencil_plan_s *const *plans, const void *const *in, vo
     return st == STENCIL_OK ? (double)ms_el : -1.0;
 }
 
-// Chooses (m, b) for every automatic grid (auto_g[g]) and the batch's tile
-// height: cached choices where the cache has them, else, for each tile height
-// of 128, 96 and 64 rows, one class at a time among the choices that keep
-// that height; then the starting set and the tuned sets are timed as whole
-// batches in turns, and a tuned set replaces the starting one only if it is
-// 5 % faster.  Every candidate is timed as a
-// batched launch that writes scratch outputs, never the caller's grids.
+// Chooses (m, b) for every automatic grid (auto_g[g]), the batch's tile
+// height and its CTA shape: cached choices where the cache has them, else,
+// for each tile height and shape (128, 96 and 64 rows with 512-thread CTAs;
+// 80 and 64 rows with two 256-thread CTAs per SM, whose tiles must fit half
+// an SM's shared memory), one class at a time among the choices that keep
+// that height; then the starting set, the tuned sets and each tuned set on
+// the other CTA shape are timed as whole batches in turns, and a tuned set
+// replaces the starting one only if it is 2 % faster (two timings of one set
+// agree to about 0.1 %).  A first plan with cta_threads 256 limits the search to the
+// half-size CTA.  Every candidate is timed as a batched launch that writes
+// scratch outputs, never the caller's grids.
 stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *const *in,
                             const int64_t *T, const std::vector<bool> &auto_g,
                             std::vector<int> &ms, std::vector<int> &bs, int *ty_out,
-                            cudaStream_t s)
+                            int *thr_out, cudaStream_t s)
 {
     stencil_plan_s *p0 = plans[0];
+    const int thr_wide = batched_threads(0), thr_half = batched_threads(256);
+    const bool half_only = p0->cta_threads == 256;
+    const int thr_start = half_only ? thr_half : thr_wide;
     *ty_out = kBatchTileYMax;
+    *thr_out = thr_start;
     cudaDeviceProp prop;
     memset(&prop, 0, sizeof(prop));
     cudaGetDeviceProperties(&prop, p0->device);
@@ -447,19 +468,23 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
         else
             all_cached = false;
     }
+    if (half_only) tile_key += "t256;";
     tile_key += std::string("|") + prop.name;
-    int ty = kBatchTileYMax;
+    int ty = kBatchTileYMax, thr = thr_start;
     {
         std::string v;
-        int t = 0;
-        if (tune_cache_get(tile_key, &v) && sscanf(v.c_str(), "%d", &t) == 1 && t >= 16 &&
-            t <= kBatchTileYMax)
+        int t = 0, h = 0;
+        if (tune_cache_get(tile_key, &v) && sscanf(v.c_str(), "%d %d", &t, &h) == 2 && t >= 16 &&
+            t <= kBatchTileYMax && (h == thr_wide || h == thr_half) && !(half_only && h != thr_half)) {
             ty = t;
-        else
+            thr = h;
+        } else {
             all_cached = false;
+        }
     }
     if (all_cached || !p0->autotune) {
         *ty_out = ty;
+        *thr_out = thr;
         return STENCIL_OK;
     }
     // scratch outputs in each grid's own layout
@@ -480,13 +505,12 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
     // each timing is the best of two launches
     auto best_of_two = [&](int nn, stencil_plan_s *const *pl, const void *const *ii,
                            void *const *oo, const int64_t *tt, const std::vector<int> &mm,
-                           const std::vector<int> &bb_, int ty_) {
-        const double t0 = time_batch(nn, pl, ii, oo, tt, mm, bb_, ty_, s, e0, e1);
-        const double t1 = time_batch(nn, pl, ii, oo, tt, mm, bb_, ty_, s, e0, e1);
+                           const std::vector<int> &bb_, int ty_, int thr_) {
+        const double t0 = time_batch(nn, pl, ii, oo, tt, mm, bb_, ty_, thr_, s, e0, e1);
+        const double t1 = time_batch(nn, pl, ii, oo, tt, mm, bb_, ty_, thr_, s, e0, e1);
         return (t0 > 0 && t1 > 0) ? std::min(t0, t1) : -1.0;
     };
     ensure_device_facts(p0);
-    const size_t max_smem = (size_t)p0->max_smem;
     // The batch shares one tile height, and a class whose halo or work
     // buffers need more shared memory shortens every grid's tiles.  So each
     // candidate height is tried in turn: the classes are tuned one at a time
@@ -506,20 +530,26 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
         best_choice[kv.first] = {m, b};
     }
     std::vector<int> best_ms = ms, best_bs = bs;
-    int best_ty = batch_tile_height(n, plans, T, ms.data(), bs.data(), kBatchTileYMax, max_smem);
+    int best_ty = batch_tile_height(n, plans, T, ms.data(), bs.data(), kBatchTileYMax,
+                                    batch_smem_budget(p0, thr_start));
     // The starting set and the tuned sets (one per tile height) are timed as
     // whole batches in turns, five rounds of one launch each, so that drift
     // over the tuning run affects them alike; each keeps its best launch, and
-    // a tuned set must beat the starting one by 5 %.
+    // a tuned set must beat the starting one by 2 %.
     struct SetChoice {
         std::vector<int> ms, bs;
-        int ty;
+        int ty, thr;
         std::map<ClassKey, std::pair<int, int>> choice;
         double t;
     };
     std::vector<SetChoice> sets;
-    sets.push_back({ms, bs, best_ty, best_choice, -1.0});
-    for (int ty_c : {128, 96, 64}) {
+    sets.push_back({ms, bs, best_ty, thr_start, best_choice, -1.0});
+    const std::pair<int, int> shapes[] = {{128, thr_wide}, {96, thr_wide}, {64, thr_wide},
+                                          {80, thr_half}, {64, thr_half}};
+    for (const auto &shape : shapes) {
+        const int ty_c = shape.first, thr_c = shape.second;
+        if (half_only && thr_c != thr_half) continue;
+        const size_t max_smem = batch_smem_budget(p0, thr_c);
         std::vector<int> tm = ms, tb = bs;
         std::map<ClassKey, std::pair<int, int>> choice = best_choice;
         for (auto &kv : classes) {
@@ -551,7 +581,7 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
                                           cb.data(), ty_c, max_smem) != ty_c)
                         continue;
                     const double t = best_of_two((int)gs.size(), cp.data(), ci.data(),
-                                                 co.data(), ct.data(), cm, cb, ty_c);
+                                                 co.data(), ct.data(), cm, cb, ty_c, thr_c);
                     if (t > 0 && (best < 0 || t < best)) {
                         best = t;
                         bm = m;
@@ -567,20 +597,37 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
             }
         }
         const int ty_real = batch_tile_height(n, plans, T, tm.data(), tb.data(), ty_c, max_smem);
-        sets.push_back({tm, tb, ty_real, choice, -1.0});
+        sets.push_back({tm, tb, ty_real, thr_c, choice, -1.0});
+    }
+    // every tuned set also on the other CTA shape, at the tallest tile that
+    // shape fits, unless an identical set is already listed
+    if (!half_only) {
+        const size_t ntuned = sets.size();
+        for (size_t i = 1; i < ntuned; ++i) {
+            SetChoice c = sets[i];
+            c.thr = c.thr == thr_wide ? thr_half : thr_wide;
+            c.ty = batch_tile_height(n, plans, T, c.ms.data(), c.bs.data(), kBatchTileYMax,
+                                     batch_smem_budget(p0, c.thr));
+            bool dup = false;
+            for (const SetChoice &o : sets)
+                dup = dup || (o.thr == c.thr && o.ty == c.ty && o.ms == c.ms && o.bs == c.bs);
+            if (!dup) sets.push_back(c);
+        }
     }
     for (int round = 0; round < 5; ++round)
         for (SetChoice &c : sets) {
-            const double t = time_batch(n, plans, in, sout.data(), T, c.ms, c.bs, c.ty, s, e0, e1);
+            const double t =
+                time_batch(n, plans, in, sout.data(), T, c.ms, c.bs, c.ty, c.thr, s, e0, e1);
             if (t > 0 && (c.t < 0 || t < c.t)) c.t = t;
         }
     size_t pick = 0;
     for (size_t i = 1; i < sets.size(); ++i)
-        if (sets[i].t > 0 && sets[0].t > 0 && sets[i].t < 0.95 * sets[0].t &&
+        if (sets[i].t > 0 && sets[0].t > 0 && sets[i].t < 0.98 * sets[0].t &&
             (pick == 0 || sets[i].t < sets[pick].t))
             pick = i;
     std::vector<int> best_ms2 = sets[pick].ms, best_bs2 = sets[pick].bs;
     best_ty = sets[pick].ty;
+    thr = sets[pick].thr;
     best_choice = sets[pick].choice;
     best_ms = best_ms2;
     best_bs = best_bs2;
@@ -592,13 +639,14 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
         snprintf(v, sizeof(v), "%d %d", kv.second.first, kv.second.second);
         tune_cache_put(class_cache_key(kv.first, prop.name), v);
     }
-    char v[16];
-    snprintf(v, sizeof(v), "%d", ty);
+    char v[32];
+    snprintf(v, sizeof(v), "%d %d", ty, thr);
     tune_cache_put(tile_key, v);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(scratch);
     *ty_out = ty;
+    *thr_out = thr;
     return STENCIL_OK;
 }
 
@@ -645,6 +693,7 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
     key.push_back(p0->fault_withhold_dep);
     key.push_back(p0->autotune);
     key.push_back(p0->tile_y);
+    key.push_back(p0->cta_threads);
 
     if (p0->use_graph && p0->graphs.find(key) != p0->graphs.end())  // a batch seen before
         return run_maybe_graph(p0, key, s, [](cudaStream_t, int *) { return STENCIL_ERR_CUDA; });
@@ -660,15 +709,17 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
         // a grid is tuned when its fold is automatic and its plan pins no depth
         auto_g[g] = req == 0 && plans[g]->block_b == 0;
     }
-    int ty = kBatchTileYMax;
-    stencil_status_t st = tune_batch(n, plans, in, T, auto_g, ms, bs, &ty, s);
+    int ty = kBatchTileYMax, thr = batched_threads(0);
+    stencil_status_t st = tune_batch(n, plans, in, T, auto_g, ms, bs, &ty, &thr, s);
     if (st != STENCIL_OK) return st;
-    // the first plan's tile_y option pins the batch's tile height
+    // the first plan's tile_y option pins the batch's tile height, and its
+    // cta_threads option (256) the half-size CTA
     if (p0->tile_y > 0) ty = std::min(p0->tile_y, kBatchTileYMax);
+    if (p0->cta_threads == 256) thr = batched_threads(256);
 
     // ---- flatten the batch (host, once per distinct batch)
     BatchBuild bb;
-    st = flatten_batch(n, plans, in, out, T, ms.data(), bs.data(), ty, &bb);
+    st = flatten_batch(n, plans, in, out, T, ms.data(), bs.data(), ty, thr, &bb);
     if (st != STENCIL_OK) {
         if (bb.dev) cudaFree(bb.dev);
         return st;
@@ -685,6 +736,7 @@ extern "C" stencil_status_t stencil_run_batched(int n, const stencil_plan_t *pla
         plans[g]->last_m = ms[g];
         plans[g]->last_b = bs[g];
         plans[g]->last_ty = bb.tile_y;
+        plans[g]->last_threads = bb.threads;
         plans[g]->last_engine = 0;
     }
     return st;

@@ -123,9 +123,11 @@ def test_batched_autotuner_tunes_and_caches(env, tmp_path, monkeypatch):
         p.close()
 
 
-def test_batched_uses_cached_choice(env, tmp_path, monkeypatch):
+@pytest.mark.parametrize("threads", [512, 256])
+def test_batched_uses_cached_choice(env, tmp_path, monkeypatch, threads):
     """A cache entry decides the fold and blocking depth the batched launch
-    picks for its class of grids (here: stars m = 1, b = 3; boxes m = 2, b = 1)."""
+    picks for its class of grids (here: stars m = 1, b = 3; boxes m = 2, b = 1),
+    and the batch's tile height and CTA shape."""
     import math
     torch, binding, oracle = env
     gpu = torch.cuda.get_device_name()
@@ -140,7 +142,7 @@ def test_batched_uses_cached_choice(env, tmp_path, monkeypatch):
         lines.append('{"key": "batched|2d|r%d|pat%d|area2^%d|f32|%s", "value": "%s"}'
                      % (cls + (gpu, val)))
     tile = "batched-tile|" + "".join("r%d.p%d.a%d;" % c for c in sorted(classes)) + "|" + gpu
-    lines.append('{"key": "%s", "value": "64"}' % tile)
+    lines.append('{"key": "%s", "value": "48 %d"}' % (tile, threads))
     cache.write_text("\n".join(lines) + "\n")
     monkeypatch.setenv("STENCIL_TUNE_CACHE", str(cache))
     plans, xs, ys, refs_in = _batch_plans(binding, torch, SPECS)
@@ -148,7 +150,7 @@ def test_batched_uses_cached_choice(env, tmp_path, monkeypatch):
     plans[0].sync()
     for p, (shape, kind, r, T, seed) in zip(plans, SPECS):
         assert (p.get("last_m"), p.get("last_b")) == ((1, 3) if kind == "star" else (2, 1))
-        assert p.get("last_tile_y") == 64
+        assert p.get("last_tile_y") == 48 and p.get("last_threads") == threads
     for y, (x, c, T) in zip(ys, refs_in):
         assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
     for p in plans:
@@ -164,6 +166,23 @@ def test_batched_tile_pinned_by_first_plan(env, tile):
     binding.run_batched(plans, xs, ys, [t for _, _, t in refs_in], [3, 2, 3, 2])
     plans[0].sync()
     assert all(p.get("last_tile_y") == tile for p in plans)
+    for y, (x, c, T) in zip(ys, refs_in):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("fold", [None, [1, 1, 1, 1], [3, 2, 3, 2]])
+def test_batched_half_size_ctas(env, fold):
+    """cta_threads 256 on the first plan runs the batch as two 256-thread
+    CTAs per SM (7 consumer warps each) with tiles that fit half an SM's
+    shared memory; the results match the oracle as with the wide CTA."""
+    torch, binding, oracle = env
+    plans, xs, ys, refs_in = _batch_plans(binding, torch, SPECS)
+    plans[0].set_option("cta_threads", 256)
+    binding.run_batched(plans, xs, ys, [t for _, _, t in refs_in], fold)
+    plans[0].sync()
+    assert all(p.get("last_tile_y") <= 96 and p.get("last_threads") == 256 for p in plans)
     for y, (x, c, T) in zip(ys, refs_in):
         assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
     for p in plans:
