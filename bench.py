@@ -349,7 +349,7 @@ def roofline_of(alg_bytes, alg_flops, pass_ms, esz, engine, sms):
     return out
 
 
-def kernel_name(engine, grouped, ndim, b, cp_k, esz=4):
+def kernel_name(engine, grouped, ndim, b, cp_k, esz=4, persistent=0):
     if engine == "tensor-core":
         if ndim == 3:  # one launch per plane offset, then the re-import of the result
             return "k_tc2d per plane offset + k_import"
@@ -359,7 +359,7 @@ def kernel_name(engine, grouped, ndim, b, cp_k, esz=4):
     if ndim == 1:
         return "k_sweep1d"
     if ndim == 3:
-        return "k_sweep3d_tb" if b == 2 else "k_sweep3d"
+        return "k_sweep3d_tb" if b == 2 else ("k_sweep3d_q" if persistent else "k_sweep3d")
     return "k_sweep2d"
 
 
@@ -371,6 +371,8 @@ def plan_facts(plan, ndim):
         f["counterparts"] = plan.get("last_cp")
     if engine == "tensor-core":
         f["tc_kernel"] = "grouped" if plan.get("last_tc_form") == 2 else "per-offset"
+    if ndim == 3 and engine == "cuda-core":
+        f["persistent"] = plan.get("last_persistent")
     return f
 
 
@@ -411,7 +413,7 @@ def measure_run(torch, binding, stream, flush, plan, x, y, T, m, npts, esz, sms,
     plan.run(x, y, T, fold_m=m, stream=stream)
     plan.sync(stream)
     roof["kernel"] = kernel_name(f["engine"], f.get("tc_kernel") == "grouped", x.dim(), bu, cp_k,
-                                 esz)
+                                 esz, f.get("persistent", 0))
     return ms_full, f, roof
 
 
@@ -668,7 +670,7 @@ def run_gpu(args):
     roof = pass_roofline(npts, mu, bu, mu * plan.radius, nnz, cp_k, 4, pass_ms,
                          facts["engine"], sms)
     roof["kernel"] = kernel_name(facts["engine"], facts.get("tc_kernel") == "grouped",
-                                 len(SHAPE), bu, cp_k)
+                                 len(SHAPE), bu, cp_k, 4, facts.get("persistent", 0))
     roof["traffic"] = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
@@ -676,7 +678,8 @@ def run_gpu(args):
             with open(tfile) as f:
                 tr = json.load(f)
             key = "%s_%s_m%d_b%d" % (args.config, facts["engine"] +
-                                     ("-grouped" if facts.get("tc_kernel") == "grouped" else ""),
+                                     ("-grouped" if facts.get("tc_kernel") == "grouped" else "") +
+                                     ("-persistent" if facts.get("persistent") else ""),
                                      mu, bu)
             roof["traffic"] = tr.get(key)
         except Exception:

@@ -139,6 +139,15 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *   "z_chunk"       3D sweeps: output planes per CTA, a multiple of 4 in 4..1024
  *                   (0 = automatic: 16 for a single radius-1 sweep, else 32, halved
  *                   down to 8 while the grid has fewer than 4 CTAs per SM).
+ *   "persistent"    3D CUDA-core runs: 1 = every run of two or more consecutive
+ *                   single sweeps of one stencil in ONE persistent launch, whose
+ *                   pieces (a 64 x 16 column, one z chunk) start as soon as the
+ *                   pieces they read have finished the previous pass, so the
+ *                   next pass fills the SMs while a pass drains; 0 = one launch
+ *                   per pass; -1 (default) = persistent when a pass has more
+ *                   than one and at most 3.5 waves of pieces (grids of about
+ *                   192^3 to 320^3, where each pass's last wave leaves SMs
+ *                   idle).  Same results either way.
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
  *   "center"        2D/3D CUDA-core runs and batches: 1 = store the grid minus its mean
  *                   mu (from an FP64 sum of the input) and add mu * (sum c)^T to the
@@ -195,7 +204,8 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, i
  * CUDA-core run's folded passes in counterpart form, 0 = direct form),
  * "last_tess" (1 if the last 1D run's first pass was tessellated exactly),
  * "last_threads" (threads per CTA of the last stencil_run_batched launch: 512,
- * or 256 for two CTAs per SM),
+ * or 256 for two CTAs per SM), "last_persistent" (1 if the last 3D CUDA-core
+ * run took its single sweeps in one persistent multi-pass launch),
  * "launches" (kernels the plan has launched so far),
  * "scratch_bytes" (device bytes the plan owns).
  */

@@ -162,6 +162,28 @@ size_t sweep3d_smem_bytes(int tile_y, int R, int *buf_floats, int nst = 3);
 cudaError_t launch_sweep3d(int rb, int m, int pattern, const CUtensorMap &map,
                            const Sweep3DArgs &a, int grid, size_t smem, cudaStream_t s);
 int sweep3d_ctas_per_sm(int rb, int m, int pattern, size_t smem);
+// Multi-pass persistent 3D sweep (k_sweep3d_q): npass single sweeps in one
+// launch, items (pass, piece) handed to the resident CTAs round robin, each
+// waiting (bounded) for its neighbour pieces to finish the previous pass.
+// Pass t reads the grid of map_e (t even) or map_o (t odd) and writes dst[t & 1]
+// (padded, pitches py/pz, ghost band gw) except the last pass, which writes
+// the Sweep3DArgs destination.
+constexpr int kDep3 = 5;  // neighbour tiles per axis and tile, -1 padded
+struct Sweep3DQueue {
+    int npass;
+    int *done;         // per piece: passes finished (zero before the launch)
+    const int *dep;    // neighbour tiles: x table (tiles_x x kDep3), then y, then z
+    int dep_y, dep_z;  // offsets of the y and z tables in dep
+    float *dst[2];     // destinations of even and odd passes (padded grid origins)
+    int64_t py, pz;
+    int gw;
+    int fault_withhold_dep;  // test hook: dependencies never count as met
+};
+bool sweep3d_q_supported(int rb, int m, int pattern);
+int sweep3d_q_ctas_per_sm(int rb, int m, int pattern, size_t smem);
+cudaError_t launch_sweep3d_q(int rb, int m, int pattern, const CUtensorMap &map_e,
+                             const CUtensorMap &map_o, const Sweep3DArgs &a,
+                             const Sweep3DQueue &q, int grid, size_t smem, cudaStream_t s);
 // Two fused 3D sweeps per launch (temporal blocking, b = 2): folded radius <= 2.
 // The staged boxes carry sweep3d_tb_halo_x() columns and 2R rows/planes of
 // halo per side; a.halo_x must be set to sweep3d_tb_halo_x().

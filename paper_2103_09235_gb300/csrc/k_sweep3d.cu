@@ -27,7 +27,6 @@ __global__ void __launch_bounds__(NT3)
 {
     using TP = Taps3<RB, M, PAT>;
     constexpr int R = TP::R, W = TP::W, RP = TP::RP;
-    constexpr int NSEG = 4 + 2 * RP;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *stages = reinterpret_cast<float *>(smem + 1024);
@@ -87,6 +86,7 @@ __global__ void __launch_bounds__(NT3)
     const int X = x0 + 4 * strip, Y = y0 + yr;
     const bool live = (Y < a.ny) && (X < a.nx);
     const bool vec4 = a.dst_vec4 && X + 3 < a.nx;  // one 16-byte store per plane
+    const Dst3 dst = dst_of(a);
 
     float acc[W][4];
 #pragma unroll
@@ -107,52 +107,10 @@ __global__ void __launch_bounds__(NT3)
         for (int q = 0; q < ZC; ++q) {
             const int p = c * ZC + q;
             if (p >= nin) break;
-            const float *pl = chunk + q * plane;
             // this input plane feeds output plane z - R + i with plane offset R - i
-#pragma unroll
-            for (int dy = -R; dy <= R; ++dy) {
-                float seg[NSEG];
-                const float4 *rp = reinterpret_cast<const float4 *>(pl + (yr + R + dy) * SP);
-#pragma unroll
-                for (int k = 0; k < NSEG / 4; ++k) {
-                    const float4 t = rp[k];
-                    seg[4 * k] = t.x;
-                    seg[4 * k + 1] = t.y;
-                    seg[4 * k + 2] = t.z;
-                    seg[4 * k + 3] = t.w;
-                }
-#pragma unroll
-                for (int i = 0; i < W; ++i) {
-                    const int az = R - i;
-#pragma unroll
-                    for (int dx = -R; dx <= R; ++dx) {
-                        if (TP::nz(az, dy, dx)) {
-                            const float w = a.c[((az + R) * W + (dy + R)) * W + (dx + R)];
-#pragma unroll
-                            for (int v = 0; v < 4; ++v)
-                                acc[i][v] = fmaf(w, seg[v + dx + RP], acc[i][v]);
-                        }
-                    }
-                }
-            }
+            add_plane3<RB, M, PAT>(acc, chunk + q * plane, yr, SP, a);
             const int zo = zin0 + p - R;  // output plane completed by this input plane
-            if (zo >= z0 && live) {
-                float *row = a.dst + zo * a.dst_pz + Y * a.dst_py;
-                if (vec4) {
-                    *reinterpret_cast<float4 *>(row + X) =
-                        make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
-                } else {
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-                        if (X + v < a.nx) row[X + v] = acc[0][v];
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < W - 1; ++i)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
+            emit_plane3<W>(acc, dst, X, Y, zo, a.nx, zo >= z0 && live, vec4);
         }
         __syncwarp();  // this warp is done with stage s
         if ((tid & 31) == 0) mbar_arrive(&empty[s]);
@@ -160,7 +118,7 @@ __global__ void __launch_bounds__(NT3)
     // every consumer gets here (all waits are bounded); the ghost band is
     // refreshed once all of the CTA's outputs are stored
     if (consumers_any3<NC3>(failed) || a.dst_gw <= 0) return;
-    refresh_ghosts3<NC3>(a, x0, y0, z0, z1, tid);
+    refresh_ghosts3<NC3>(a, dst, x0, y0, z0, z1, tid);
 }
 
 template <int RB, int M, int PAT>

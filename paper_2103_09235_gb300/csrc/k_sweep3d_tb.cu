@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(NTT)
         }
     }
     if (consumers_any3<NCT>(failed) || a.dst_gw <= 0) return;
-    refresh_ghosts3<NCT>(a, x0, y0, z0, z1, tid);
+    refresh_ghosts3<NCT>(a, dst_of(a), x0, y0, z0, z1, tid);
 }
 
 }  // namespace

@@ -39,6 +39,7 @@ struct stencil_plan_s {
     int stages = 0;  // TMA stages per CTA of the 2D sweep (0 = automatic)
     int cta_threads = 0;  // threads per CTA of the 2D sweep (0 = automatic, or 256)
     int z_chunk = 0;  // output planes per CTA of the 3D sweeps (0 = automatic)
+    int persistent = -1;  // 3D single sweeps in one persistent launch: 1 always, 0 never, -1 automatic
     int tc_center = 1;
     int tc_tma_store = 1;
     int tc_form = 0;  // tensor cores: 0 by folded radius, 1 one MMA per row offset, 2 grouped
@@ -87,6 +88,9 @@ struct stencil_plan_s {
     int use_graph = 1;
     // device work lists of batched runs led by this plan, by batch key
     std::map<std::vector<int64_t>, unsigned char *> batch_mem;
+    // multi-pass 3D sweeps: per (R, z chunk, halo columns) the pieces' pass
+    // counters and neighbour lists
+    std::map<std::tuple<int, int, int>, int *> q3_mem;
 
     // bookkeeping
     long long launches = 0;
@@ -94,6 +98,7 @@ struct stencil_plan_s {
     int last_tc_form = 0;  // tensor-core kernel of the last tensor-core run (1 or 2)
     int last_ty = 0;  // tile height of the last 2D CUDA-core run's first pass
     int last_threads = 0;  // threads per CTA of the last batched launch
+    int last_persist = 0;  // 1 if the last 3D run used the multi-pass persistent launch
     int last_cp = 0;  // counterpart terms of the last 2D CUDA-core run's folded passes (0 = direct)
     int last_tess = 0;  // 1 if the last 1D run's folded passes used exact tessellate tiling
     // autotuner choice for fold_m = 0: m, b, tile_y, engine (m = 0: not tuned yet)

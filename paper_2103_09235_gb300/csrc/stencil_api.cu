@@ -353,6 +353,9 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "cta_threads")) {
         if (v != 0 && v != 256) goto bad;
         p->cta_threads = (int)v;
+    } else if (!strcmp(key, "persistent")) {
+        if (v < -1 || v > 1) goto bad;
+        p->persistent = (int)v;
     } else if (!strcmp(key, "z_chunk")) {
         if (v != 0 && (v < 4 || v > 1024 || v % 4)) goto bad;
         p->z_chunk = (int)v;
@@ -419,6 +422,7 @@ stencil_status_t stencil_plan_get(stencil_plan_t p, const char *key, int64_t *va
     else if (!strcmp(key, "last_tile_y")) *value = p->last_ty;
     else if (!strcmp(key, "last_engine")) *value = p->last_engine;
     else if (!strcmp(key, "last_threads")) *value = p->last_threads;
+    else if (!strcmp(key, "last_persistent")) *value = p->last_persist;
     else if (!strcmp(key, "last_tc_form")) *value = p->last_tc_form;
     else if (!strcmp(key, "last_cp")) *value = p->last_cp;
     else if (!strcmp(key, "last_tess")) *value = p->last_tess;
@@ -578,6 +582,7 @@ void stencil_plan_destroy(stencil_plan_t p)
     if (p->stage_out) cudaFree(p->stage_out);
     for (auto &kv : p->panels) cudaFree(kv.second);
     for (auto &kv : p->batch_mem) cudaFree(kv.second);
+    for (auto &kv : p->q3_mem) cudaFree(kv.second);
     delete p;
 }
 

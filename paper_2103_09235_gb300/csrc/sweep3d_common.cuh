@@ -27,11 +27,22 @@ struct Taps3 {
     }
 };
 
+// Where a sweep's outputs go: the origin (interior point 0) of a grid, its
+// row and plane pitches and the ghost band to refresh (0 = none).
+struct Dst3 {
+    float *p;
+    int64_t py, pz;
+    int gw;
+};
+
+__device__ __forceinline__ Dst3 dst_of(const Sweep3DArgs &a) { return {a.dst, a.dst_py, a.dst_pz, a.dst_gw}; }
+
 // Copies of output (X, Y, Z) across every edge of the ghost band it lies
 // within (up to seven: faces, edges and corners of the periodic box).
-__device__ __forceinline__ void mirror3(const Sweep3DArgs &a, int X, int Y, int Z, float v)
+__device__ __forceinline__ void mirror3(const Sweep3DArgs &a, const Dst3 &d, int X, int Y, int Z,
+                                        float v)
 {
-    const int gw = a.dst_gw;
+    const int gw = d.gw;
     // per axis: the cell itself, its copy past the high edge, past the low edge
     const int xs[3] = {X, X < gw ? X + a.nx : INT_MIN, X >= a.nx - gw ? X - a.nx : INT_MIN};
     const int ys[3] = {Y, Y < gw ? Y + a.ny : INT_MIN, Y >= a.ny - gw ? Y - a.ny : INT_MIN};
@@ -43,7 +54,7 @@ __device__ __forceinline__ void mirror3(const Sweep3DArgs &a, int X, int Y, int 
 #pragma unroll
             for (int k = 0; k < 3; ++k)
                 if ((i | j | k) && zs[i] != INT_MIN && ys[j] != INT_MIN && xs[k] != INT_MIN)
-                    a.dst[zs[i] * a.dst_pz + ys[j] * a.dst_py + xs[k]] = v;
+                    d.p[zs[i] * d.pz + ys[j] * d.py + xs[k]] = v;
 }
 
 // Ghost band of a padded destination, for the CTA's block of outputs
@@ -55,10 +66,10 @@ __device__ __forceinline__ void mirror3(const Sweep3DArgs &a, int X, int Y, int 
 // CTAs that touch the band have work; a cell in two bands is handled twice,
 // writing the same values.
 template <int NC>
-__device__ __forceinline__ void refresh_ghosts3(const Sweep3DArgs &a, int x0, int y0, int z0,
-                                                int z1, int tid)
+__device__ __forceinline__ void refresh_ghosts3(const Sweep3DArgs &a, const Dst3 &d, int x0,
+                                                int y0, int z0, int z1, int tid)
 {
-    const int gw = a.dst_gw, nx = a.nx, ny = a.ny, nz = a.nz;
+    const int gw = d.gw, nx = a.nx, ny = a.ny, nz = a.nz;
     const int vx = min(TX3, nx - x0), vy = min(TY3, ny - y0);
     const int nt = y0 < gw ? min(y0 + vy, gw) - y0 : 0;  // band rows and columns of the tile
     const int yb0 = max(y0, ny - gw), nb = y0 + vy > yb0 ? y0 + vy - yb0 : 0;
@@ -98,12 +109,75 @@ __device__ __forceinline__ void refresh_ghosts3(const Sweep3DArgs &a, int x0, in
                 Y[u] = y0 + c / vx;
                 X[u] = x0 + c % vx;
             }
-            v[u] = a.dst[Z[u] * a.dst_pz + Y[u] * a.dst_py + X[u]];
+            v[u] = d.p[Z[u] * d.pz + Y[u] * d.py + X[u]];
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (base + u * NC < total) mirror3(a, X[u], Y[u], Z[u], v[u]);
+            if (base + u * NC < total) mirror3(a, d, X[u], Y[u], Z[u], v[u]);
     }
+}
+
+// Adds one staged input plane into a thread's register window of W output
+// planes (4 columns each): with the weights of plane offset R - i, into the
+// partial sums of output plane i of the window.  `pl` points at the thread's
+// strip in the plane's first staged row, RP columns before its first output
+// column; rows are SP floats apart and the thread's row is yr.
+template <int RB, int M, int PAT>
+__device__ __forceinline__ void add_plane3(float (&acc)[Taps3<RB, M, PAT>::W][4], const float *pl,
+                                           int yr, int SP, const Sweep3DArgs &a)
+{
+    using TP = Taps3<RB, M, PAT>;
+    constexpr int R = TP::R, W = TP::W, RP = TP::RP;
+    constexpr int NSEG = 4 + 2 * RP;
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy) {
+        float seg[NSEG];
+        const float4 *rp = reinterpret_cast<const float4 *>(pl + (yr + R + dy) * SP);
+#pragma unroll
+        for (int k = 0; k < NSEG / 4; ++k) {
+            const float4 t = rp[k];
+            seg[4 * k] = t.x;
+            seg[4 * k + 1] = t.y;
+            seg[4 * k + 2] = t.z;
+            seg[4 * k + 3] = t.w;
+        }
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const int az = R - i;
+#pragma unroll
+            for (int dx = -R; dx <= R; ++dx) {
+                if (TP::nz(az, dy, dx)) {
+                    const float w = a.c[((az + R) * W + (dy + R)) * W + (dx + R)];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[i][v] = fmaf(w, seg[v + dx + RP], acc[i][v]);
+                }
+            }
+        }
+    }
+}
+
+// Stores the window's completed plane (acc[0]: 4 columns from X of row Y)
+// when `store`, then shifts the window by one plane.
+template <int W>
+__device__ __forceinline__ void emit_plane3(float (&acc)[W][4], const Dst3 &d, int X, int Y,
+                                            int zo, int nx, bool store, bool vec4)
+{
+    if (store) {
+        float *row = d.p + zo * d.pz + Y * d.py;
+        if (vec4) {
+            *reinterpret_cast<float4 *>(row + X) = make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                if (X + v < nx) row[X + v] = acc[0][v];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < W - 1; ++i)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[i][v] = acc[i + 1][v];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[W - 1][v] = 0.f;
 }
 
 // OR of a predicate over the consumer threads (named barrier 1); also orders

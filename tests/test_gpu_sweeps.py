@@ -392,6 +392,90 @@ def test_sweep3d_z_chunk(env, shape, kind, m, zc):
     assert info["m"] == m
 
 
+CASES_3D_PERSISTENT = [
+    # shape (z, y, x), kind, r, T, m, z_chunk: many passes in one persistent
+    # launch; ragged tiles, tiny grids (one or two tiles per axis, so a piece
+    # is its own periodic neighbour), many z chunks, folded runs with a plain
+    # remainder, and fewer items per pass than resident CTAs
+    ((100, 40, 70), "star", 1, 23, 1, 0),
+    ((100, 40, 70), "box", 1, 21, 1, 0),
+    ((66, 33, 130), "box", 1, 17, 2, 0),
+    ((100, 40, 70), "star", 1, 19, 2, 8),
+    ((40, 36, 64), "star", 2, 12, 1, 0),
+    ((40, 36, 64), "box", 2, 9, 1, 4),
+    ((12, 9, 11), "star", 1, 15, 2, 0),
+    ((7, 6, 9), "box", 1, 14, 1, 4),
+    ((150, 20, 24), "box", 1, 25, 1, 8),
+    ((150, 20, 24), "star", 1, 31, 3, 0),
+    ((96, 80, 200), "box", 1, 12, 1, 0),
+]
+
+
+@pytest.mark.parametrize("shape,kind,r,T,m,zc", CASES_3D_PERSISTENT)
+def test_sweep3d_persistent(env, shape, kind, r, T, m, zc):
+    """The persistent multi-pass launch: bit-identical to one launch per pass
+    (the same arithmetic in the same order) and within the oracle's bounds;
+    the passes of one stencil take one launch."""
+    _, _, oracle = env
+    c = synth.dyadic_coeffs(3300 + r, 3, r, kind)
+    x = synth.grid(3400 + T, shape, np.float32)
+    y0, i0 = gpu_run(env, shape, c, x, T, m, block_b=1, z_chunk=zc, persistent=0)
+    y1, i1 = gpu_run(env, shape, c, x, T, m, block_b=1, z_chunk=zc, persistent=1)
+    assert np.array_equal(y0, y1)
+    check(y1, oracle.run(x.astype(np.float64), c, T))
+    assert i1["m"] == m
+    nfold, rem = divmod(T, m)
+    per_pass = nfold + rem
+    groups = (nfold >= 2) + (rem >= 2) + (nfold == 1) + (rem == 1)
+    assert i0["launches"] - i1["launches"] == per_pass - groups
+
+
+@pytest.mark.parametrize("shape,expect", [((256, 256, 256), 1), ((64, 64, 64), 0)])
+def test_sweep3d_persistent_automatic(env, shape, expect):
+    """The automatic choice (persistent option -1): one persistent launch when
+    a pass has between one and 3.5 waves of pieces (the 256^3 grid: 1024
+    pieces on 608 resident CTAs), one launch per pass for a grid with fewer
+    pieces than CTAs; the result is the oracle's either way (checked at 64^3)."""
+    torch, binding, oracle = env
+    c = synth.dyadic_coeffs(3500, 3, 1, "box")
+    x = synth.grid(3501, shape, np.float32)
+    plan = binding.Plan(shape, c).set_option("block_b", 1).set_option("autotune", 0)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, 4, fold_m=1)
+    plan.sync()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    if shape[0] == 256 and sms == 152:
+        assert plan.get("last_persistent") == expect
+    if shape[0] == 64:
+        assert plan.get("last_persistent") == expect
+        check(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, 4))
+    plan.close()
+
+
+@pytest.mark.parametrize("hook", ["fault_withhold_dep", "fault_withhold_copy"])
+def test_bounded_wait_reports_timeout_3d_persistent(env, hook):
+    """The persistent 3D launch: dependencies that never count as met, or a
+    withheld chunk, end the producer's and the consumers' bounded waits with
+    a status; the next run is correct."""
+    torch, binding, oracle = env
+    shape = (40, 48, 64)
+    c = synth.dyadic_coeffs(25, 3, 1, "box")
+    x = synth.grid(26, shape, np.float32)
+    plan = binding.Plan(shape, c).set_option("block_b", 1).set_option("persistent", 1)
+    plan.set_option("wait_limit_ms", 50).set_option(hook, 1)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, 6, fold_m=1)
+    assert plan.sync_status() == 5
+    assert plan.sync_status() == 0
+    plan.set_option(hook, 0)
+    plan.run(xd, yd, 6, fold_m=1)
+    plan.sync()
+    check(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, 6))
+    plan.close()
+
+
 CASES_3D_FUSED = [
     # shape (z, y, x), kind, r, T, m: two fused sweeps per pass (block_b = 2)
     ((100, 40, 70), "star", 1, 7, 1),    # three pairs and one single sweep
