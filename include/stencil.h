@@ -245,8 +245,10 @@ stencil_status_t stencil_run(stencil_plan_t plan, const void *in, void *out, int
  *             has (the result is the same T steps).  With 0 and no block_b
  *             option on the grid's plan, the fold and blocking depth come from
  *             the batch autotuner, which times each class of grids (radius,
- *             pattern, floor(log2 area)) and caches its choice per class and
- *             GPU; it also picks the batch's tile height unless plans[0] sets
+ *             pattern, floor(log2 area)) and caches its choices per batch
+ *             composition (the set of classes) and GPU, so that one batch's
+ *             choice for a class never seeds another batch; it also picks the
+ *             batch's tile height unless plans[0] sets
  *             the "tile_y" option, which then pins it (at most 128 rows), and
  *             the CTA shape: 512 threads, one CTA per SM, or 256 threads, two
  *             per SM with tiles that fit half an SM's shared memory (pinned

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <map>
+#include <sstream>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -453,33 +454,61 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
             bs[g] = clamp_b(plans[g], ms[g], b);
         }
     };
+    // The cache holds one entry per batch composition (its set of classes):
+    // "tile_y threads" and then every class's "m b" in class order.  Class
+    // entries (one per class, "m b") are written too and read only for a
+    // composition entry without the per-class choices.  Another batch's
+    // choice for a class (e.g. b = 3, fine for a few small grids) can shorten
+    // every tile of a batch it does not suit, so a new composition is tuned
+    // from the default choices.
     std::string tile_key = "batched-tile|";
-    bool all_cached = true;
     for (auto &kv : classes) {
         char cls[64];
         snprintf(cls, sizeof(cls), "r%d.p%d.a%d;", kv.first.r, kv.first.pattern,
                  kv.first.size_class);
         tile_key += cls;
-        std::string v;
-        int m = 0, b = 0;
-        if (tune_cache_get(class_cache_key(kv.first, prop.name), &v) &&
-            sscanf(v.c_str(), "%d %d", &m, &b) == 2 && m >= 1 && b >= 1)
-            apply(kv.first, m, b);
-        else
-            all_cached = false;
     }
     if (half_only) tile_key += "t256;";
     tile_key += std::string("|") + prop.name;
     int ty = kBatchTileYMax, thr = thr_start;
+    bool all_cached = false;
     {
         std::string v;
         int t = 0, h = 0;
         if (tune_cache_get(tile_key, &v) && sscanf(v.c_str(), "%d %d", &t, &h) == 2 && t >= 16 &&
             t <= kBatchTileYMax && (h == thr_wide || h == thr_half) && !(half_only && h != thr_half)) {
-            ty = t;
-            thr = h;
-        } else {
-            all_cached = false;
+            all_cached = true;
+            // the composition's own per-class choices, if it carries them
+            std::vector<int> own;
+            {
+                std::istringstream is(v);
+                int x = 0;
+                while (is >> x) own.push_back(x);
+            }
+            const bool has_own = own.size() == 2 + 2 * classes.size();
+            std::vector<std::pair<ClassKey, std::pair<int, int>>> got;
+            size_t ci = 0;
+            for (auto &kv : classes) {
+                std::string cv;
+                int m = 0, b = 0;
+                if (has_own) {
+                    m = own[2 + 2 * ci];
+                    b = own[3 + 2 * ci];
+                } else if (!(tune_cache_get(class_cache_key(kv.first, prop.name), &cv) &&
+                             sscanf(cv.c_str(), "%d %d", &m, &b) == 2)) {
+                    m = b = 0;
+                }
+                ++ci;
+                if (m >= 1 && b >= 1)
+                    got.push_back({kv.first, {m, b}});
+                else
+                    all_cached = false;
+            }
+            if (all_cached) {
+                for (auto &g : got) apply(g.first, g.second.first, g.second.second);
+                ty = t;
+                thr = h;
+            }
         }
     }
     if (all_cached || !p0->autotune) {
@@ -639,9 +668,12 @@ stencil_status_t tune_batch(int n, stencil_plan_s *const *plans, const void *con
         snprintf(v, sizeof(v), "%d %d", kv.second.first, kv.second.second);
         tune_cache_put(class_cache_key(kv.first, prop.name), v);
     }
-    char v[32];
-    snprintf(v, sizeof(v), "%d %d", ty, thr);
-    tune_cache_put(tile_key, v);
+    std::string tv = std::to_string(ty) + " " + std::to_string(thr);
+    for (auto &kv : classes) {
+        const std::pair<int, int> &mb = best_choice[kv.first];
+        tv += " " + std::to_string(mb.first) + " " + std::to_string(mb.second);
+    }
+    tune_cache_put(tile_key, tv);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(scratch);

@@ -157,6 +157,67 @@ def test_batched_uses_cached_choice(env, tmp_path, monkeypatch, threads):
         p.close()
 
 
+def _class_keys(specs):
+    import math
+    classes = []
+    for shape, kind, r, T, seed in specs:
+        cls = (r, 0 if kind == "star" else 1, int(math.floor(math.log2(shape[0] * shape[1]))))
+        if cls not in classes:
+            classes.append(cls)
+    return sorted(classes)
+
+
+def test_batched_composition_entry_wins(env, tmp_path, monkeypatch):
+    """A batch composition's cache entry carries its own per-class choices
+    ("tile_y threads" then "m b" per class in class order) and they take
+    precedence over the per-class entries another batch may have written."""
+    torch, binding, oracle = env
+    gpu = torch.cuda.get_device_name()
+    classes = _class_keys(SPECS)
+    lines = ['{"key": "batched|2d|r%d|pat%d|area2^%d|f32|%s", "value": "1 3"}' % (c + (gpu,))
+             for c in classes]
+    own = " ".join("3 2" if c[1] == 0 else "2 2" for c in classes)
+    tile = "batched-tile|" + "".join("r%d.p%d.a%d;" % c for c in classes) + "|" + gpu
+    lines.append('{"key": "%s", "value": "64 512 %s"}' % (tile, own))
+    cache = tmp_path / "tune.jsonl"
+    cache.write_text("\n".join(lines) + "\n")
+    monkeypatch.setenv("STENCIL_TUNE_CACHE", str(cache))
+    plans, xs, ys, refs_in = _batch_plans(binding, torch, SPECS)
+    binding.run_batched(plans, xs, ys, [t for _, _, t in refs_in])
+    plans[0].sync()
+    for p, (shape, kind, r, T, seed) in zip(plans, SPECS):
+        assert (p.get("last_m"), p.get("last_b")) == ((3, 2) if kind == "star" else (2, 2))
+        assert p.get("last_tile_y") == 64 and p.get("last_threads") == 512
+    for y, (x, c, T) in zip(ys, refs_in):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
+    for p in plans:
+        p.close()
+
+
+def test_batched_new_composition_ignores_other_class_entries(env, tmp_path, monkeypatch):
+    """Class entries alone (written by other batches) do not seed a batch
+    whose composition has no entry: with autotuning off it runs the default
+    choices (stars m = 3, boxes m = 2, b = 2), not the cached b = 3."""
+    torch, binding, oracle = env
+    gpu = torch.cuda.get_device_name()
+    lines = ['{"key": "batched|2d|r%d|pat%d|area2^%d|f32|%s", "value": "1 3"}' % (c + (gpu,))
+             for c in _class_keys(SPECS)]
+    cache = tmp_path / "tune.jsonl"
+    cache.write_text("\n".join(lines) + "\n")
+    monkeypatch.setenv("STENCIL_TUNE_CACHE", str(cache))
+    plans, xs, ys, refs_in = _batch_plans(binding, torch, SPECS)
+    for p in plans:
+        p.set_option("autotune", 0)
+    binding.run_batched(plans, xs, ys, [t for _, _, t in refs_in])
+    plans[0].sync()
+    for p, (shape, kind, r, T, seed) in zip(plans, SPECS):
+        assert (p.get("last_m"), p.get("last_b")) == ((3, 2) if kind == "star" else (2, 2))
+    for y, (x, c, T) in zip(ys, refs_in):
+        assert oracle.rel_l2(y.cpu().numpy(), oracle.run(x.astype(np.float64), c, T)) <= 1e-5
+    for p in plans:
+        p.close()
+
+
 @pytest.mark.parametrize("tile", [64, 96])
 def test_batched_tile_pinned_by_first_plan(env, tile):
     """The first plan's tile_y option pins the batch's tile height."""
