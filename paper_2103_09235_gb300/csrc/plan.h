@@ -127,6 +127,37 @@ inline bool grid_vec4(const stencil_plan_s *p, const void *base)
            (uintptr_t)base % 16 == 0;
 }
 
+// One axis of the multi-pass sweep's neighbour lists.  Tile t (of ntile
+// tiles of S cells over n cells) reads the cells [lo(t), hi(t)) of the
+// previous pass's grid, ghost cells standing for their periodic images.  Its
+// list holds the tiles owning such a cell (whose output it reads) and the
+// tiles whose window holds one of its cells (whose reads of the grid it will
+// overwrite two passes on), -1 padded to kDep3 entries.  False if a list
+// would be longer.
+template <class Window>
+inline bool axis_deps(int n, int S, int ntile, Window window, int *out)
+{
+    std::vector<std::vector<char>> rel(ntile, std::vector<char>(ntile, 0));
+    for (int t = 0; t < ntile; ++t) {
+        const std::pair<int, int> w = window(t);
+        for (int c = w.first; c < w.second; ++c) {
+            const int o = (((c % n) + n) % n) / S;
+            rel[t][o] = 1;  // t reads o's cells
+            rel[o][t] = 1;  // o's writes replace what t read
+        }
+    }
+    for (int t = 0; t < ntile; ++t) {
+        int k = 0;
+        for (int o = 0; o < ntile; ++o) {
+            if (!rel[t][o]) continue;
+            if (k == kDep3) return false;
+            out[t * kDep3 + k++] = o;
+        }
+        for (; k < kDep3; ++k) out[t * kDep3 + k] = -1;
+    }
+    return true;
+}
+
 // Copies the nx x ny x nz points of a caller-layout grid (both sides use the
 // plan's pitches), skipping the gaps between rows and planes.
 cudaError_t copy_grid(const stencil_plan_s *p, void *dst, const void *src, cudaMemcpyKind kind,

@@ -411,7 +411,7 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
     };
     std::vector<int64_t> key = {2, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, b,
                                 p->tile_y, p->wait_ms, p->fault_withhold_copy, cpm->k, cp1->k,
-                                cr.on ? 1 : 0};
+                                cr.on ? 1 : 0, p->cta_threads, p->stages};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = b;
