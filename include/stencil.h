@@ -147,7 +147,10 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *                   per pass; -1 (default) = persistent when a pass has more
  *                   than one and at most 3.5 waves of pieces (grids of about
  *                   192^3 to 320^3, where each pass's last wave leaves SMs
- *                   idle).  Same results either way.
+ *                   idle).  Same results either way.  Like the batch queue,
+ *                   the persistent launch needs all its CTAs resident at once;
+ *                   if other work holds SMs past the wait limit, the run ends
+ *                   with TIMEOUT (reported by stencil_sync).
  *   "tc_center"     1 = subtract the grid mean before the BF16 split (default 1).
  *   "center"        2D/3D CUDA-core runs and batches: 1 = store the grid minus its mean
  *                   mu (from an FP64 sum of the input) and add mu * (sum c)^T to the
@@ -254,7 +257,9 @@ stencil_status_t stencil_run(stencil_plan_t plan, const void *in, void *out, int
  *             per SM with tiles that fit half an SM's shared memory (pinned
  *             by "cta_threads" 256 on plans[0]).
  * Grids must not alias one another.  Errors as for stencil_run; a timed-out
- * dependency wait is reported by stencil_sync on plans[0].
+ * dependency wait is reported by stencil_sync on plans[0] (the launch needs
+ * all its CTAs resident at once: other work holding SMs past the wait limit
+ * ends it that way).
  */
 stencil_status_t stencil_run_batched(int n, const stencil_plan_t *plans,
                                      const void *const *in, void *const *out,
