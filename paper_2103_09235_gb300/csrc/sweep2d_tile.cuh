@@ -171,7 +171,7 @@ __device__ __forceinline__ void sweep_region(const float *__restrict__ S, float 
     const int nr = r1 - r0;
     if (nsx <= 0 || nr <= 0) return;
     // row groups: as many as the threads allow, each at least 2R rows tall
-    const int nthr = Sync::nthr();  // 256 or 512, chosen per kernel instance
+    const int nthr = Sync::nthr();  // the threads running the tile body (224 to 512)
     int G;
     uint32_t mn = 0, mg = 0;
     if (gm && gm->nsx_G == 0) gm = nullptr;  // a split without a usable reciprocal
