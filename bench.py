@@ -369,6 +369,8 @@ def plan_facts(plan, ndim):
     if ndim == 2 and engine == "cuda-core":
         f["tile_y"] = plan.get("last_tile_y")
         f["counterparts"] = plan.get("last_cp")
+        f["cta_threads"] = plan.get("last_threads")
+        f["stages"] = plan.get("last_stages")
     if engine == "tensor-core":
         f["tc_kernel"] = "grouped" if plan.get("last_tc_form") == 2 else "per-offset"
     if ndim == 3 and engine == "cuda-core":
@@ -734,10 +736,11 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args.config),
             "run": {"fold_m": facts["m"], "block_b": facts["b"],
-                    "tile_y": facts.get("tile_y"), "engine": facts["engine"],
+                    "tile_y": facts.get("tile_y"), "cta_threads": facts.get("cta_threads"),
+                    "stages": facts.get("stages"), "engine": facts["engine"],
                     "counterparts": facts.get("counterparts", 0),
                     "tc_kernel": facts.get("tc_kernel"),
-                    "precision": ["fp32", "bf16x3", "bf16x1"][args.precision],
+                    "precision": ["fp32", "bf16x3", "bf16x1", "tf32x3"][args.precision],
                     "chosen_by": "autotuner" if args.fold_m == 0 else "command line",
                     "parallelism": "replicas" if ws > 1 else "single"},
             "l2": "flushed between timed steps (512 MB write)",

@@ -189,9 +189,10 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *                   never issue a CTA's first copy, so their bounded waits run out
  *                   and stencil_sync reports STENCIL_ERR_TIMEOUT (no GPU fault; the
  *                   context stays usable).
- *   "fault_withhold_dep"   test hook: 1 = in a batched run led by this plan every
- *                   dependency on a previous pass counts as unmet, so the work
- *                   queue's bounded dependency wait runs out (TIMEOUT, as above).
+ *   "fault_withhold_dep"   test hook: 1 = in a batched run led by this plan, or in
+ *                   this plan's persistent 3D launch, every dependency on a
+ *                   previous pass counts as unmet, so the bounded dependency
+ *                   wait runs out (TIMEOUT, as above).
  *   "fault_withhold_mma"   test hook: 1 = the tensor-core kernels' MMA issuer stops
  *                   before its first MMA, so the other roles' bounded waits run out
  *                   (TIMEOUT, as above; tensor memory is still freed).
@@ -207,7 +208,9 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, i
  * CUDA-core run's folded passes in counterpart form, 0 = direct form),
  * "last_tess" (1 if the last 1D run's first pass was tessellated exactly),
  * "last_threads" (threads per CTA of the last stencil_run_batched launch: 512,
- * or 256 for two CTAs per SM), "last_persistent" (1 if the last 3D CUDA-core
+ * or 256 for two CTAs per SM; or of the first pass of the last 2D CUDA-core
+ * run), "last_stages" (TMA stages per CTA of that pass), "last_persistent"
+ * (1 if the last 3D CUDA-core
  * run took its single sweeps in one persistent multi-pass launch),
  * "launches" (kernels the plan has launched so far),
  * "scratch_bytes" (device bytes the plan owns).

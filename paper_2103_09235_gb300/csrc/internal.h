@@ -86,6 +86,8 @@ size_t sweep2d_smem_bytes(int tile_y, int b, int R, int *buf_floats, int nstages
 // threads: 0 = the instance's own block size; 256 = two half-size CTAs for
 // instances that run 512.
 int sweep2d_ctas_per_sm(int rb, int m, int pattern, size_t smem, int threads = 0);
+// Threads per CTA a launch of the instance runs (threads as for the launch).
+int sweep2d_block_threads(int rb, int m, int pattern, int threads = 0);
 cudaError_t launch_sweep2d(int rb, int m, int pattern, const CUtensorMap &map,
                            const Sweep2DArgs &a, int grid, size_t smem, int threads,
                            cudaStream_t s);

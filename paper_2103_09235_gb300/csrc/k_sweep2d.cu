@@ -210,6 +210,15 @@ int sweep2d_ctas_per_sm(int rb, int m, int pattern, size_t smem, int threads)
     return 0;
 }
 
+int sweep2d_block_threads(int rb, int m, int pattern, int threads)
+{
+#define SG_X(RB_, M_, P_) \
+    if (rb == RB_ && m == M_ && pattern == P_) return threads_t<RB_, M_, P_>(threads);
+    SG_SWEEP2D_LIST(SG_X)
+#undef SG_X
+    return 0;
+}
+
 cudaError_t launch_sweep2d(int rb, int m, int pattern, const CUtensorMap &map,
                            const Sweep2DArgs &a, int grid, size_t smem, int threads,
                            cudaStream_t s)

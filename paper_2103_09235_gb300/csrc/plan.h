@@ -97,7 +97,8 @@ struct stencil_plan_s {
     int last_m = 0, last_b = 0, last_engine = 0;
     int last_tc_form = 0;  // tensor-core kernel of the last tensor-core run (1 or 2)
     int last_ty = 0;  // tile height of the last 2D CUDA-core run's first pass
-    int last_threads = 0;  // threads per CTA of the last batched launch
+    int last_threads = 0;  // threads per CTA: the last batched launch, or the last 2D run's first pass
+    int last_stages = 0;   // TMA stages per CTA of the last 2D CUDA-core run's first pass
     int last_persist = 0;  // 1 if the last 3D run used the multi-pass persistent launch
     int last_cp = 0;  // counterpart terms of the last 2D CUDA-core run's folded passes (0 = direct)
     int last_tess = 0;  // 1 if the last 1D run's folded passes used exact tessellate tiling

@@ -366,12 +366,18 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
     int gw = 0;
     for (const Pass &ps : passes) gw = std::max(gw, ps.b * ps.m * p->r);
     // resolve every pass configuration before any capture starts
-    int first_ty = 0;
+    int first_ty = 0, first_thr = 0, first_ns = 0;
     for (const Pass &ps : passes) {
         stencil_plan_s::PassCfg cfg;
         st = pass2d_config(p, ps.m, ps.b, &cfg, cp_of(ps)->k);
         if (st != STENCIL_OK) return st;
-        if (!first_ty) first_ty = cfg.ty;
+        if (!first_ty) {
+            const int cpk = cp_of(ps)->k;
+            first_ty = cfg.ty;
+            first_ns = cfg.nstages;
+            first_thr = cpk ? sweep2d_block_threads(1, ps.m * p->r, PAT_CP1 + cpk - 1, cfg.threads)
+                            : sweep2d_block_threads(p->r, ps.m, p->pattern, cfg.threads);
+        }
     }
     const bool out_vec4 = grid_vec4(p, out);
     const CentredRun cr = centred_run(p, T);
@@ -416,6 +422,8 @@ stencil_status_t run2d(stencil_plan_s *p, const float *in, float *out, int64_t T
     p->last_m = m;
     p->last_b = b;
     p->last_ty = first_ty;
+    p->last_threads = first_thr;
+    p->last_stages = first_ns;
     p->last_cp = cpm->k;
     p->last_engine = 0;
     return st;

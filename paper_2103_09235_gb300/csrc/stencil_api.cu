@@ -422,6 +422,7 @@ stencil_status_t stencil_plan_get(stencil_plan_t p, const char *key, int64_t *va
     else if (!strcmp(key, "last_tile_y")) *value = p->last_ty;
     else if (!strcmp(key, "last_engine")) *value = p->last_engine;
     else if (!strcmp(key, "last_threads")) *value = p->last_threads;
+    else if (!strcmp(key, "last_stages")) *value = p->last_stages;
     else if (!strcmp(key, "last_persistent")) *value = p->last_persist;
     else if (!strcmp(key, "last_tc_form")) *value = p->last_tc_form;
     else if (!strcmp(key, "last_cp")) *value = p->last_cp;

@@ -96,14 +96,24 @@ def test_sweep2d_parity(env, shape, kind, r, T, m, b):
                                                    (64, 2, 256), (96, 1, 256), (32, 3, 0)])
 def test_sweep2d_tile_shapes(env, tile_y, stages, threads):
     """Tile heights, TMA stage counts (one stage: refilled after a tile's first
-    sweep) and half-size CTAs all give the oracle's result."""
-    _, _, oracle = env
+    sweep) and half-size CTAs all give the oracle's result; the plan reports
+    the CTA size and stage count its first pass ran with."""
+    torch, binding, oracle = env
     shape = (250, 300)
     c = synth.dyadic_coeffs(7, 2, 1, "star")
     x = synth.grid(8, shape, np.float32)
-    y, _ = gpu_run(env, shape, c, x, 18, 2, block_b=3, tile_y=tile_y, stages=stages,
-                   cta_threads=threads)
-    check(y, oracle.run(x.astype(np.float64), c, 18))
+    plan = binding.Plan(shape, c)
+    for k, v in dict(block_b=3, tile_y=tile_y, stages=stages, cta_threads=threads).items():
+        plan.set_option(k, v)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, 18, fold_m=2)
+    plan.sync()
+    check(yd.cpu().numpy(), oracle.run(x.astype(np.float64), c, 18))
+    assert plan.get("last_threads") == (256 if threads == 256 else 512)
+    if stages:
+        assert plan.get("last_stages") == stages
+    plan.close()
 
 
 CASES_1D = [
