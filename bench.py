@@ -607,6 +607,10 @@ def run_gpu(args):
         plan.set_option("tc_form", args.tc_form)
     if args.tile_y:
         plan.set_option("tile_y", args.tile_y)
+    if args.cta_threads:
+        plan.set_option("cta_threads", args.cta_threads)
+    if args.stages:
+        plan.set_option("stages", args.stages)
     m_req = args.fold_m
 
     xd = torch.from_numpy(x_host).to(dev)
@@ -772,6 +776,10 @@ def main():
     ap.add_argument("--block-b", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0,
                     help="rows per 2D tile (0 = the autotuner's or the library's choice)")
+    ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 256],
+                    help="2D CUDA-core sweeps: 256 = two half-size CTAs per SM (0 = automatic)")
+    ap.add_argument("--stages", type=int, default=0,
+                    help="2D CUDA-core sweeps: TMA stages per CTA (0 = automatic)")
     ap.add_argument("--tc-form", type=int, default=0, choices=[0, 1, 2],
                     help="tensor-core kernel: 0 by folded radius, 1 per row offset, 2 grouped")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1, 2, 3],
