@@ -136,7 +136,7 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *                   (chosen by the autotuner, else the kernel's own size), 256 =
  *                   two half-size CTAs per SM for folded sweeps that run 512,
  *                   and, on plans[0] of stencil_run_batched, for the batch.
- *   "z_chunk"       3D sweeps: output planes per CTA, a multiple of 4 in 4..1024
+ *   "z_chunk"       3D sweeps: output planes per CTA (or persistent piece), 2..1024
  *                   (0 = automatic: 16 for a single radius-1 sweep, else 32, halved
  *                   down to 8 while the grid has fewer than 4 CTAs per SM).
  *   "persistent"    3D CUDA-core runs: 1 = every run of two or more consecutive

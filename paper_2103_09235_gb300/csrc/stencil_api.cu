@@ -357,7 +357,7 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
         if (v < -1 || v > 1) goto bad;
         p->persistent = (int)v;
     } else if (!strcmp(key, "z_chunk")) {
-        if (v != 0 && (v < 4 || v > 1024 || v % 4)) goto bad;
+        if (v != 0 && (v < 2 || v > 1024)) goto bad;
         p->z_chunk = (int)v;
     } else if (!strcmp(key, "stages")) {
         if (v < 0 || v > 6) goto bad;

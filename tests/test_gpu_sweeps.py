@@ -389,7 +389,7 @@ def test_sweep3d_parity(env, shape, kind, r, T, m, stages):
     assert info["m"] == m
 
 
-@pytest.mark.parametrize("zc", [4, 8, 32, 1024])
+@pytest.mark.parametrize("zc", [2, 4, 6, 8, 14, 32, 1024])
 @pytest.mark.parametrize("shape,kind,m", [((150, 20, 24), "box", 1), ((100, 40, 70), "star", 2)])
 def test_sweep3d_z_chunk(env, shape, kind, m, zc):
     """The z_chunk option (output planes per CTA): chunks shorter than the halo,
@@ -416,6 +416,8 @@ CASES_3D_PERSISTENT = [
     ((12, 9, 11), "star", 1, 15, 2, 0),
     ((7, 6, 9), "box", 1, 14, 1, 4),
     ((150, 20, 24), "box", 1, 25, 1, 8),
+    ((150, 20, 24), "box", 1, 19, 1, 6),
+    ((100, 40, 70), "star", 1, 17, 1, 14),
     ((150, 20, 24), "star", 1, 31, 3, 0),
     ((96, 80, 200), "box", 1, 12, 1, 0),
 ]
