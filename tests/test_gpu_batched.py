@@ -250,15 +250,17 @@ def test_batched_half_size_ctas(env, fold):
         p.close()
 
 
+@pytest.mark.parametrize("threads", [0, 256])
 @pytest.mark.parametrize("fold", [None, 1, 2, 8])
-def test_batched_radius2_and_fold_clamp(env, fold):
+def test_batched_radius2_and_fold_clamp(env, fold, threads):
     """Radius-2 bases (stars folded up to m = 2, boxes plain) beside radius-1
-    ones; a fold request above the kernel's (8) is lowered to the largest it
-    has, which gives the same T steps."""
+    ones, with either CTA shape; a fold request above the kernel's (8) is
+    lowered to the largest it has, which gives the same T steps."""
     torch, binding, oracle = env
     specs = [((220, 260), "star", 2, 31, 9400), ((130, 170), "box", 2, 17, 9401),
              ((160, 150), "star", 1, 29, 9402), ((200, 120), "box", 1, 23, 9403)]
     plans, xs, ys, refs_in = _batch_plans(binding, torch, specs)
+    plans[0].set_option("cta_threads", threads)
     folds = None if fold is None else [fold] * len(specs)
     binding.run_batched(plans, xs, ys, [t for _, _, t in refs_in], folds)
     plans[0].sync()
