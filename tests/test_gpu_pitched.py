@@ -53,6 +53,9 @@ def gaps_untouched(buf, shape):
     ((257, 300), (0, 12), "box", 29, 3, {"block_b": 3}),
     ((40, 50, 60), (0, 3, 4), "star", 23, 2, {}),
     ((36, 40, 44), (0, 0, 20), "box", 21, 1, {"block_b": 2}),
+    # the persistent multi-pass launch writes its last pass into the strided grid
+    ((40, 50, 60), (0, 3, 4), "box", 19, 1, {"block_b": 1, "persistent": 1}),
+    ((36, 40, 44), (0, 5, 0), "star", 25, 2, {"block_b": 1, "persistent": 1, "z_chunk": 6}),
 ])
 def test_pitched_device_grid_matches_oracle(env, shape, pad, kind, T, m, opts):
     torch, binding, oracle = env
