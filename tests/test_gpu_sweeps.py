@@ -465,6 +465,30 @@ def test_sweep3d_persistent_automatic(env, shape, expect):
     plan.close()
 
 
+@pytest.mark.parametrize("in_place", [False, True])
+def test_sweep3d_persistent_replay_and_in_place(env, in_place):
+    """A second run of the same persistent 3D launch replays its captured graph
+    (the pass counters are zeroed inside it) and gives the same result; in
+    place (in == out) the input is imported before the first pass."""
+    torch, binding, oracle = env
+    shape = (70, 48, 100)
+    c = synth.dyadic_coeffs(3800, 3, 1, "box")
+    x = synth.grid(3801, shape, np.float32)
+    ref = oracle.run(x.astype(np.float64), c, 13)
+    plan = binding.Plan(shape, c).set_option("block_b", 1).set_option("persistent", 1)
+    outs = []
+    for _ in range(2):
+        xd = torch.from_numpy(x).cuda()
+        yd = xd if in_place else torch.empty_like(xd)
+        plan.run(xd, yd, 13, fold_m=1)
+        plan.sync()
+        assert plan.get("last_persistent") == 1
+        outs.append(yd.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    check(outs[1], ref)
+    plan.close()
+
+
 @pytest.mark.parametrize("hook", ["fault_withhold_dep", "fault_withhold_copy"])
 def test_bounded_wait_reports_timeout_3d_persistent(env, hook):
     """The persistent 3D launch: dependencies that never count as met, or a
