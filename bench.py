@@ -349,7 +349,7 @@ def roofline_of(alg_bytes, alg_flops, pass_ms, esz, engine, sms):
     return out
 
 
-def kernel_name(engine, grouped, ndim, b, cp_k, esz=4, persistent=0):
+def kernel_name(engine, grouped, ndim, b, cp_k, esz=4, persistent=0, tessellated=0):
     if engine == "tensor-core":
         if ndim == 3:  # one launch per plane offset, then the re-import of the result
             return "k_tc2d per plane offset + k_import"
@@ -357,7 +357,7 @@ def kernel_name(engine, grouped, ndim, b, cp_k, esz=4, persistent=0):
     if esz == 8 and ndim >= 2:
         return "k_sweep_f64"
     if ndim == 1:
-        return "k_sweep1d"
+        return "k_tess_tri + k_tess_inv" if tessellated else "k_sweep1d"
     if ndim == 3:
         return "k_sweep3d_tb" if b == 2 else ("k_sweep3d_q" if persistent else "k_sweep3d")
     return "k_sweep2d"
@@ -375,6 +375,9 @@ def plan_facts(plan, ndim):
         f["tc_kernel"] = "grouped" if plan.get("last_tc_form") == 2 else "per-offset"
     if ndim == 3 and engine == "cuda-core":
         f["persistent"] = plan.get("last_persistent")
+    if ndim == 1:
+        f["tile_1d"] = plan.get("last_tile_y")
+        f["tessellated"] = plan.get("last_tess")
     return f
 
 
@@ -415,7 +418,7 @@ def measure_run(torch, binding, stream, flush, plan, x, y, T, m, npts, esz, sms,
     plan.run(x, y, T, fold_m=m, stream=stream)
     plan.sync(stream)
     roof["kernel"] = kernel_name(f["engine"], f.get("tc_kernel") == "grouped", x.dim(), bu, cp_k,
-                                 esz, f.get("persistent", 0))
+                                 esz, f.get("persistent", 0), f.get("tessellated", 0))
     return ms_full, f, roof
 
 

@@ -139,6 +139,9 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *   "z_chunk"       3D sweeps: output planes per CTA (or persistent piece), 2..1024
  *                   (0 = automatic: 16 for a single radius-1 sweep, else 32, halved
  *                   down to 8 while the grid has fewer than 4 CTAs per SM).
+ *   "tile_1d"       1D sweeps: points per CTA tile, a multiple of 256 in 256..16384
+ *                   (0 = automatic: the autotuner's size for fold_m = 0, else 4096
+ *                   for FP32 and 2048 for FP64).
  *   "persistent"    3D CUDA-core runs: 1 = every run of two or more consecutive
  *                   single sweeps of one stencil in ONE persistent launch, whose
  *                   pieces (a 64 x 16 column, one z chunk) start as soon as the
@@ -203,7 +206,7 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t plan, const char *key, i
 /*
  * Reads a plan property.  Keys: "last_m", "last_b", "last_engine" (0 CUDA core,
  * 1 tensor core), "last_tile_y" (rows per tile of the last 2D CUDA-core run's
- * first pass), "last_tc_form" (1 per-offset, 2 grouped: the tensor-core kernel
+ * first pass, or points per tile of the last 1D run), "last_tc_form" (1 per-offset, 2 grouped: the tensor-core kernel
  * of the last tensor-core run), "last_cp" (separable terms K of the last 2D
  * CUDA-core run's folded passes in counterpart form, 0 = direct form),
  * "last_tess" (1 if the last 1D run's first pass was tessellated exactly),

@@ -29,13 +29,21 @@ namespace sg {
 
 namespace {
 
-constexpr const char *kLibVersion = "9";
-// Steps of a timed candidate run.
-constexpr int64_t kTuneSteps(int ndim) { return ndim == 1 ? 96 : 48; }
+constexpr const char *kLibVersion = "10";
+// Steps of a timed candidate run: 48 for 2D/3D; for 1D the run's own step
+// count within 16..512 (96 if unknown), so that each fold's plain remainder
+// pass is timed as the run will make it (a 1D run is short, and one extra
+// pass is a large share of it: at T = 100, m = 6 leaves 4 plain steps where
+// m = 4 leaves none).
+int64_t tune_steps(const stencil_plan_s *p, int64_t T_run)
+{
+    if (p->ndim != 1) return 48;
+    return T_run > 0 ? std::min<int64_t>(512, std::max<int64_t>(16, T_run)) : 96;
+}
 
 struct Cand {
     int engine;  // 0 CUDA core, 1 tensor core
-    int m, b, ty;
+    int m, b, ty;  // ty: 2D tile rows; 1D points per CTA tile (0 = the default)
     int tess;    // 1D: exact tessellate tiling instead of overlapped tiles
     int thr = 0;  // 2D: threads per CTA (0 = the kernel's own, 256 = two half-size CTAs)
     int ns = 0;   // 2D: TMA stages per CTA (0 = automatic)
@@ -165,9 +173,11 @@ void tune_cache_put(const std::string &key, const std::string &value)
     fclose(f);
 }
 
-stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
+stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s, int64_t T_run)
 {
-    const std::string key = cache_key(p);
+    const int64_t T_tune = tune_steps(p, T_run);
+    // 1D choices depend on the steps they were timed over
+    const std::string key = cache_key(p) + (p->ndim == 1 ? "|T" + std::to_string(T_tune) : "");
     Cand best{0, 1, 1, 0, 0};
     if (cache_lookup(key, &best)) {
         p->tuned_engine = best.engine;
@@ -198,14 +208,20 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
             // every fold the 1D kernel has (radius up to 16): a fold costs
             // (2m+1)/m multiply-adds per step but saves m-1 shared-memory
             // round trips, and FP64 in particular is bound by the former
+            // and tile sizes: short tiles give more CTAs per SM for the
+            // latency-bound sweeps (measured on GB300, 2^20 points, T = 100:
+            // FP32 m = 4, b = 32 overlapped 3293 GS/s with 1024-point tiles
+            // against 2624 with 4096; FP64 m = 16 tessellated 238 with 256
+            // against 203 with 2048), long ones waste less rim at larger R
             if (sweep1d_supported(R, p->dtype == STENCIL_F64))
-                for (int b : {16, 32, 64}) {
-                    cands.push_back({0, m, b, 0, 0});
-                    // exact tessellate tiling (Section 3.4) of the same passes
-                    const int w = p->dtype == STENCIL_F64 ? 2048 : 4096;
-                    if (tess1d_fits(p->nx, w, std::min<int64_t>(b, kTuneSteps(1) / m + 1), R))
-                        cands.push_back({0, m, b, 0, 1});
-                }
+                for (int b : {16, 32, 64})
+                    for (int w : (p->dtype == STENCIL_F64 ? std::vector<int>{256, 512, 1024, 2048}
+                                                          : std::vector<int>{512, 1024, 2048, 4096})) {
+                        cands.push_back({0, m, b, w, 0});
+                        // exact tessellate tiling (Section 3.4) of the same passes
+                        if (tess1d_fits(p->nx, w, std::min<int64_t>(b, T_tune / m + 1), R))
+                            cands.push_back({0, m, b, w, 1});
+                    }
         } else if (p->ndim == 3) {
             if (sweep3d_supported(p->r, m, p->pattern)) cands.push_back({0, m, 1, 0, 0});
             if (sweep3d_tb_supported(p->r, m, p->pattern) && 2 * R <= std::min(kGhost, nmin))
@@ -249,7 +265,7 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     cudaEventCreate(&e1);
     const int saved_prec = p->precision, saved_b = p->block_b, saved_ty = p->tile_y;
     const int saved_thr = p->cta_threads, saved_ns = p->stages;
-    const int saved_tess = p->tessellate;
+    const int saved_tess = p->tessellate, saved_t1 = p->tile_1d;
     const int saved_graph = p->use_graph;
     // 2D/3D tuning runs are not worth capturing; 1D runs are launch-bound, so
     // their candidates are timed as the captured graphs a real run replays
@@ -258,12 +274,15 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     if (p->ndim != 1) p->use_graph = 0;
     // steps per timed run: 1D runs are short and launch-bound, so their
     // candidates are timed over more steps, closer to a whole run
-    const int64_t T = kTuneSteps(p->ndim);
+    const int64_t T = T_tune;
     double best_rate = -1.0;
     for (const Cand &c : cands) {
         p->precision = c.engine == 1 ? (saved_prec ? saved_prec : STENCIL_PREC_BF16X3) : STENCIL_PREC_FP32;
         p->block_b = c.b;
-        p->tile_y = c.ty;
+        if (p->ndim == 1)
+            p->tile_1d = c.ty;
+        else
+            p->tile_y = c.ty;
         p->tessellate = c.tess;
         if (p->ndim == 2 && c.engine == 0) {
             p->cta_threads = c.thr ? c.thr : saved_thr;
@@ -297,6 +316,7 @@ stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s)
     p->cta_threads = saved_thr;
     p->stages = saved_ns;
     p->tessellate = saved_tess;
+    p->tile_1d = saved_t1;
     p->use_graph = saved_graph;
     if (p->ndim == 1) {
         cudaStreamSynchronize(s);

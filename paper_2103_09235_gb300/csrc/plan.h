@@ -39,6 +39,7 @@ struct stencil_plan_s {
     int stages = 0;  // TMA stages per CTA of the 2D sweep (0 = automatic)
     int cta_threads = 0;  // threads per CTA of the 2D sweep (0 = automatic, or 256)
     int z_chunk = 0;  // output planes per CTA of the 3D sweeps (0 = automatic)
+    int tile_1d = 0;  // points per CTA of the 1D sweeps (0 = automatic)
     int persistent = -1;  // 3D single sweeps in one persistent launch: 1 always, 0 never, -1 automatic
     int tc_center = 1;
     int tc_tma_store = 1;
@@ -192,7 +193,8 @@ stencil_status_t launch_pass3d(stencil_plan_s *p, const Padded &src, int m, int 
 // FP64 2D and 3D grids (k_sweep_f64.cu), plain or folded.
 stencil_status_t run_f64nd(stencil_plan_s *p, const double *in, double *out, int64_t T, int m,
                            cudaStream_t s);
-stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s);
+// T_run: the steps of the run that asked (1D candidates are timed over them, capped).
+stencil_status_t autotune2d(stencil_plan_s *p, cudaStream_t s, int64_t T_run = 0);
 
 void clear_graphs(stencil_plan_s *p);
 // cpk: counterpart terms of the pass (0 = direct form); cp: their factors.

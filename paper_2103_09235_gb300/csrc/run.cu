@@ -75,7 +75,7 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
     const bool auto_fold = m == 0;
     if (m == 0) {
         if (p->tuned_m == 0 && p->autotune) {
-            stencil_status_t st = autotune2d(p, s);
+            stencil_status_t st = autotune2d(p, s, T);
             if (st != STENCIL_OK) return st;
         }
         m = p->tuned_m > 0 ? p->tuned_m : 1;
@@ -98,7 +98,11 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
     if (st == STENCIL_OK) st = plan_folded(p, 1, &c1);
     if (st != STENCIL_OK) return st;
 
-    const int tile = f64 ? 2048 : 4096;
+    // points per CTA tile: the plan's option, else the tuned size of an
+    // automatic fold, else 4096 (FP32) / 2048 (FP64)
+    const int tile = p->tile_1d > 0                    ? p->tile_1d
+                     : (auto_fold && p->tuned_ty > 0) ? p->tuned_ty
+                                                      : (f64 ? 2048 : 4096);
     const int bsteps = p->block_b > 0 ? p->block_b : 32;  // sweeps per launch
     const size_t bytes = esz * (size_t)p->nx;
     if (!p->d1a) {
@@ -181,12 +185,13 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
         return STENCIL_OK;
     };
     std::vector<int64_t> key = {1, (int64_t)(uintptr_t)in, (int64_t)(uintptr_t)out, T, m, bsteps,
-                                any_tess ? 1 : 0};
+                                any_tess ? 1 : 0, tile};
     st = run_maybe_graph(p, key, s, enqueue);
     p->last_m = m;
     p->last_b = bsteps;
     p->last_engine = 0;
     p->last_tess = (!passes.empty() && tess_pass[0]) ? 1 : 0;
+    p->last_ty = tile;
     return st;
 }
 

@@ -353,6 +353,9 @@ stencil_status_t stencil_plan_set_option(stencil_plan_t p, const char *key, int6
     } else if (!strcmp(key, "cta_threads")) {
         if (v != 0 && v != 256) goto bad;
         p->cta_threads = (int)v;
+    } else if (!strcmp(key, "tile_1d")) {
+        if (v != 0 && (v < 256 || v > 16384 || v % 256)) goto bad;
+        p->tile_1d = (int)v;
     } else if (!strcmp(key, "persistent")) {
         if (v < -1 || v > 1) goto bad;
         p->persistent = (int)v;

@@ -151,6 +151,33 @@ CASES_TESS = [
 ]
 
 
+@pytest.mark.parametrize("tile", [256, 512, 1024, 2048, 4096])
+@pytest.mark.parametrize("n,T,m,b,dt,tess", [
+    (65539, 100, 4, 32, "f32", 0), (65539, 100, 6, 16, "f32", 1), (1000, 37, 2, 16, "f32", 0),
+    (65539, 100, 16, 32, "f64", 1), (65539, 83, 8, 16, "f64", 0), (4097, 50, 3, 64, "f64", 1)])
+def test_sweep1d_tile_sizes(env, n, T, m, b, dt, tess, tile):
+    """The tile_1d option: every tile size, overlapped or tessellated (passes
+    that do not fit a short tile fall back to overlapped tiles), on ragged
+    lengths, matches the oracle (FP64 to 1e-12); the plan reports the size."""
+    torch, binding, oracle = env
+    c = synth.heat1d_coeffs() if n % 2 == 0 else synth.dyadic_coeffs(6, 1, 1, "box")
+    npdt = np.float64 if dt == "f64" else np.float32
+    x = synth.grid(3900 + n, (n,), npdt)
+    plan = binding.Plan((n,), c, dt)
+    plan.set_option("tessellate", tess).set_option("block_b", b).set_option("tile_1d", tile)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.run(xd, yd, T, fold_m=m)
+    plan.sync()
+    assert plan.get("last_tile_y") == tile
+    ref = oracle.run(x.astype(np.float64), c, T)
+    if dt == "f64":
+        check(yd.cpu().numpy(), ref, tol=1e-12, abs_tol=1e-12)
+    else:
+        check(yd.cpu().numpy(), ref)
+    plan.close()
+
+
 @pytest.mark.parametrize("n,T,m,b,dt", CASES_TESS)
 def test_sweep1d_tessellated(env, n, T, m, b, dt):
     """Triangles then inverted triangles: every pass that fits the tile runs
