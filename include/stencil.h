@@ -140,8 +140,9 @@ stencil_status_t stencil_plan_ex(stencil_plan_t *out_plan, int ndim, const int64
  *                   (0 = automatic: 16 for a single radius-1 sweep, else 32, halved
  *                   down to 8 while the grid has fewer than 4 CTAs per SM).
  *   "tile_1d"       1D sweeps: points per CTA tile, a multiple of 256 in 256..16384
- *                   (0 = automatic: the autotuner's size for fold_m = 0, else 4096
- *                   for FP32 and 2048 for FP64).
+ *                   (0 = automatic: the autotuner's size for fold_m = 0, else 1024
+ *                   for overlapped tiles up to folded radius 6 and 4096 above,
+ *                   4096 for tessellated FP32 and 1024 for tessellated FP64).
  *   "persistent"    3D CUDA-core runs: 1 = every run of two or more consecutive
  *                   single sweeps of one stencil in ONE persistent launch, whose
  *                   pieces (a 64 x 16 column, one z chunk) start as soon as the

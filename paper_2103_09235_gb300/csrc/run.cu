@@ -99,10 +99,16 @@ stencil_status_t run1d(stencil_plan_s *p, const void *in, void *out, int64_t T, 
     if (st != STENCIL_OK) return st;
 
     // points per CTA tile: the plan's option, else the tuned size of an
-    // automatic fold, else 4096 (FP32) / 2048 (FP64)
+    // automatic fold, else by form and radius -- measured on GB300, 2^20
+    // points, T = 100: overlapped tiles of 1024 points up to radius 6 (FP32
+    // m = 1 1176 against 993 GS/s with 4096, m = 4 3293 against 2624; FP64
+    // m = 1 156 against 138 with 2048) and 4096 above (m = 8: 2129 against
+    // 1859); tessellated FP32 4096 (m = 6: 2492 against 2174 with 1024),
+    // tessellated FP64 1024 (m = 4: 199 against 181 with 2048)
     const int tile = p->tile_1d > 0                    ? p->tile_1d
                      : (auto_fold && p->tuned_ty > 0) ? p->tuned_ty
-                                                      : (f64 ? 2048 : 4096);
+                     : use_tess                        ? (f64 ? 1024 : 4096)
+                     : (R <= 6 ? 1024 : 4096);
     const int bsteps = p->block_b > 0 ? p->block_b : 32;  // sweeps per launch
     const size_t bytes = esz * (size_t)p->nx;
     if (!p->d1a) {
